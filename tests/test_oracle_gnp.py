@@ -1,0 +1,232 @@
+"""Pins for the GNP oracle (oracle/gnp_ref.py) against the mathematics of Sec. 2.3.
+
+Every expected value here comes from a closed form, a hand computation, an
+independent brute-force evaluation or a library routine, never from the oracle.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import gnp_ref as G
+from paper_2406_00809_gb300 import inputs as I
+
+
+
+# ------------------------------------------------------------------ gamma (Eq. 6)
+
+def test_gamma_poisson_closed_form():
+    # interior row of the 5-point Laplacian: |4| + 4*|-1| = 8, and it is symmetric
+    A = I.poisson2d(7).to_scipy()
+    assert G.gamma(A) == 8.0
+
+
+def test_gamma_aniso3d_closed_form():
+    # interior row: 4 + 2*100 + 4*1 + 2*100 = 408 (the matrix is symmetric)
+    A = I.aniso3d(4, 100.0).to_scipy()
+    assert G.gamma(A) == 408.0
+
+
+def test_gamma_convdiff_closed_form():
+    nx, beta = 9, 100.0
+    h = 1.0 / (nx + 1)
+    expect = 8.0 / h**2 + 4.0 * beta / h  # c + 2|w| + 2|e| for interior rows and columns
+    assert abs(G.gamma(I.convdiff2d(nx, beta).to_scipy()) - expect) <= 1e-12 * expect
+
+
+def test_gamma_row_and_column_maxima_differ():
+    # rows sum to 3, 1, 1 (max 3); columns to 1, 2, 2 (max 2): gamma = min = 2
+    A = sp.csr_matrix(np.array([[1.0, -1.0, 1.0], [0.0, 1.0, 0.0], [0.0, 0.0, -1.0]]))
+    assert G.gamma(A) == 2.0
+    assert G.gamma(sp.csr_matrix(A.T)) == 2.0
+
+
+def test_gamma_matches_matrix_norms():
+    rng = np.random.default_rng(3)
+    D = rng.standard_normal((9, 9)) * (rng.random((9, 9)) < 0.4)
+    g = G.gamma(sp.csr_matrix(D))
+    assert np.isclose(g, min(np.linalg.norm(D, np.inf), np.linalg.norm(D, 1)), rtol=1e-15)
+
+
+# ------------------------------------------------------- forward vs brute force
+
+def brute_force_M(Adense, b, blob, L, form):
+    """Eqs. 6-8 evaluated with explicit scalar loops over a dense matrix."""
+    n = len(b)
+    d, hd = 16, 32
+    w = [float(t) for t in blob]
+    p = [0]
+
+    def take(k):
+        out = w[p[0]:p[0] + k]
+        p[0] += k
+        return out
+
+    eW1, eb1, eW2, eb2 = take(hd), take(hd), take(hd * d), take(d)
+    Us, Ws = [], []
+    for _ in range(L):
+        Us.append(take(d * d))
+        Ws.append(take(d * d))
+    dW1, db1, dW2, db2 = take(d * hd), take(hd), take(hd), take(1)
+    rowsum = max(sum(abs(Adense[i][j]) for j in range(n)) for i in range(n))
+    colsum = max(sum(abs(Adense[i][j]) for i in range(n)) for j in range(n))
+    gam = min(rowsum, colsum)
+    Ah = [[Adense[i][j] / gam for j in range(n)] for i in range(n)]
+    tau = sum(v * v for v in b) ** 0.5
+    u = [v * (n ** 0.5) / tau for v in b]
+    H = []
+    for i in range(n):
+        hid = [max(0.0, u[i] * eW1[k] + eb1[k]) for k in range(hd)]
+        H.append([sum(hid[k] * eW2[k * d + c] for k in range(hd)) + eb2[c] for c in range(d)])
+    for l in range(L):
+        U, W = Us[l], Ws[l]
+        AX = [[sum(Ah[i][j] * H[j][c] for j in range(n)) for c in range(d)] for i in range(n)]
+        Hn = []
+        for i in range(n):
+            row = []
+            for c in range(d):
+                s_w = sum(AX[i][k] * W[k * d + c] for k in range(d))
+                if form == 0:
+                    s_u = sum(H[i][k] * U[k * d + c] for k in range(d))
+                    row.append(max(0.0, s_u + s_w))
+                else:
+                    row.append(H[i][c] + max(0.0, s_w))
+            Hn.append(row)
+        H = Hn
+    z = []
+    for i in range(n):
+        hid = [max(0.0, sum(H[i][c] * dW1[c * hd + k] for c in range(d)) + db1[k]) for k in range(hd)]
+        z.append((sum(hid[k] * dW2[k] for k in range(hd)) + db2[0]) * tau / (n ** 0.5))
+    return np.array(z)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_forward_matches_brute_force(form):
+    rng = np.random.default_rng(11)
+    n, L = 7, 2
+    D = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.5) + np.diag(rng.random(n) + 1)
+    blob = I.init_weights(L, seed=5).astype(np.float64)
+    blob[np.r_[32:64]] = rng.standard_normal(32) * 0.3       # nonzero encoder biases
+    blob[-33:-1] = rng.standard_normal(32) * 0.3            # nonzero decoder b1
+    blob[-1] = 0.2
+    b = rng.standard_normal(n)
+    Ahat = G.normalise(sp.csr_matrix(D))
+    z = G.forward(Ahat, b, G.unpack(blob, L), form)
+    zb = brute_force_M(D.tolist(), b.tolist(), blob, L, form)
+    np.testing.assert_allclose(z, zb, rtol=1e-12, atol=1e-12)
+
+
+def test_linear_regime_kronecker_form():
+    """With every weight, bias, A_hat entry and b nonnegative no ReLU clips, and each
+    layer is the linear map vec(H') = (U^T (x) I + W^T (x) A_hat) vec(H)."""
+    rng = np.random.default_rng(2)
+    n, L = 6, 3
+    D = rng.random((n, n)) * (rng.random((n, n)) < 0.6) + np.eye(n)
+    Ahat = G.normalise(sp.csr_matrix(D)).toarray()
+    blob = np.abs(I.init_weights(L, seed=1).astype(np.float64)) * 0.5
+    P = G.unpack(blob, L)
+    b = rng.random(n) + 0.1
+    z = G.forward(sp.csr_matrix(Ahat), b, P, 0)
+    tau = np.linalg.norm(b)
+    u = b * np.sqrt(n) / tau
+    H0 = np.outer(u, P["enc_W1"][0] @ P["enc_W2"]) + np.outer(np.ones(n), P["enc_b1"] @ P["enc_W2"] + P["enc_b2"])
+    vecH = H0.reshape(-1, order="F")
+    for l in range(L):
+        T = np.kron(P["U"][l].T, np.eye(n)) + np.kron(P["W"][l].T, Ahat)
+        vecH = T @ vecH
+    HL = vecH.reshape(n, 16, order="F")
+    zz = (HL @ P["dec_W1"] + P["dec_b1"]) @ P["dec_W2"][:, 0] + P["dec_b2"][0]
+    np.testing.assert_allclose(z, zz * tau / np.sqrt(n), rtol=1e-12)
+
+
+def test_scale_equivariance_positive_alpha():
+    A = I.convdiff2d(6).to_scipy()
+    Ahat = G.normalise(A)
+    P = G.unpack(I.init_weights(3, seed=0), 3)
+    b = np.random.default_rng(0).standard_normal(A.shape[0])
+    z = G.forward(Ahat, b, P)
+    for alpha in (1e-3, 2.5, 1e5):
+        np.testing.assert_allclose(G.forward(Ahat, alpha * b, P), alpha * z, rtol=1e-12, atol=0)
+    assert np.all(G.forward(Ahat, 0 * b, P) == 0.0)
+
+
+def test_zero_layer_weights():
+    A = I.poisson2d(5).to_scipy()
+    Ahat = G.normalise(A)
+    L = 2
+    blob = I.init_weights(L, seed=4).astype(np.float64)
+    P = G.unpack(blob, L)
+    for l in range(L):
+        P["U"][l][:] = 0
+        P["W"][l][:] = 0
+    P["dec_b1"][:] = np.linspace(-1, 1, 32)
+    P["dec_b2"][:] = 0.3
+    b = np.random.default_rng(1).standard_normal(A.shape[0])
+    n = A.shape[0]
+    tau = np.linalg.norm(b)
+    # paper form: every hidden block after layer 1 is ReLU(0) = 0
+    z0 = G.forward(Ahat, b, P, 0)
+    const = (np.maximum(P["dec_b1"], 0) @ P["dec_W2"][:, 0] + 0.3) * tau / np.sqrt(n)
+    np.testing.assert_allclose(z0, np.full(n, const), rtol=1e-14)
+    # residual form with W = 0: the layers are the identity, so M = dec(enc(s(b)))
+    z1 = G.forward(Ahat, b, P, 1)
+    Hs = G.hidden_trace(Ahat, b, P, 1)
+    for H in Hs[1:]:
+        np.testing.assert_array_equal(H, Hs[0])
+    assert z1.shape == (n,)
+
+
+# ------------------------------------------------------------------- backward
+
+def _numeric_grad(f, w, idx, h=1e-6):
+    g = np.zeros(len(idx))
+    for t, i in enumerate(idx):
+        wp = w.copy(); wp[i] += h
+        wm = w.copy(); wm[i] -= h
+        g[t] = (f(wp) - f(wm)) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_backward_matches_central_differences(form):
+    rng = np.random.default_rng(7)
+    A = I.convdiff2d(4).to_scipy()
+    Ahat = G.normalise(A)
+    n, L, B = A.shape[0], 2, 3
+    blob = I.init_weights(L, seed=9).astype(np.float64)
+    blob[32:64] = 0.1 * rng.standard_normal(32)
+    b = rng.standard_normal((n, B))
+    c = rng.standard_normal((n, B))
+
+    def f(w):
+        return float((G.forward(Ahat, b, G.unpack(w, L), form) * c).sum())
+
+    P = G.unpack(blob, L)
+    _, cache = G.forward(Ahat, b, P, form, keep=True)
+    g = G.pack(G.backward(Ahat, P, cache, c))
+    idx = rng.choice(blob.size, 120, replace=False)
+    gn = _numeric_grad(f, blob, idx)
+    err = np.linalg.norm(g[idx] - gn) / np.linalg.norm(gn)
+    assert err < 1e-6, err
+
+
+def test_l1_loss_and_gradient():
+    # hand example: A = [[2, 1], [0, 1]], z = [1, -1], b = [0, 1]  ->  r = [1, -2]
+    A = sp.csr_matrix(np.array([[2.0, 1.0], [0.0, 1.0]]))
+    z = np.array([[1.0], [-1.0]])
+    b = np.array([[0.0], [1.0]])
+    loss, dz = G.l1_loss(A, z, b)
+    assert loss == 1.5  # (|1| + |-2|) / 2
+    # A^T sign(r) / 2 = [[2, 0], [1, 1]] [1, -1] / 2 = [1, 0]
+    np.testing.assert_array_equal(dz[:, 0], [1.0, 0.0])
+
+
+def test_adam_first_step_moves_by_lr():
+    # first step: m_hat = g and v_hat = g^2, so the update is lr * g / (|g| + eps)
+    opt = G.Adam(4, lr=1e-3)
+    w = np.array([1.0, -2.0, 0.5, 3.0])
+    g = np.array([0.3, -4.0, 1e-3, 0.0])
+    w1 = opt.step(w, g)
+    np.testing.assert_allclose(w - w1, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    # second step with the same gradient: m_hat = g, v_hat = g^2 again
+    w2 = opt.step(w1, g)
+    np.testing.assert_allclose(w1 - w2, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
