@@ -1,0 +1,230 @@
+/*
+ * gnp.h -- C ABI of the GB300 graph-neural-preconditioner library (libgnp.so).
+ *
+ * The library implements, as hand-written sm_103a CUDA kernels, the data-parallel hot
+ * path of "Graph Neural Preconditioners for Iterative Solutions of Sparse Linear
+ * Systems" (Chen, ICLR 2025):
+ *   - the GNP operator z = M(v): scaling s (Eq. 8), MLP encoder, L Res-GCONV layers
+ *     over A_hat = A / gamma (Eqs. 6-7), MLP decoder, back-scaling s^{-1};
+ *   - restarted flexible GMRES with M as a nonlinear right preconditioner (Sec. 2.1,
+ *     Eq. 1, Algorithm 1) in float64: SpMV, CGS2 orthogonalisation, Givens QR of the
+ *     Hessenberg matrix;
+ *   - GNP training (Sec. 2.2, Eq. 5, Sec. 3 "Hyperparameters"): the Arnoldi/Gaussian
+ *     training-pair sampler, forward, l1 residual loss, hand-written backward, Adam;
+ *   - a continuous-batching solve server on top of the solver.
+ *
+ * Conventions shared by every call
+ *   - Every call returns a gnp_status (0 = GNP_OK) and never aborts.  On failure
+ *     gnp_last_error() returns a message for the calling thread.
+ *   - Pointers named *_dev are device pointers owned by the caller, valid on the
+ *     current CUDA device; pointers named *_host are host pointers owned by the caller.
+ *     The library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Work is enqueued on that stream; calls documented "synchronous" wait for it.
+ *   - Objects returned through gnp_*_create are owned by the library and released by
+ *     the matching gnp_*_destroy.  They allocate device memory at creation; calls that
+ *     allocate later say so.
+ *   - Sparse matrices are CSR with int32 row_ptr[n+1] (row_ptr[0] = 0, nondecreasing),
+ *     int32 col[nnz] (0 <= col < n; any order within a row; duplicates are summed) and
+ *     float64 val[nnz].
+ *   - Hidden width d = 16 and MLP hidden width 32 are fixed (Sec. 3 "Hyperparameters").
+ *
+ * Weight blob (float32, count = gnp_weight_count(L)), every matrix row-major and applied
+ * from the right (y = x W + b, with W of shape d_in x d_out as in Sec. 2.3):
+ *   enc_W1[1*32], enc_b1[32], enc_W2[32*16], enc_b2[16],
+ *   for l in 0..L-1: U_l[16*16], W_l[16*16],
+ *   dec_W1[16*32], dec_b1[32], dec_W2[32*1], dec_b2[1].
+ * The residual layer form ignores U_l but keeps its slot.
+ */
+#ifndef GNP_H
+#define GNP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GNP_D 16
+#define GNP_MLP_HIDDEN 32
+#define GNP_MAX_LAYERS 32
+#define GNP_MAX_RESTART 128
+#define GNP_MAX_BATCH 64
+
+typedef enum {
+  GNP_OK = 0,
+  GNP_ERR_INVALID_ARG = 1,       /* bad argument (null pointer, size out of range) */
+  GNP_ERR_INVALID_CSR = 2,       /* CSR structure violates the conventions above */
+  GNP_ERR_OOM = 3,               /* device allocation failed */
+  GNP_ERR_CUDA = 4,              /* a CUDA runtime call failed (message has details) */
+  GNP_ERR_BREAKDOWN = 5,         /* Arnoldi breakdown with no usable direction */
+  GNP_ERR_STAGNATION = 6,        /* two restart cycles without residual decrease */
+  GNP_ERR_RESIDUAL_MISMATCH = 7, /* Givens residual met tol three cycles running while
+                                    the true residual did not (Sec. 4 "solution failure") */
+  GNP_ERR_NOT_CONVERGED = 8,     /* maxiters reached before rtol */
+  GNP_ERR_TIMEOUT = 9,           /* a bounded wait expired */
+  GNP_ERR_NAN = 10,              /* a NaN/Inf appeared in the iteration */
+  GNP_ERR_BUSY = 11              /* server: no capacity for the request right now */
+} gnp_status;
+
+typedef enum {
+  GNP_LAYER_PAPER = 0, /* Res-GCONV(X) = ReLU(X U + A_hat X W)         (Eq. 7) */
+  GNP_LAYER_RESID = 1  /* X + ReLU(A_hat X W)                          (residual variant) */
+} gnp_layer_form;
+
+typedef enum {
+  GNP_H_FP32 = 0, /* hidden block stored in float32 */
+  GNP_H_BF16 = 1  /* hidden block stored in bfloat16 (round-to-nearest-even), float32
+                     accumulation and weights */
+} gnp_hprec;
+
+typedef struct gnp_config {
+  int L;            /* Res-GCONV layers, 0..GNP_MAX_LAYERS (paper: 8) */
+  int form;         /* gnp_layer_form */
+  int hprec;        /* gnp_hprec used by gnp_apply / fgmres_solve */
+  int batch;        /* training batch B: a power of two in [4, GNP_MAX_BATCH] (paper: 16) */
+  int arnoldi_m;    /* Arnoldi steps of the Eq. 5 sampler, 1..64 (paper: 40) */
+  float lr;         /* Adam learning rate (paper: 1e-3) */
+  float beta1, beta2, eps; /* Adam constants (0.9, 0.999, 1e-8) */
+  unsigned long long seed; /* Philox key of all training draws */
+} gnp_config;
+
+typedef struct gnp_solve_info {
+  int iters;            /* Arnoldi steps taken (applications of M) */
+  int restarts;         /* completed restart cycles that did not converge */
+  int status;           /* gnp_status of the solve (also the return value) */
+  double rel_res_est;   /* last Givens residual estimate / ||b|| */
+  double rel_res_true;  /* ||b - A x|| / ||b|| of the returned x */
+  double seconds;       /* wall time of the solve, device-synchronised */
+  /* optional outputs, owned by the caller, may be NULL: */
+  double* res_history;  /* [maxiters+1]: relative residual after each iteration
+                           (entry 0 = initial); res_history_len receives the count */
+  int res_history_len;
+  double* hessenberg;   /* [(restart+1)*restart] column-major H_bar of the last cycle */
+  int hessenberg_cols;  /* receives the number of valid columns of it */
+  int cycles;           /* restart cycles launched */
+  int gconv_launches;   /* Res-GCONV launches timed (gnp_profile_gconv on), else 0 */
+  double gconv_ms;      /* their summed CUDA-event time in milliseconds */
+} gnp_solve_info;
+
+typedef struct gnp_mat gnp_mat;
+typedef struct gnp_model gnp_model;
+typedef struct gnp_server gnp_server;
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* Human-readable name of a status code (static string). */
+const char* gnp_status_string(int status);
+/* Message of the last failing call on this thread (static storage, never NULL). */
+const char* gnp_last_error(void);
+/* Number of float32 weights for L layers: 592 + 512 L + 577. */
+int gnp_weight_count(int L);
+
+/* ---------------------------------------------------------------- matrices */
+
+/* Copy a CSR matrix to the device.  on_device = 0: the three arrays are host
+ * pointers; 1: device pointers.  The structure is validated (row_ptr monotone,
+ * 0 <= col < n) before anything is allocated: violations give GNP_ERR_INVALID_CSR.
+ * 1 <= n, 0 <= nnz < 2^31.  Synchronous.  The matrix also builds its transpose
+ * lazily on first use by training (one extra allocation of nnz + n ints). */
+int gnp_mat_create(int n, long long nnz, const int* row_ptr, const int* col,
+                   const double* val, int on_device, void* stream, gnp_mat** out);
+void gnp_mat_destroy(gnp_mat* A);
+int gnp_mat_info(const gnp_mat* A, int* n, long long* nnz);
+
+/* gamma = min(max_i sum_j |a_ij|, max_j sum_i |a_ij|)  (Eq. 6), computed on the
+ * device in float64.  Synchronous; writes the host scalar *gamma_out. */
+int gnp_gamma(const gnp_mat* A, double* gamma_out, void* stream);
+
+/* y = A x in float64 (the SpMV of the FGMRES step, Algorithm 1).  x_dev, y_dev:
+ * device float64 [n]; they must not overlap. */
+int gnp_spmv(const gnp_mat* A, const double* x_dev, double* y_dev, void* stream);
+
+/* ---------------------------------------------------------------- GNP model */
+
+/* Build the preconditioner for A: computes gamma and A_hat = A/gamma (Eq. 6) as
+ * float32 values on the device and uploads the weight blob (weights_host, float32,
+ * gnp_weight_count(cfg->L) entries).  A must outlive the model.  Synchronous. */
+int gnp_create(const gnp_mat* A, const gnp_config* cfg, const float* weights_host,
+               gnp_model** out);
+void gnp_destroy(gnp_model* M);
+/* The model's gamma (Eq. 6). */
+int gnp_model_gamma(const gnp_model* M, double* gamma_out);
+/* Copy the weights out: after training, the best-loss snapshot (Sec. 3 keeps the
+ * model of the best training step).  *count receives the blob length; host_blob may
+ * be NULL to query it.  Synchronous. */
+int gnp_get_weights(gnp_model* M, float* host_blob, int* count);
+/* Replace the weights (and reset the Adam state and the best-loss snapshot). */
+int gnp_set_weights(gnp_model* M, const float* host_blob, int count);
+/* Change the hidden-block storage precision used by gnp_apply / fgmres_solve. */
+int gnp_set_hprec(gnp_model* M, int hprec);
+
+/* z = M(v) (Sec. 2.3, Fig. 1, Eqs. 6-8) for one vector: v_dev float64 [n] (read
+ * only), z_dev float32 [n].  tau = ||v||_2 = 0 gives z = 0.  Asynchronous. */
+int gnp_apply(gnp_model* M, const double* v_dev, float* z_dev, void* stream);
+/* As gnp_apply, and also writes the hidden blocks H^0..H^L as float32
+ * [(L+1) * n * 16] (node-major, 16 contiguous per node) to hidden_dev (may be NULL). */
+int gnp_apply_trace(gnp_model* M, const double* v_dev, float* z_dev, float* hidden_dev,
+                    void* stream);
+
+/* ---------------------------------------------------------------- training */
+
+/* Batched forward z = M(b) for B right-hand sides stored node-major (b_dev float32
+ * [n*B], element (i, k) at i*B + k); z_dev float32 [n*B].  Saves the activations in
+ * the model for gnp_backward_batch (one batch at a time).  FP32 hidden block. */
+int gnp_forward_batch(gnp_model* M, const float* b_dev, int B, float* z_dev, void* stream);
+/* Hand-written backward of the last gnp_forward_batch: given dL/dz (float32 [n*B]),
+ * writes dL/dweights (float32 [gnp_weight_count(L)]) to grad_dev (overwritten). */
+int gnp_backward_batch(gnp_model* M, const float* dz_dev, float* grad_dev, void* stream);
+/* Training pairs of step `step` (Sec. 3: the first B/2 columns x = V_m Z S^-1 eps of
+ * Eq. 5, the rest x ~ N(0, I)), written node-major to x_dev float32 [n*B] with
+ * B = cfg.batch.  The first call runs the sampler's Arnoldi process and SVD. */
+int gnp_sample_batch(gnp_model* M, int step, float* x_dev, void* stream);
+/* One optimisation step on given solutions x (float32 [n*B] node-major): b = A_hat x,
+ * z = M(b), loss = mean |A_hat z - b| (Sec. 3), backward, Adam, best-loss snapshot.
+ * *loss_out (host, may be NULL) receives the loss before the update (synchronous
+ * when non-NULL). */
+int gnp_train_step_pairs(gnp_model* M, const float* x_dev, int B, float* loss_out,
+                         void* stream);
+/* One optimisation step on the model's own sampled batch (gnp_sample_batch of the
+ * model's internal step counter, then gnp_train_step_pairs). */
+int gnp_train_step(gnp_model* M, float* loss_out, void* stream);
+/* Run `steps` training steps back to back (no per-step host sync); *best_loss_out
+ * (host, may be NULL) receives the best loss seen.  Synchronous. */
+int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream);
+
+/* Replace the training weights from device memory (float32 [count], count =
+ * gnp_weight_count(L)); also becomes the applied (best) snapshot.  Asynchronous. */
+int gnp_set_weights_device(gnp_model* M, const float* w_dev, int count, void* stream);
+
+/* Philox4x32-10 (Salmon et al., SC'11), the generator of every training draw: out[i] =
+ * philox(ctr[i], key) for `count` 4 x uint32 counters (device arrays of 4*count words).
+ * Exposed so that callers can check the generator bit for bit. */
+int gnp_philox4x32_10(const unsigned* ctr_dev, unsigned key0, unsigned key1, int count,
+                      unsigned* out_dev, void* stream);
+
+/* ---------------------------------------------------------------- solver */
+
+/* Solve A x = b by restarted FGMRES(restart) with right preconditioner M (NULL =
+ * identity, i.e. plain GMRES), x0 = the incoming x_dev, tolerance rtol * ||b||_2,
+ * at most maxiters Arnoldi steps (Algorithm 1; stopping rules in the oracle's
+ * documentation).  b_dev, x_dev: device float64 [n].  The Krylov basis V
+ * ([n*(restart+1)] float64), Z ([n*restart] float32) and the reduction scratch are
+ * cached in A and grown on demand (this may allocate).  Synchronous: returns when
+ * the solve has ended; `info` (may be NULL) receives the statistics.
+ * Returns GNP_OK on convergence, otherwise the failure status. */
+int fgmres_solve(gnp_mat* A, const double* b_dev, double* x_dev, gnp_model* M,
+                 int restart, double rtol, int maxiters, gnp_solve_info* info,
+                 void* stream);
+
+/* Time every Res-GCONV launch of the following solves with CUDA events recorded on
+ * the solve's stream around the launch (inside the captured restart cycle); the sums
+ * arrive in gnp_solve_info.gconv_ms / gconv_launches.  The event records add a little
+ * time to the solve, so keep it off when timing the solve itself.  Process-wide. */
+int gnp_profile_gconv(int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GNP_H */

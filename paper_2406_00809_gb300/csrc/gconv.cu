@@ -1,0 +1,578 @@
+// The GNP operator z = M(v) (Sec. 2.3, Fig. 1): scaling s (Eq. 8), MLP encoder,
+// L Res-GCONV layers over A_hat = A/gamma (Eqs. 6-7), MLP decoder, back-scaling.
+//
+// Kernels (one launch each):
+//   k_vnorm    tau = ||v||_2 (deterministic two-level reduction); optionally first
+//              divides v in place by a device scalar (the FGMRES step normalises
+//              v_j = w / h_{j,j-1} in the same pass).
+//   k_encode   u_i = (sqrt(n)/tau) v_i; h_i = W2^T ReLU(W1^T u_i + b1) + b2 (1->32->16).
+//   k_gconv    one Res-GCONV layer: nnz-balanced CSR gather (A_hat H)_i over the n x 16
+//              hidden block with 16-byte loads, then per row (thread-per-row epilogue)
+//              ReLU(h_i U + (A_hat H)_i W)  or  h_i + ReLU((A_hat H)_i W), with U and W
+//              read as uniform constant-bank operands from the kernel parameters.
+//   k_gconv_dec the last layer with the decoder (16->32->1) and the back-scaling
+//              tau/sqrt(n) fused into the epilogue: writes z_i, never H^L.
+// Hidden blocks are node-major (16 contiguous values per node), float32 or bfloat16.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace gnp {
+
+
+// A_hat values = A / gamma in float32 (Eq. 6), in the CSR order.
+__global__ void k_scale_values(const double* __restrict__ val, long long nnz, double gamma,
+                               float* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = (float)(val[e] / gamma);
+}
+
+// ---------------------------------------------------------------- traits
+
+struct TrF32 {  // float32 hidden block: 4 lanes x float4 per 64-byte row
+  static constexpr int G = 4, NV = 4, STRIDE = 20;
+  using acc = float;
+  using val_t = float;
+  using x_t = float;
+  __device__ __forceinline__ static void load(const float* X, int c, int q, float (&h)[4]) {
+    float4 t = __ldg(reinterpret_cast<const float4*>(X + (size_t)c * 16) + q);
+    h[0] = t.x; h[1] = t.y; h[2] = t.z; h[3] = t.w;
+  }
+};
+
+struct TrBF16 {  // bfloat16 hidden block: 2 lanes x 8 values (16 bytes) per 32-byte row
+  static constexpr int G = 2, NV = 8, STRIDE = 20;
+  using acc = float;
+  using val_t = float;
+  using x_t = uint16_t;
+  __device__ __forceinline__ static void load(const uint16_t* X, int c, int q, float (&h)[8]) {
+    uint4 t = __ldg(reinterpret_cast<const uint4*>(X + (size_t)c * 16) + q);
+    h[0] = bf16lo(t.x); h[1] = bf16hi(t.x); h[2] = bf16lo(t.y); h[3] = bf16hi(t.y);
+    h[4] = bf16lo(t.z); h[5] = bf16hi(t.z); h[6] = bf16lo(t.w); h[7] = bf16hi(t.w);
+  }
+};
+
+template <class HT> struct HTraits;
+template <> struct HTraits<float> {
+  using TR = TrF32;
+  static constexpr int ROW_BYTES = 64;
+  static constexpr int SROW = 20;  // smem staging stride in floats
+};
+template <> struct HTraits<uint16_t> {
+  using TR = TrBF16;
+  static constexpr int ROW_BYTES = 32;
+  static constexpr int SROW = 12;  // smem staging stride in 32-bit words (48 bytes)
+};
+
+__device__ __forceinline__ void* colptr(const ColPtr& p) {
+  int j = p.jptr ? *p.jptr : 0;
+  return static_cast<char*>(p.base) + (size_t)(j + p.off) * p.stride;
+}
+
+// ---------------------------------------------------------------- k_vnorm
+
+template <bool SCALE>
+__global__ void __launch_bounds__(RED_THREADS)
+k_vnorm(ColPtr vp, const double* __restrict__ vscale, const int* __restrict__ ctl, int n,
+        double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ tau) {
+  if (ctl && !ctl[1]) return;
+  __shared__ double sh[32];
+  double* v = static_cast<double*>(colptr(vp));
+  double s = SCALE ? *vscale : 1.0;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x = v[i];
+    if (SCALE) {
+      x = x / s;
+      v[i] = x;
+    }
+    acc += x * x;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block_arrive(counter)) {
+    __shared__ double tot[1];
+    reduce_partials(partials, gridDim.x, 1, tot);
+    if (threadIdx.x == 0) {
+      *tau = sqrt(tot[0]);
+      *counter = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- tile staging
+
+// Store one hidden row per thread (float32 values) to a smem staging tile, then the
+// block writes the tile to global memory with coalesced 16-byte stores.
+template <class HT>
+__device__ __forceinline__ void stage_row(uint32_t* stile, int t, const float (&o)[16]) {
+  if constexpr (sizeof(HT) == 4) {
+    float4* d = reinterpret_cast<float4*>(stile + t * HTraits<HT>::SROW);
+    d[0] = make_float4(o[0], o[1], o[2], o[3]);
+    d[1] = make_float4(o[4], o[5], o[6], o[7]);
+    d[2] = make_float4(o[8], o[9], o[10], o[11]);
+    d[3] = make_float4(o[12], o[13], o[14], o[15]);
+  } else {
+    uint4* d = reinterpret_cast<uint4*>(stile + t * HTraits<HT>::SROW);
+    d[0] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                      pack_bf16x2(o[6], o[7]));
+    d[1] = make_uint4(pack_bf16x2(o[8], o[9]), pack_bf16x2(o[10], o[11]),
+                      pack_bf16x2(o[12], o[13]), pack_bf16x2(o[14], o[15]));
+  }
+}
+
+template <class HT>
+__device__ __forceinline__ void unstage_row(const uint32_t* stile, int t, float (&o)[16]) {
+  if constexpr (sizeof(HT) == 4) {
+    const float4* s = reinterpret_cast<const float4*>(stile + t * HTraits<HT>::SROW);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 v = s[k];
+      o[4 * k] = v.x; o[4 * k + 1] = v.y; o[4 * k + 2] = v.z; o[4 * k + 3] = v.w;
+    }
+  } else {
+    const uint4* s = reinterpret_cast<const uint4*>(stile + t * HTraits<HT>::SROW);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      uint4 v = s[k];
+      o[8 * k + 0] = bf16lo(v.x); o[8 * k + 1] = bf16hi(v.x);
+      o[8 * k + 2] = bf16lo(v.y); o[8 * k + 3] = bf16hi(v.y);
+      o[8 * k + 4] = bf16lo(v.z); o[8 * k + 5] = bf16hi(v.z);
+      o[8 * k + 6] = bf16lo(v.w); o[8 * k + 7] = bf16hi(v.w);
+    }
+  }
+}
+
+// Coalesced copy between a global tile of `rows` hidden rows and the smem staging tile.
+template <class HT, bool TO_GLOBAL>
+__device__ __forceinline__ void tile_copy(uint32_t* stile, HT* g, int r0, int rows) {
+  constexpr int V16 = HTraits<HT>::ROW_BYTES / 16;  // 16-byte chunks per row
+  uint4* gb = reinterpret_cast<uint4*>(g + (size_t)r0 * 16);
+  for (int i = threadIdx.x; i < rows * V16; i += blockDim.x) {
+    int r = i / V16, k = i % V16;
+    uint4* s = reinterpret_cast<uint4*>(stile + r * HTraits<HT>::SROW) + k;
+    if (TO_GLOBAL) gb[i] = *s;
+    else *s = __ldg(gb + i);
+  }
+}
+
+// ---------------------------------------------------------------- k_encode
+
+template <class HT>
+__global__ void __launch_bounds__(TILE)
+k_encode(ColPtr vp, const double* __restrict__ tau, const int* __restrict__ ctl, int n,
+         double sqrt_n, HT* __restrict__ H, const __grid_constant__ EncW ew) {
+  if (ctl && !ctl[1]) return;
+  __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
+  const double* v = static_cast<const double*>(colptr(vp));
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  const int t = threadIdx.x;
+  const double tv = *tau;
+  const double f = tv > 0.0 ? sqrt_n / tv : 0.0;
+  if (t < rows) {
+    float u = (float)(v[r0 + t] * f);
+    float h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = ew.b2[c];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      float a = fmaxf(fmaf(u, ew.W1[k], ew.b1[k]), 0.0f);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) h[c] = fmaf(a, ew.W2[k * 16 + c], h[c]);
+    }
+    stage_row<HT>(stile, t, h);
+  }
+  __syncthreads();
+  tile_copy<HT, true>(stile, H, r0, rows);
+}
+
+// ---------------------------------------------------------------- k_gconv
+
+template <class HT>
+struct GconvSmem {
+  TileSmem<typename HTraits<HT>::TR> g;
+  __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
+};
+
+// Layer epilogue for one row: out = ReLU(h U + agg W) (paper) or h + ReLU(agg W).
+template <int FORM>
+__device__ __forceinline__ void layer_rows(const float (&h)[16], const float (&agg)[16],
+                                           const LayerW& lw, float (&o)[16]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) o[k] = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) o[k] = fmaf(agg[c], lw.W[c * 16 + k], o[k]);
+  }
+  if (FORM == GNP_LAYER_PAPER) {
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o[k] = fmaf(h[c], lw.U[c * 16 + k], o[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) o[k] = fmaxf(o[k], 0.0f);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) o[k] = h[k] + fmaxf(o[k], 0.0f);
+  }
+}
+
+// Gather + per-row layer; leaves the layer output of row t in `o` (valid for t < rows).
+template <class HT, int FORM>
+__device__ __forceinline__ void gconv_body(GconvSmem<HT>& sm, const int* __restrict__ rp,
+                                           const int* __restrict__ col, const float* __restrict__ valhat,
+                                           const HT* __restrict__ Hin, int r0, int rows,
+                                           const LayerW& lw, float (&o)[16]) {
+  using TR = typename HTraits<HT>::TR;
+  tile_load_rp<TR>(sm.g, rp, r0, rows);
+  tile_copy<HT, false>(sm.stile, const_cast<HT*>(Hin), r0, rows);
+  __syncthreads();
+  tile_gather<TR>(sm.g, rows, col, valhat, Hin);
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < rows) {
+    float h[16], agg[16];
+    unstage_row<HT>(sm.stile, t, h);
+    tile_row_sum<TR, 16>(sm.g, t, 0, agg);
+    layer_rows<FORM>(h, agg, lw, o);
+  }
+}
+
+template <class HT, int FORM>
+__global__ void __launch_bounds__(TILE, 3)
+k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
+        const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
+        const __grid_constant__ LayerW lw) {
+  if (ctl && !ctl[1]) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  GconvSmem<HT>& sm = *reinterpret_cast<GconvSmem<HT>*>(smraw);
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  float o[16];
+  gconv_body<HT, FORM>(sm, rp, col, valhat, Hin, r0, rows, lw, o);
+  // own row was read from stile by this thread only: safe to overwrite in place
+  if (threadIdx.x < rows) stage_row<HT>(sm.stile, threadIdx.x, o);
+  __syncthreads();
+  tile_copy<HT, true>(sm.stile, Hout, r0, rows);
+}
+
+// Decoder for one row: (w2^T ReLU(D1^T h + e1) + e2) * back.
+__device__ __forceinline__ float decode_row(const float (&o)[16], const DecW& dw) {
+  float z = dw.b2;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    float a = dw.b1[k];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a = fmaf(o[c], dw.W1[c * 32 + k], a);
+    z = fmaf(fmaxf(a, 0.0f), dw.W2[k], z);
+  }
+  return z;
+}
+
+template <class HT, int FORM>
+__global__ void __launch_bounds__(TILE, 3)
+k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
+            const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n,
+            int n, const int* __restrict__ ctl, const __grid_constant__ LayerW lw,
+            const __grid_constant__ DecW dw) {
+  if (ctl && !ctl[1]) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  GconvSmem<HT>& sm = *reinterpret_cast<GconvSmem<HT>*>(smraw);
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  float o[16];
+  gconv_body<HT, FORM>(sm, rp, col, valhat, Hin, r0, rows, lw, o);
+  if (threadIdx.x < rows) {
+    const double tv = *tau;
+    const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+    float* z = static_cast<float*>(colptr(zp));
+    z[r0 + threadIdx.x] = decode_row(o, dw) * back;
+  }
+}
+
+// Standalone decoder (L = 0, or the trace path that keeps H^L).
+template <class HT>
+__global__ void __launch_bounds__(TILE)
+k_decode(const HT* __restrict__ H, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
+         const int* __restrict__ ctl, const __grid_constant__ DecW dw) {
+  if (ctl && !ctl[1]) return;
+  __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  tile_copy<HT, false>(stile, const_cast<HT*>(H), r0, rows);
+  __syncthreads();
+  if (threadIdx.x < rows) {
+    float o[16];
+    unstage_row<HT>(stile, threadIdx.x, o);
+    const double tv = *tau;
+    const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+    float* z = static_cast<float*>(colptr(zp));
+    z[r0 + threadIdx.x] = decode_row(o, dw) * back;
+  }
+}
+
+template <class HT>
+__global__ void k_hidden_to_f32(const HT* __restrict__ H, float* __restrict__ out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(HT) == 4) out[i] = H[i];
+    else out[i] = __uint_as_float(((uint32_t)H[i]) << 16);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+static void fill_params(const std::vector<float>& w, int L, EncW& ew, DecW& dw) {
+  memcpy(ew.W1, w.data() + ENC_W1, sizeof(ew.W1));
+  memcpy(ew.b1, w.data() + ENC_B1, sizeof(ew.b1));
+  memcpy(ew.W2, w.data() + ENC_W2, sizeof(ew.W2));
+  memcpy(ew.b2, w.data() + ENC_B2, sizeof(ew.b2));
+  const float* d = w.data() + dec_off(L);
+  memcpy(dw.W1, d, sizeof(dw.W1));
+  memcpy(dw.b1, d + 512, sizeof(dw.b1));
+  memcpy(dw.W2, d + 544, sizeof(dw.W2));
+  dw.b2 = d[576];
+}
+
+static void fill_layer(const std::vector<float>& w, int l, LayerW& lw) {
+  const float* p = w.data() + layer_off(l);
+  memcpy(lw.U, p, sizeof(lw.U));
+  memcpy(lw.W, p + 256, sizeof(lw.W));
+}
+
+template <class HT, int FORM>
+static int set_smem_attrs() {
+  static bool done = false;
+  if (done) return GNP_OK;
+  const int bytes = (int)sizeof(GconvSmem<HT>);
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = true;
+  return GNP_OK;
+}
+
+template <class HT, int FORM>
+static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
+                      const int* ctl, cudaStream_t st, cudaEvent_t* ev) {
+  const gnp_mat* A = M->A;
+  const int n = A->n, L = M->cfg.L;
+  const double sqrt_n = std::sqrt((double)n);
+  GNP_TRY((set_smem_attrs<HT, FORM>()));
+  const int smem = (int)sizeof(GconvSmem<HT>);
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  if (vscale)
+    k_vnorm<true><<<nb, RED_THREADS, 0, st>>>(v, vscale, ctl, n, M->red.partials, M->red.counter, M->tau);
+  else
+    k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, M->red.partials, M->red.counter, M->tau);
+  EncW ew;
+  DecW dw;
+  fill_params(M->w_host, L, ew, dw);
+  HT* H0 = static_cast<HT*>(M->H[0]);
+  HT* H1 = static_cast<HT*>(M->H[1]);
+  k_encode<HT><<<nt, TILE, 0, st>>>(v, M->tau, ctl, n, sqrt_n, H0, ew);
+  const long long hcount = (long long)n * 16;
+  if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, hcount);
+  const int fused_last = (L > 0 && !trace) ? 1 : 0;
+  for (int l = 0; l < L - fused_last; ++l) {
+    LayerW lw;
+    fill_layer(M->w_host, l, lw);
+    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * l], st));
+    k_gconv<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
+    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * l + 1], st));
+    if (trace)
+      k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
+    std::swap(H0, H1);
+  }
+  if (fused_last) {
+    LayerW lw;
+    fill_layer(M->w_host, L - 1, lw);
+    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * (L - 1)], st));
+    k_gconv_dec<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, M->tau, sqrt_n, n,
+                                                  ctl, lw, dw);
+    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * (L - 1) + 1], st));
+  } else {
+    k_decode<HT><<<nt, TILE, 0, st>>>(H0, z, M->tau, sqrt_n, n, ctl, dw);
+  }
+  return check_launch("gnp apply");
+}
+
+int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
+                 const int* ctl, cudaStream_t st, cudaEvent_t* ev) {
+  GNP_TRY(model_sync_host(M));
+  const int form = M->cfg.form;
+  if (M->hprec == GNP_H_BF16) {
+    return form == GNP_LAYER_PAPER ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev)
+                                   : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev);
+  }
+  return form == GNP_LAYER_PAPER ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev)
+                                 : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev);
+}
+
+int apply_prepare(gnp_model* M) {
+  GNP_TRY(model_sync_host(M));
+  if (M->hprec == GNP_H_BF16) {
+    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((set_smem_attrs<uint16_t, GNP_LAYER_PAPER>()));
+    else GNP_TRY((set_smem_attrs<uint16_t, GNP_LAYER_RESID>()));
+  } else {
+    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((set_smem_attrs<float, GNP_LAYER_PAPER>()));
+    else GNP_TRY((set_smem_attrs<float, GNP_LAYER_RESID>()));
+  }
+  return GNP_OK;
+}
+
+unsigned long long model_version(const gnp_model* M) { return M->version; }
+
+int model_sync_host(gnp_model* M) {
+  if (!M->host_stale) return GNP_OK;
+  GNP_TRY_CUDA(cudaMemcpy(M->w_host.data(), M->w_best, sizeof(float) * M->w_host.size(),
+                          cudaMemcpyDeviceToHost));
+  M->host_stale = false;
+  return GNP_OK;
+}
+
+}  // namespace gnp
+
+using namespace gnp;
+
+extern "C" {
+
+int gnp_create(const gnp_mat* Ac, const gnp_config* cfg, const float* weights_host, gnp_model** out) {
+  GNP_REQUIRE(out != nullptr, "gnp_create: out is null");
+  *out = nullptr;
+  GNP_REQUIRE(Ac && cfg && weights_host, "gnp_create: null argument");
+  GNP_REQUIRE(cfg->L >= 0 && cfg->L <= GNP_MAX_LAYERS, "gnp_create: L = %d out of range", cfg->L);
+  GNP_REQUIRE(cfg->form == GNP_LAYER_PAPER || cfg->form == GNP_LAYER_RESID, "gnp_create: bad form");
+  GNP_REQUIRE(cfg->hprec == GNP_H_FP32 || cfg->hprec == GNP_H_BF16, "gnp_create: bad hprec");
+  gnp_mat* A = const_cast<gnp_mat*>(Ac);
+  gnp_model* M = new gnp_model();
+  M->A = A;
+  M->cfg = *cfg;
+  M->hprec = cfg->hprec;
+  const int cnt = weight_count(cfg->L);
+  M->w_host.assign(weights_host, weights_host + cnt);
+  int s = GNP_OK;
+  const int n = A->n;
+  const long long nnz = A->nnz;
+  double* gdev = nullptr;
+  do {
+    if ((s = dev_alloc(&M->valhat, (size_t)std::max<long long>(nnz, 1))) != GNP_OK) break;
+    if ((s = dev_alloc(reinterpret_cast<float**>(&M->H[0]), (size_t)n * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(reinterpret_cast<float**>(&M->H[1]), (size_t)n * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&M->tau, 2)) != GNP_OK) break;
+    if ((s = dev_alloc(&M->w_dev, (size_t)cnt)) != GNP_OK) break;
+    if ((s = dev_alloc(&M->w_best, (size_t)cnt)) != GNP_OK) break;
+    if ((s = red_alloc(M->red, 4 * NUM_SMS_GB300, 1)) != GNP_OK) break;
+    if ((s = dev_alloc(&gdev, 1)) != GNP_OK) break;
+    if ((s = gamma_launch(A, gdev, 0)) != GNP_OK) break;
+    cudaError_t e = cudaMemcpy(&M->gamma, gdev, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      set_error("gnp_create: %s", cudaGetErrorString(e));
+      s = GNP_ERR_CUDA;
+      break;
+    }
+    if (!(M->gamma > 0.0) || !std::isfinite(M->gamma)) {
+      set_error("gnp_create: gamma = %g (matrix is zero or not finite)", M->gamma);
+      s = GNP_ERR_INVALID_ARG;
+      break;
+    }
+    if ((s = gnp_set_weights(M, weights_host, cnt)) != GNP_OK) break;
+  } while (0);
+  dev_free(gdev);
+  if (s != GNP_OK) {
+    gnp_destroy(M);
+    return s;
+  }
+  // A_hat = A / gamma in float32 (Eq. 6)
+  if (nnz > 0) k_scale_values<<<4 * NUM_SMS_GB300, 256>>>(A->val, nnz, M->gamma, M->valhat);
+  s = check_launch("k_scale_values");
+  if (s == GNP_OK && cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("gnp_create: %s", cudaGetErrorString(cudaGetLastError()));
+    s = GNP_ERR_CUDA;
+  }
+  if (s != GNP_OK) {
+    gnp_destroy(M);
+    return s;
+  }
+  *out = M;
+  return GNP_OK;
+}
+
+void gnp_destroy(gnp_model* M) {
+  if (!M) return;
+  train_free(M->train);
+  M->train = nullptr;
+  dev_free(M->valhat);
+  dev_free(M->valhat_t);
+  float* h0 = static_cast<float*>(M->H[0]);
+  float* h1 = static_cast<float*>(M->H[1]);
+  dev_free(h0);
+  dev_free(h1);
+  dev_free(M->tau);
+  dev_free(M->w_dev);
+  dev_free(M->w_best);
+  red_free(M->red);
+  delete M;
+}
+
+int gnp_model_gamma(const gnp_model* M, double* gamma_out) {
+  GNP_REQUIRE(M && gamma_out, "gnp_model_gamma: null argument");
+  *gamma_out = M->gamma;
+  return GNP_OK;
+}
+
+int gnp_set_hprec(gnp_model* M, int hprec) {
+  GNP_REQUIRE(M, "gnp_set_hprec: null model");
+  GNP_REQUIRE(hprec == GNP_H_FP32 || hprec == GNP_H_BF16, "gnp_set_hprec: bad hprec %d", hprec);
+  if (M->hprec != hprec) ++M->version;
+  M->hprec = hprec;
+  return GNP_OK;
+}
+
+int gnp_apply(gnp_model* M, const double* v_dev, float* z_dev, void* stream) {
+  return gnp_apply_trace(M, v_dev, z_dev, nullptr, stream);
+}
+
+int gnp_apply_trace(gnp_model* M, const double* v_dev, float* z_dev, float* hidden_dev, void* stream) {
+  GNP_REQUIRE(M && v_dev && z_dev, "gnp_apply: null argument");
+  ColPtr v{const_cast<double*>(v_dev), 0, nullptr, 0};
+  ColPtr z{z_dev, 0, nullptr, 0};
+  return apply_launch(M, v, nullptr, z, hidden_dev, nullptr, as_stream(stream));
+}
+
+
+
+int gnp_get_weights(gnp_model* M, float* host_blob, int* count) {
+  GNP_REQUIRE(M && count, "gnp_get_weights: null argument");
+  const int cnt = weight_count(M->cfg.L);
+  if (!host_blob) {
+    *count = cnt;
+    return GNP_OK;
+  }
+  GNP_REQUIRE(*count >= cnt, "gnp_get_weights: buffer of %d < %d floats", *count, cnt);
+  GNP_TRY(model_sync_host(M));
+  memcpy(host_blob, M->w_host.data(), sizeof(float) * cnt);
+  *count = cnt;
+  return GNP_OK;
+}
+
+int gnp_set_weights(gnp_model* M, const float* host_blob, int count) {
+  GNP_REQUIRE(M && host_blob, "gnp_set_weights: null argument");
+  const int cnt = weight_count(M->cfg.L);
+  GNP_REQUIRE(count == cnt, "gnp_set_weights: got %d floats, expected %d", count, cnt);
+  M->w_host.assign(host_blob, host_blob + cnt);
+  M->host_stale = false;
+  ++M->version;
+  GNP_TRY_CUDA(cudaMemcpy(M->w_dev, host_blob, sizeof(float) * cnt, cudaMemcpyHostToDevice));
+  GNP_TRY_CUDA(cudaMemcpy(M->w_best, host_blob, sizeof(float) * cnt, cudaMemcpyHostToDevice));
+  train_reset(M->train);
+  return GNP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Host-side objects and the launchers that one translation unit exposes to another.
+#pragma once
+
+#include "common.cuh"
+
+namespace gnp {
+
+// Weight views inside the flat blob (float32, layout in include/gnp.h).
+constexpr int D = GNP_D;
+constexpr int HID = GNP_MLP_HIDDEN;
+constexpr int ENC_W1 = 0, ENC_B1 = 32, ENC_W2 = 64, ENC_B2 = 64 + 512;
+constexpr int ENC_COUNT = 592;
+constexpr int LAYER_COUNT = 512;
+constexpr int DEC_COUNT = 577;
+inline int layer_off(int l) { return ENC_COUNT + l * LAYER_COUNT; }
+inline int dec_off(int L) { return ENC_COUNT + L * LAYER_COUNT; }
+inline int weight_count(int L) { return ENC_COUNT + L * LAYER_COUNT + DEC_COUNT; }
+
+// Kernel-parameter copies of the weights: passed by value (__grid_constant__), so the
+// epilogues read them as uniform constant-bank operands.
+struct EncW { float W1[32]; float b1[32]; float W2[512]; float b2[16]; };
+struct LayerW { float U[256]; float W[256]; };
+struct DecW { float W1[512]; float b1[32]; float W2[32]; float b2; };
+
+// Indexed vector inside a basis: base + (*jptr + off) * stride (jptr may be null).
+struct ColPtr {
+  void* base;
+  size_t stride;
+  const int* jptr;
+  int off;
+};
+
+struct TrainState;  // train.cu
+struct Server;      // serve.cu
+
+// CSC (transpose) of a matrix, built on the device once (train and gamma use it).
+int mat_build_csc(gnp_mat* A, cudaStream_t st);
+
+// y = A x (float64 values), x in float64 or float32 (xf).  Tile SpMV kernel.
+int spmv_launch(const gnp_mat* A, const double* x, const float* xf, double* y, cudaStream_t st);
+
+}  // namespace gnp
+
+struct gnp_model {
+  gnp_mat* A = nullptr;
+  gnp_config cfg{};
+  int hprec = GNP_H_FP32;
+  double gamma = 0.0;
+  float* valhat = nullptr;        // [nnz] A/gamma in the CSR order
+  float* valhat_t = nullptr;      // [nnz] A/gamma in the CSC order (training)
+  std::vector<float> w_host;      // weights used to build kernel parameters
+  bool host_stale = false;        // device weights changed by training
+  float* w_dev = nullptr;         // [count] training copy
+  float* w_best = nullptr;        // [count] best-loss snapshot
+  void* H[2] = {nullptr, nullptr};  // apply ping-pong hidden blocks (n*16 float32 each)
+  double* tau = nullptr;          // device scalar ||v||
+  gnp::RedScratch red;            // apply reductions
+  gnp::TrainState* train = nullptr;
+  unsigned long long version = 1; // bumped whenever weights or hprec change
+};
+
+namespace gnp {
+
+// z = M(v) on `st`.  v: column of a basis (may be scaled in place first by 1/(*vscale)
+// when vscale is non-null: the FGMRES step normalises v_{j} inside the same pass).
+// ctl (may be null): device {j, active}; when active == 0 every kernel returns at once.
+// z: float32 output column; trace: optional float32 [(L+1)*n*16].
+// ev (may be null): 2*L events; ev[2l] / ev[2l+1] are recorded on `st` just before /
+// after the launch of layer l's Res-GCONV kernel (the timing of the hot kernel).
+int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
+                 const int* ctl, cudaStream_t st, cudaEvent_t* ev = nullptr);
+
+// Make the host copy of the weights current (after training).
+int model_sync_host(gnp_model* M);
+// Everything apply_launch needs that is not a stream operation (host weights, kernel
+// attributes); call before capturing apply_launch into a CUDA graph.
+int apply_prepare(gnp_model* M);
+unsigned long long model_version(const gnp_model* M);
+int gamma_launch(gnp_mat* A, double* gamma_dev, cudaStream_t st);
+void solver_free(Solver* s);
+void train_reset(TrainState* t);
+void train_free(TrainState* t);
+
+}  // namespace gnp

@@ -1,0 +1,747 @@
+// Restarted flexible GMRES with a nonlinear right preconditioner (Sec. 2.1, Eq. 1,
+// Algorithm 1), float64 throughout except the preconditioner output z_j (float32).
+//
+// One Arnoldi step j (all on the device, no host round trip):
+//   [M]    z_j = M(v_j): k_vnorm first turns the stored w into v_j = w / h_{j,j-1}
+//          (or r / beta), then the GNP kernels write Z[:, j].  For M = I, k_vscale
+//          only normalises and z_j = v_j.
+//   k_spmv_tile   w = A z_j (nnz-balanced tile gather, float64 values).
+//   k_cgs<1>      h1 = V_j^T w and ||w||^2.
+//   k_cgs<2>      w1 = w - V_j h1 (stored in place), h2 = V_j^T w1.
+//   k_cgs<3>      w2 = w1 - V_j h2 -> V[:, j+1] (not yet normalised), ||w2||; its last
+//                 block forms column j of H_bar (h1 + h2, ||w2||), applies the previous
+//                 Givens rotations and the new one, updates g and the residual estimate
+//                 |g_{j+1}| (Sec. 4), and decides whether the cycle continues.
+// Cycle end: k_xupdate (y = R^{-1} g by back substitution, x += Z y) and k_residual
+// (r = b - A x, beta = ||r||, which restarts the cycle).  Every kernel reads the step
+// index j and an `active` flag from device memory, so one captured CUDA graph replays a
+// whole restart cycle; steps after an early exit return at once.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace gnp {
+
+// ---------------------------------------------------------------- device state
+
+enum : int {
+  FL_EST_CONV = 1,
+  FL_BREAKDOWN = 2,
+  FL_DROPPED = 4,
+  FL_NAN = 8,
+  FL_MAXIT = 16,
+  FL_FULL = 32,
+};
+
+struct DevState {
+  int j;        // current Arnoldi step within the cycle   (ctl[0])
+  int active;   // 1 while the cycle runs                    (ctl[1])
+  int iters;    // Arnoldi steps so far
+  int maxiters;
+  int m;        // restart length
+  int jj;       // columns used by the cycle-end update
+  int flags;
+  int last_flags;  // flags of the cycle that just ended (kept by k_residual)
+  int last_jj;     // columns that cycle used
+  int pad;
+  double bnorm, tol, rtol, beta, vscale, wnorm0, hn, res_est;
+};
+
+constexpr double BREAKDOWN_REL = 1e-14;
+
+struct Solver {
+  int n = 0, m_cap = 0, maxit_cap = -1;
+  double* V = nullptr;   // [n*(m+1)] column-major basis
+  float* Z = nullptr;    // [n*m] preconditioned directions
+  double* w = nullptr;   // [n]
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;  // pinned mirror
+  double* H = nullptr;   // [(m+1)*m] unrotated H_bar of the current cycle
+  double* R = nullptr;   // [(m+1)*m] rotated (upper triangular part used)
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* g = nullptr;   // [m+1]
+  double* h1 = nullptr;  // [m+2]
+  double* h2 = nullptr;  // [m+2]
+  double* hist = nullptr;  // [maxiters+1]
+  RedScratch red;
+  // captured restart cycle
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_model = nullptr;
+  unsigned long long g_version = 0;
+  int g_m = 0, g_hprec = -1;
+  const double* g_b = nullptr;
+  double* g_x = nullptr;
+  cudaStream_t g_stream = nullptr;
+  cudaStream_t own = nullptr;  // used when the caller passes the legacy default stream
+  // optional timing of the Res-GCONV launches: events[(j*L + l)*2 + {0,1}]
+  std::vector<cudaEvent_t> events;
+  int ev_L = 0, ev_m = 0;
+  bool g_prof = false;
+};
+
+static bool g_profile_gconv = false;
+
+static int ensure_events(Solver* S, int m, int L) {
+  if ((int)S->events.size() >= 2 * m * L && S->ev_L == L) return GNP_OK;
+  for (cudaEvent_t e : S->events) cudaEventDestroy(e);
+  S->events.assign((size_t)2 * m * L, nullptr);
+  for (auto& e : S->events) GNP_TRY_CUDA(cudaEventCreate(&e));
+  S->ev_L = L;
+  S->ev_m = m;
+  return GNP_OK;
+}
+
+void solver_free(Solver* s) {
+  if (!s) return;
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->own) cudaStreamDestroy(s->own);
+  for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  dev_free(s->V);
+  dev_free(s->Z);
+  dev_free(s->w);
+  dev_free(s->st);
+  if (s->st_host) cudaFreeHost(s->st_host);
+  dev_free(s->H);
+  dev_free(s->R);
+  dev_free(s->cs);
+  dev_free(s->sn);
+  dev_free(s->g);
+  dev_free(s->h1);
+  dev_free(s->h2);
+  dev_free(s->hist);
+  red_free(s->red);
+  delete s;
+}
+
+static int solver_ensure(gnp_mat* A, int m, int maxiters) {
+  Solver* s = A->solver;
+  const int n = A->n;
+  if (s && s->m_cap >= m && s->maxit_cap >= maxiters) return GNP_OK;
+  int m_new = std::max(m, s ? s->m_cap : 0);
+  int it_new = std::max(maxiters, s ? s->maxit_cap : 0);
+  solver_free(s);
+  A->solver = nullptr;
+  s = new Solver();
+  s->n = n;
+  int e = GNP_OK;
+  do {
+    if ((e = dev_alloc(&s->V, (size_t)n * (m_new + 1))) != GNP_OK) break;
+    if ((e = dev_alloc(&s->Z, (size_t)n * m_new)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->w, (size_t)n)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->st, 1)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->H, (size_t)(m_new + 1) * m_new)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->R, (size_t)(m_new + 1) * m_new)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->cs, (size_t)m_new)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->sn, (size_t)m_new)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->g, (size_t)m_new + 1)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->h1, (size_t)m_new + 2)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->h2, (size_t)m_new + 2)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->hist, (size_t)it_new + 1)) != GNP_OK) break;
+    const int maxb = std::max(red_blocks(n), (n + TILE - 1) / TILE);
+    if ((e = red_alloc(s->red, maxb, m_new + 2)) != GNP_OK) break;
+    if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("cudaStreamCreate failed");
+      e = GNP_ERR_CUDA;
+      break;
+    }
+    if (cudaMallocHost(reinterpret_cast<void**>(&s->st_host), sizeof(DevState)) != cudaSuccess) {
+      set_error("cudaMallocHost failed");
+      e = GNP_ERR_OOM;
+      break;
+    }
+  } while (0);
+  if (e != GNP_OK) {
+    solver_free(s);
+    return e;
+  }
+  s->m_cap = m_new;
+  s->maxit_cap = it_new;
+  A->solver = s;
+  return GNP_OK;
+}
+
+// ---------------------------------------------------------------- SpMV traits
+
+template <class XT>
+struct TrSpmv {
+  static constexpr int G = 1, NV = 1, STRIDE = 1;
+  using acc = double;
+  using val_t = double;
+  using x_t = XT;
+  __device__ __forceinline__ static void load(const XT* X, int c, int, double (&h)[1]) {
+    h[0] = (double)__ldg(X + c);
+  }
+};
+
+__device__ __forceinline__ const void* colptr_c(const ColPtr& p) {
+  int j = p.jptr ? *p.jptr : 0;
+  return static_cast<const char*>(p.base) + (size_t)(j + p.off) * p.stride;
+}
+
+// y = A x.  x: float64 or float32 column (ColPtr); y float64.
+template <class XT>
+__global__ void __launch_bounds__(TILE)
+k_spmv_tile(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+            ColPtr xp, double* __restrict__ y, int n, const int* __restrict__ ctl) {
+  if (ctl && !ctl[1]) return;
+  using TR = TrSpmv<XT>;
+  __shared__ TileSmem<TR> sm;
+  const XT* x = static_cast<const XT*>(colptr_c(xp));
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  tile_load_rp<TR>(sm, rp, r0, rows);
+  __syncthreads();
+  tile_gather<TR>(sm, rows, col, val, x);
+  __syncthreads();
+  if (threadIdx.x < rows) {
+    double s[1];
+    tile_row_sum<TR, 1>(sm, threadIdx.x, 0, s);
+    y[r0 + threadIdx.x] = s[0];
+  }
+}
+
+// r = b - A x -> V[:, 0], beta = ||r||; the last block restarts the cycle state.
+__global__ void __launch_bounds__(TILE)
+k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+           const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ V0, int n,
+           DevState* st, double* __restrict__ g, double* __restrict__ hist,
+           double* __restrict__ partials, unsigned* counter) {
+  using TR = TrSpmv<double>;
+  __shared__ TileSmem<TR> sm;
+  __shared__ double sh[32];
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  tile_load_rp<TR>(sm, rp, r0, rows);
+  __syncthreads();
+  tile_gather<TR>(sm, rows, col, val, x);
+  __syncthreads();
+  double acc = 0.0;
+  if (threadIdx.x < rows) {
+    double s[1];
+    tile_row_sum<TR, 1>(sm, threadIdx.x, 0, s);
+    double r = b[r0 + threadIdx.x] - s[0];
+    V0[r0 + threadIdx.x] = r;
+    acc = r * r;
+  }
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block_arrive(counter)) {
+    __shared__ double tot[1];
+    reduce_partials(partials, gridDim.x, 1, tot);
+    if (threadIdx.x == 0) {
+      const double beta = sqrt(tot[0]);
+      st->beta = beta;
+      if (st->iters == 0) hist[0] = beta / st->bnorm;
+      st->last_flags = st->flags;
+      st->last_jj = st->jj;
+      st->j = 0;
+      st->jj = 0;
+      st->flags = 0;
+      st->vscale = beta;
+      g[0] = beta;
+      st->active = (isfinite(beta) && beta > st->tol && st->iters < st->maxiters) ? 1 : 0;
+      *counter = 0;
+    }
+  }
+}
+
+// ||b|| and tol = rtol ||b||.
+__global__ void __launch_bounds__(RED_THREADS)
+k_bnorm(const double* __restrict__ b, int n, DevState* st, double* __restrict__ partials, unsigned* counter) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += b[i] * b[i];
+  double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block_arrive(counter)) {
+    __shared__ double tot[1];
+    reduce_partials(partials, gridDim.x, 1, tot);
+    if (threadIdx.x == 0) {
+      st->bnorm = sqrt(tot[0]);
+      st->tol = st->rtol * st->bnorm;
+      *counter = 0;
+    }
+  }
+}
+
+// v_j <- v_j / vscale (M = identity: the normalisation that k_vnorm does for the GNP).
+__global__ void __launch_bounds__(RED_THREADS)
+k_vscale(double* __restrict__ V, int n, const DevState* st) {
+  if (!st->active) return;
+  double* v = V + (size_t)st->j * n;
+  const double s = st->vscale;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = v[i] / s;
+}
+
+// ---------------------------------------------------------------- CGS2 passes
+
+constexpr int KC = 8;  // basis columns per register chunk
+
+// Sum KC per-thread values over the block; thread kc < KC writes partial kc.
+__device__ __forceinline__ void block_sum_store(double (&a)[KC], double (*sh)[32], double* dst, int kvalid) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) {
+    double v = warp_sum(a[kc]);
+    if (lane == 0) sh[kc][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kvalid) {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += sh[threadIdx.x][k];
+    dst[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(RED_THREADS)
+k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, double* __restrict__ h1,
+      double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
+      double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
+      double* __restrict__ partials, unsigned* counter) {
+  if (!st->active) return;
+  __shared__ double shh[GNP_MAX_RESTART + 2];
+  __shared__ double shred[KC][32];
+  __shared__ double shtot[GNP_MAX_RESTART + 2];
+  const int j = st->j;
+  const size_t ld = (size_t)n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstride = gridDim.x * blockDim.x;
+  if (PASS >= 2) {
+    const double* hp = (PASS == 2) ? h1 : h2;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) shh[k] = hp[k];
+    __syncthreads();
+  }
+  if (PASS == 3) {
+    // w2 = w1 - V h2 -> V[:, j+1]; ||w2||^2
+    double acc = 0.0;
+    double* vout = V + (size_t)(j + 1) * ld;
+    for (int i = gtid; i < n; i += gstride) {
+      double x = w[i];
+      for (int k = 0; k <= j; ++k) x -= V[k * ld + i] * shh[k];
+      vout[i] = x;
+      acc += x * x;
+    }
+    double t = block_sum(acc, shred[0]);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  } else {
+    if (PASS == 2) {
+      for (int i = gtid; i < n; i += gstride) {
+        double x = w[i];
+        for (int k = 0; k <= j; ++k) x -= V[k * ld + i] * shh[k];
+        w[i] = x;
+      }
+    }
+    const int K = (PASS == 1) ? j + 2 : j + 1;  // pass 1 also ||w||^2 as entry j+1
+    for (int k0 = 0; k0 < K; k0 += KC) {
+      double acc[KC];
+#pragma unroll
+      for (int kc = 0; kc < KC; ++kc) acc[kc] = 0.0;
+      for (int i = gtid; i < n; i += gstride) {
+        const double y = w[i];
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc) {
+          const int k = k0 + kc;
+          if (k < K) {
+            const double vk = (PASS == 1 && k == j + 1) ? y : V[k * ld + i];
+            acc[kc] += vk * y;
+          }
+        }
+      }
+      block_sum_store(acc, shred, partials + (size_t)blockIdx.x * K + k0, min(KC, K - k0));
+    }
+  }
+  if (!last_block_arrive(counter)) return;
+  const int K = (PASS == 1) ? j + 2 : (PASS == 2 ? j + 1 : 1);
+  reduce_partials(partials, gridDim.x, K, shtot);
+  if (threadIdx.x != 0) return;
+  *counter = 0;
+  if (PASS == 1) {
+    for (int k = 0; k <= j; ++k) h1[k] = shtot[k];
+    st->wnorm0 = sqrt(shtot[j + 1]);
+    return;
+  }
+  if (PASS == 2) {
+    for (int k = 0; k <= j; ++k) h2[k] = shtot[k];
+    return;
+  }
+  // PASS 3: column j of H_bar, Givens QR update (rotation convention: rho = hypot(a,b),
+  // c = a/rho, s = b/rho; rho = 0 gives c = 1, s = 0), residual estimate |g_{j+1}|.
+  const int m = st->m;
+  const int ldh = m + 1;
+  const double hn = sqrt(shtot[0]);
+  st->hn = hn;
+  double col[GNP_MAX_RESTART + 2];
+  bool finite = isfinite(hn);
+  for (int i = 0; i <= j; ++i) {
+    col[i] = h1[i] + h2[i];
+    H[(size_t)j * ldh + i] = col[i];
+  }
+  col[j + 1] = hn;
+  H[(size_t)j * ldh + j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  for (int i = 0; i <= j + 1; ++i) finite = finite && isfinite(col[i]);
+  const double a = col[j], b = col[j + 1];
+  const double rho = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (rho != 0.0) {
+    c = a / rho;
+    s = b / rho;
+  }
+  const int iters = st->iters + 1;
+  st->iters = iters;
+  const double wn0 = st->wnorm0;
+  int flags = 0;
+  int jj;
+  if (!finite || !isfinite(rho)) {
+    flags |= FL_NAN;
+    jj = j;
+  } else if (rho <= BREAKDOWN_REL * wn0) {
+    hist[iters] = fabs(g[j]) / st->bnorm;
+    flags |= FL_DROPPED;
+    jj = j;
+  } else {
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = rho;
+    col[j + 1] = 0.0;
+    for (int i = 0; i <= j + 1; ++i) R[(size_t)j * ldh + i] = col[i];
+    const double gj = g[j];
+    g[j + 1] = -s * gj;
+    g[j] = c * gj;
+    jj = j + 1;
+    const double res = fabs(g[j + 1]);
+    st->res_est = res;
+    hist[iters] = res / st->bnorm;
+    if (hn <= BREAKDOWN_REL * wn0) flags |= FL_BREAKDOWN;
+    else if (res <= st->tol) flags |= FL_EST_CONV;
+    else if (iters >= st->maxiters) flags |= FL_MAXIT;
+    else if (j + 1 >= m) flags |= FL_FULL;
+  }
+  st->jj = jj;
+  st->flags = flags;
+  if (flags) {
+    st->active = 0;
+  } else {
+    st->j = j + 1;
+    st->vscale = hn;
+  }
+}
+
+// y = R^{-1} g (back substitution, redundantly in every block), x += Z[:, :jj] y.
+template <class ZT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevState* st,
+          const double* __restrict__ R, const double* __restrict__ g) {
+  __shared__ double y[GNP_MAX_RESTART];
+  const int jj = st->jj;
+  if (jj == 0) return;
+  const int ldh = st->m + 1;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = jj - 1; i >= 0; --i) {
+      double part = 0.0;
+      for (int k = i + 1 + lane; k < jj; k += 32) part += R[(size_t)k * ldh + i] * y[k];
+      part = warp_sum(part);
+      if (lane == 0) y[i] = (g[i] - part) / R[(size_t)i * ldh + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const size_t ld = (size_t)n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = x[i];
+    for (int k = 0; k < jj; ++k) acc += (double)Z[k * ld + i] * y[k];
+    x[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+int spmv_launch(const gnp_mat* A, const double* x, const float* xf, double* y, cudaStream_t st) {
+  const int nt = (A->n + TILE - 1) / TILE;
+  if (xf) {
+    ColPtr xp{const_cast<float*>(xf), 0, nullptr, 0};
+    k_spmv_tile<float><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, xp, y, A->n, nullptr);
+  } else {
+    ColPtr xp{const_cast<double*>(x), 0, nullptr, 0};
+    k_spmv_tile<double><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, xp, y, A->n, nullptr);
+  }
+  return check_launch("k_spmv_tile");
+}
+
+// Enqueue one restart cycle: m Arnoldi steps, x update, residual.
+static int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, double* x,
+                        cudaStream_t st, bool prof) {
+  const int n = A->n;
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  const int* ctl = reinterpret_cast<const int*>(S->st);
+  const int* jptr = ctl;
+  for (int j = 0; j < m; ++j) {
+    if (M) {
+      ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
+      ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
+      cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
+      GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev));
+      k_spmv_tile<float><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, n, ctl);
+    } else {
+      k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
+      ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
+      k_spmv_tile<double><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, n, ctl);
+    }
+    k_cgs<1><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->red.partials, S->red.counter);
+    k_cgs<2><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->red.partials, S->red.counter);
+    k_cgs<3><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->red.partials, S->red.counter);
+  }
+  if (M)
+    k_xupdate<float><<<nb, RED_THREADS, 0, st>>>(S->Z, x, n, S->st, S->R, S->g);
+  else
+    k_xupdate<double><<<nb, RED_THREADS, 0, st>>>(S->V, x, n, S->st, S->R, S->g);
+  k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
+                                  S->red.partials, S->red.counter);
+  return check_launch("fgmres cycle");
+}
+
+static int read_state(Solver* S, cudaStream_t st) {
+  GNP_TRY_CUDA(cudaMemcpyAsync(S->st_host, S->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  return GNP_OK;
+}
+
+// The unpreconditioned m-step Arnoldi process (Eq. 4) from v1 (not necessarily
+// normalised), CGS2 as in the solver: V_out receives the k+1 basis vectors (k <= m, k
+// < m only at a breakdown), Hbar_host the (m+1) x m column-major H_bar (first k
+// columns valid).  Runs on `st` and synchronises it.
+int arnoldi_basis(gnp_mat* A, const double* v1, int m, double* V_out, double* Hbar_host, int* k_out,
+                  cudaStream_t st) {
+  GNP_TRY(solver_ensure(A, m, m));
+  Solver* S = A->solver;
+  if (st == nullptr || st == cudaStreamLegacy) {
+    GNP_TRY_CUDA(cudaStreamSynchronize(st));
+    st = S->own;
+  }
+  const int n = A->n;
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  DevState init{};
+  init.maxiters = m;
+  init.m = m;
+  init.rtol = 0.0;
+  memcpy(S->st_host, &init, sizeof(DevState));
+  GNP_TRY_CUDA(cudaMemcpyAsync(S->st, S->st_host, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  GNP_TRY_CUDA(cudaMemsetAsync(S->w, 0, sizeof(double) * n, st));  // x0 = 0
+  k_bnorm<<<nb, RED_THREADS, 0, st>>>(v1, n, S->st, S->red.partials, S->red.counter);
+  k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, S->w, v1, S->V, n, S->st, S->g, S->hist,
+                                  S->red.partials, S->red.counter);
+  const int* jptr = reinterpret_cast<const int*>(S->st);
+  for (int j = 0; j < m; ++j) {
+    k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
+    ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
+    k_spmv_tile<double><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, n, jptr);
+    k_cgs<1><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->red.partials, S->red.counter);
+    k_cgs<2><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->red.partials, S->red.counter);
+    k_cgs<3><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->red.partials, S->red.counter);
+  }
+  GNP_TRY(check_launch("arnoldi"));
+  GNP_TRY(read_state(S, st));
+  const DevState hs = *S->st_host;
+  if (hs.flags & FL_NAN) {
+    set_error("arnoldi: NaN in the basis");
+    return GNP_ERR_NAN;
+  }
+  int k = hs.jj;
+  // a breakdown keeps column j (jj = j + 1); the basis has k + 1 vectors unless the
+  // last one was never formed
+  GNP_TRY_CUDA(cudaMemcpyAsync(V_out, S->V, sizeof(double) * (size_t)n * (k + 1), cudaMemcpyDeviceToDevice, st));
+  GNP_TRY_CUDA(cudaMemcpyAsync(Hbar_host, S->H, sizeof(double) * (size_t)(m + 1) * m, cudaMemcpyDeviceToHost, st));
+  GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  *k_out = k;
+  return GNP_OK;
+}
+
+static bool graphs_enabled() {
+  const char* e = getenv("GNP_NO_GRAPH");
+  return !(e && e[0] == '1');
+}
+
+}  // namespace gnp
+
+using namespace gnp;
+
+extern "C" int gnp_profile_gconv(int on) {
+  gnp::g_profile_gconv = on != 0;
+  return GNP_OK;
+}
+
+extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M, int restart,
+                            double rtol, int maxiters, gnp_solve_info* info, void* stream) {
+  GNP_REQUIRE(A && b && x, "fgmres_solve: null argument");
+  GNP_REQUIRE(restart >= 1 && restart <= GNP_MAX_RESTART, "fgmres_solve: restart %d out of [1, %d]",
+              restart, GNP_MAX_RESTART);
+  GNP_REQUIRE(maxiters >= 0, "fgmres_solve: maxiters < 0");
+  GNP_REQUIRE(rtol >= 0.0, "fgmres_solve: rtol < 0");
+  GNP_REQUIRE(!M || M->A == A, "fgmres_solve: the preconditioner was built for another matrix");
+  cudaStream_t st = as_stream(stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  GNP_TRY(solver_ensure(A, restart, maxiters));
+  Solver* S = A->solver;
+  if (st == nullptr || st == cudaStreamLegacy) {
+    // graphs cannot be captured on the legacy default stream: order the caller's
+    // earlier work, then run the (synchronous) solve on the solver's own stream
+    GNP_TRY_CUDA(cudaStreamSynchronize(st));
+    st = S->own;
+  }
+  if (M) GNP_TRY(apply_prepare(M));
+  const int n = A->n;
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  DevState init{};
+  init.maxiters = maxiters;
+  init.m = restart;
+  init.rtol = rtol;
+  memcpy(S->st_host, &init, sizeof(DevState));
+  GNP_TRY_CUDA(cudaMemcpyAsync(S->st, S->st_host, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  k_bnorm<<<nb, RED_THREADS, 0, st>>>(b, n, S->st, S->red.partials, S->red.counter);
+  k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
+                                  S->red.partials, S->red.counter);
+  GNP_TRY(check_launch("fgmres init"));
+  GNP_TRY(read_state(S, st));
+  int status = GNP_OK;
+  int restarts = 0;
+  const bool prof = g_profile_gconv && M != nullptr && M->cfg.L > 0;
+  double gconv_ms = 0.0;
+  long long gconv_launches = 0;
+  int cycles = 0;
+  int stagn = 0, mism = 0;
+  DevState hs = *S->st_host;
+  if (hs.bnorm == 0.0) {
+    GNP_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    hs.beta = 0.0;
+  } else if (!std::isfinite(hs.beta) || !std::isfinite(hs.bnorm)) {
+    status = GNP_ERR_NAN;
+  } else if (hs.beta > hs.tol) {
+    if (maxiters == 0) status = GNP_ERR_NOT_CONVERGED;
+    const bool use_graph = graphs_enabled();
+    if (prof) GNP_TRY(ensure_events(S, restart, M->cfg.L));
+    while (status == GNP_OK && hs.iters < maxiters) {
+      const double beta_prev = hs.beta;
+      if (use_graph) {
+        const unsigned long long ver = M ? model_version(M) : 0ull;
+        if (!S->gexec || S->g_model != M || S->g_version != ver || S->g_m != restart ||
+            S->g_hprec != (M ? M->hprec : -1) || S->g_b != b || S->g_x != x || S->g_stream != st ||
+            S->g_prof != prof) {
+          if (S->gexec) cudaGraphExecDestroy(S->gexec);
+          S->gexec = nullptr;
+          cudaGraph_t graph;
+          GNP_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+          int ls = launch_cycle(A, S, M, restart, b, x, st, prof);
+          cudaError_t ce = cudaStreamEndCapture(st, &graph);
+          if (ls != GNP_OK) return ls;
+          if (ce != cudaSuccess) {
+            set_error("fgmres: graph capture failed: %s", cudaGetErrorString(ce));
+            return GNP_ERR_CUDA;
+          }
+          ce = cudaGraphInstantiate(&S->gexec, graph, 0);
+          cudaGraphDestroy(graph);
+          if (ce != cudaSuccess) {
+            set_error("fgmres: graph instantiate failed: %s", cudaGetErrorString(ce));
+            S->gexec = nullptr;
+            return GNP_ERR_CUDA;
+          }
+          S->g_model = M;
+          S->g_version = ver;
+          S->g_m = restart;
+          S->g_hprec = M ? M->hprec : -1;
+          S->g_b = b;
+          S->g_x = x;
+          S->g_stream = st;
+          S->g_prof = prof;
+        }
+        GNP_TRY_CUDA(cudaGraphLaunch(S->gexec, st));
+      } else {
+        GNP_TRY(launch_cycle(A, S, M, restart, b, x, st, prof));
+      }
+      const int iters_before = hs.iters;
+      ++cycles;
+      GNP_TRY(read_state(S, st));
+      hs = *S->st_host;
+      if (prof) {
+        const int steps = hs.iters - iters_before;  // Arnoldi steps this cycle ran
+        for (int j = 0; j < steps; ++j)
+          for (int l = 0; l < M->cfg.L; ++l) {
+            float ms = 0.f;
+            const size_t e = ((size_t)j * M->cfg.L + l) * 2;
+            GNP_TRY_CUDA(cudaEventElapsedTime(&ms, S->events[e], S->events[e + 1]));
+            gconv_ms += ms;
+            ++gconv_launches;
+          }
+      }
+      if ((hs.last_flags & FL_NAN) || !std::isfinite(hs.beta)) {
+        status = GNP_ERR_NAN;
+        break;
+      }
+      if (hs.beta <= hs.tol) break;
+      mism = (hs.last_flags & FL_EST_CONV) ? mism + 1 : 0;
+      stagn = (hs.beta >= beta_prev) ? stagn + 1 : 0;
+      if (mism >= 3) {
+        status = GNP_ERR_RESIDUAL_MISMATCH;
+        break;
+      }
+      if (stagn >= 2) {
+        status = GNP_ERR_STAGNATION;
+        break;
+      }
+      ++restarts;
+      if (hs.iters >= maxiters) {
+        status = GNP_ERR_NOT_CONVERGED;
+        break;
+      }
+    }
+  }
+  GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    info->iters = hs.iters;
+    info->restarts = restarts;
+    info->status = status;
+    info->seconds = secs;
+    info->gconv_ms = gconv_ms;
+    info->gconv_launches = (int)gconv_launches;
+    info->cycles = cycles;
+    const double bn = hs.bnorm > 0.0 ? hs.bnorm : 1.0;
+    info->rel_res_true = hs.bnorm > 0.0 ? hs.beta / bn : 0.0;
+    info->rel_res_est = hs.iters > 0 ? hs.res_est / bn : info->rel_res_true;
+    if (info->res_history) {
+      const int cnt = hs.bnorm > 0.0 ? hs.iters + 1 : 1;
+      if (hs.bnorm > 0.0) {
+        GNP_TRY_CUDA(cudaMemcpy(info->res_history, S->hist, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+      } else {
+        info->res_history[0] = 0.0;
+      }
+      info->res_history_len = cnt;
+    }
+    if (info->hessenberg) {
+      const int cols = hs.iters > 0 ? hs.last_jj : 0;
+      GNP_TRY_CUDA(cudaMemcpy(info->hessenberg, S->H, sizeof(double) * (size_t)(restart + 1) * restart,
+                              cudaMemcpyDeviceToHost));
+      info->hessenberg_cols = cols;
+    }
+  }
+  return status;
+}

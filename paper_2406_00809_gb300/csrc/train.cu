@@ -1,0 +1,1129 @@
+// GNP training (Sec. 2.2, Sec. 3 "Hyperparameters"): batched forward with saved
+// activations, l1 residual loss, hand-written backward, Adam, best-loss snapshot, and
+// the training-pair sampler (half Eq. 5 Arnoldi samples, half N(0, I)).
+//
+// Batched layout: B right-hand sides node-major, element (i, k) at i*B + k; hidden
+// blocks (i, k, c) at (i*B + k)*16 + c, so one CSR gather of node j moves the whole
+// contiguous B x 16 block.  R = n*B "rows" for the row-wise kernels.
+//
+// Backward (App. E: the same products with A_hat and with tall n-row matrices):
+//   decoder:  do = dz * tau_k/sqrt(n); dc1 = (do w2^T) * 1[c1 > 0]; dH^L = dc1 D1^T
+//   layer l:  Gp = G * 1[pre > 0]; Y = Gp W^T; dX = (Gp U^T | G) + A_hat^T Y, the last
+//             product a gather through the canonical CSC of A_hat;
+//             dU = sum X^T Gp, dW = sum (A_hat X)^T Gp
+//   encoder:  da1 = (dH^0 W2^T) * 1[a1 > 0]; dW2 = sum r1^T dH^0, dW1 = sum u da1
+// Weight gradients are column-sum reductions over the R rows (k_wgrad): fixed row
+// chunks per block in float32, then a fixed-order float64 sum over blocks.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace gnp {
+
+int arnoldi_basis(gnp_mat* A, const double* v1, int m, double* V_out, double* Hbar_host,
+                  int* k_out, cudaStream_t st);  // krylov.cu
+
+struct TrainState {
+  int n = 0, B = 0, L = 0;
+  long long R = 0;
+  // forward activations
+  float* u = nullptr;      // [R]
+  double* tau = nullptr;   // [B]
+  float* Hs = nullptr;     // [(L+1) * R * 16]
+  float* AGG = nullptr;    // [L * R * 16]
+  float* z = nullptr;      // [R]
+  // backward scratch
+  float* g16a = nullptr;   // [R*16]
+  float* g16b = nullptr;   // [R*16]
+  float* y16 = nullptr;    // [R*16]
+  float* gp16 = nullptr;   // [R*16]
+  float* s32a = nullptr;   // [R*32]
+  float* s32b = nullptr;   // [R*32]
+  float* r1 = nullptr;     // [R]   (do)
+  float* grad = nullptr;   // [count]
+  float* partials = nullptr;  // wgrad partials
+  int part_cap = 0;
+  RedScratch red;          // column norms / loss
+  // batch buffers
+  float* xb = nullptr;     // [R]
+  float* bb = nullptr;     // [R]
+  float* rr = nullptr;     // [R]
+  float* dz = nullptr;     // [R]
+  // optimiser
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  float* loss = nullptr;       // device scalar: last loss
+  float* best_loss = nullptr;  // device scalar
+  int* adam_t = nullptr;       // device step counter
+  int step = 0;                // host step counter of gnp_train_step
+  // sampler
+  bool sampler_ready = false;
+  int mA = 0;                  // Arnoldi columns actually used
+  double* V = nullptr;         // [n*(mA+1)]
+  double* Q = nullptr;         // [mA*mA] Z S^-1, row-major
+  double* C = nullptr;         // [mA*B]
+  double* Hbar = nullptr;      // device copy of H_bar / gamma, column-major (mA+1) x mA
+};
+
+void train_free(TrainState* t) {
+  if (!t) return;
+  float* fs[] = {t->u, t->Hs, t->AGG, t->z, t->g16a, t->g16b, t->y16, t->gp16, t->s32a, t->s32b,
+                 t->r1, t->grad, t->partials, t->xb, t->bb, t->rr, t->dz, t->adam_m, t->adam_v, t->loss,
+                 t->best_loss};
+  for (float* p : fs) if (p) cudaFree(p);
+  if (t->tau) cudaFree(t->tau);
+  if (t->adam_t) cudaFree(t->adam_t);
+  if (t->V) cudaFree(t->V);
+  if (t->Q) cudaFree(t->Q);
+  if (t->C) cudaFree(t->C);
+  if (t->Hbar) cudaFree(t->Hbar);
+  red_free(t->red);
+  delete t;
+}
+
+void train_reset(TrainState* t) {
+  if (!t) return;
+  const int cnt = weight_count(t->L);
+  cudaMemset(t->adam_m, 0, sizeof(float) * cnt);
+  cudaMemset(t->adam_v, 0, sizeof(float) * cnt);
+  cudaMemset(t->adam_t, 0, sizeof(int));
+  const float inf = INFINITY;
+  cudaMemcpy(t->best_loss, &inf, sizeof(float), cudaMemcpyHostToDevice);
+  t->step = 0;
+}
+
+__global__ void k_gather_vals(const float* __restrict__ v, const int* __restrict__ perm, long long nnz,
+                              float* __restrict__ out);
+
+static int train_ensure(gnp_model* M, int B) {
+  TrainState* t = M->train;
+  if (t && t->B == B) return GNP_OK;
+  GNP_REQUIRE(B >= 4 && B <= GNP_MAX_BATCH && (B & (B - 1)) == 0,
+              "training batch %d must be a power of two in [4, %d]", B, GNP_MAX_BATCH);
+  GNP_TRY(mat_build_csc(M->A, 0));
+  if (!M->valhat_t) {
+    GNP_TRY(dev_alloc(&M->valhat_t, (size_t)std::max<long long>(M->A->nnz, 1)));
+    if (M->A->nnz > 0) {
+      k_gather_vals<<<4 * NUM_SMS_GB300, 256>>>(M->valhat, M->A->csc.perm, M->A->nnz, M->valhat_t);
+      GNP_TRY(check_launch("k_gather_vals"));
+      GNP_TRY_CUDA(cudaDeviceSynchronize());
+    }
+  }
+  bool keep_opt = t != nullptr;
+  TrainState* nt = new TrainState();
+  const int n = M->A->n, L = M->cfg.L;
+  const long long R = (long long)n * B;
+  nt->n = n;
+  nt->B = B;
+  nt->L = L;
+  nt->R = R;
+  const int cnt = weight_count(L);
+  int s = GNP_OK;
+  do {
+    if ((s = dev_alloc(&nt->u, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->tau, (size_t)B)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->Hs, (size_t)(L + 1) * R * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->AGG, (size_t)std::max(L, 1) * R * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->z, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->g16a, (size_t)R * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->g16b, (size_t)R * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->y16, (size_t)R * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->gp16, (size_t)R * 16)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->s32a, (size_t)R * 32)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->s32b, (size_t)R * 32)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->r1, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->grad, (size_t)cnt)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->xb, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->bb, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->rr, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->dz, (size_t)R)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->adam_m, (size_t)cnt)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->adam_v, (size_t)cnt)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->loss, 1)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->best_loss, 1)) != GNP_OK) break;
+    if ((s = dev_alloc(&nt->adam_t, 1)) != GNP_OK) break;
+    if ((s = red_alloc(nt->red, 4 * NUM_SMS_GB300, GNP_MAX_BATCH)) != GNP_OK) break;
+  } while (0);
+  if (s != GNP_OK) {
+    train_free(nt);
+    return s;
+  }
+  if (keep_opt) {
+    // a new batch size keeps the optimiser state and the sampler
+    cudaMemcpy(nt->adam_m, t->adam_m, sizeof(float) * cnt, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(nt->adam_v, t->adam_v, sizeof(float) * cnt, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(nt->adam_t, t->adam_t, sizeof(int), cudaMemcpyDeviceToDevice);
+    cudaMemcpy(nt->best_loss, t->best_loss, sizeof(float), cudaMemcpyDeviceToDevice);
+    nt->step = t->step;
+    std::swap(nt->V, t->V);
+    std::swap(nt->Q, t->Q);
+    std::swap(nt->Hbar, t->Hbar);
+    nt->mA = t->mA;
+    nt->sampler_ready = t->sampler_ready;
+    train_free(t);
+  } else {
+    train_reset(nt);
+  }
+  M->train = nt;
+  return GNP_OK;
+}
+
+// ---------------------------------------------------------------- Philox / Box-Muller
+
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies with
+// M0 = 0xD2511F53 (on c0) and M1 = 0xCD9E8D57 (on c2), key bumped by (0x9E3779B9,
+// 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Uniform in (0,1) with at most 24 significant bits: ((r >> 9) + 0.5) * 2^-23.
+__device__ __forceinline__ float uniform24(uint32_t r) {
+  return ((float)(r >> 9) + 0.5f) * 0x1p-23f;
+}
+
+// Element e of stream (seed, step, stream): output e%4 of call e/4, Box-Muller pairs
+// (w0, w1) -> [rho cos, rho sin], (w2, w3) -> [rho cos, rho sin].
+__device__ __forceinline__ float philox_normal(unsigned long long e, unsigned long long seed,
+                                               uint32_t step, uint32_t stream) {
+  const unsigned long long idx = e >> 2;
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), step, stream),
+                                (uint32_t)seed, (uint32_t)(seed >> 32));
+  const int lane = (int)(e & 3);
+  const uint32_t ra = lane < 2 ? w.x : w.z;
+  const uint32_t rb = lane < 2 ? w.y : w.w;
+  const float rho = sqrtf(-2.0f * logf(uniform24(ra)));
+  float sn, cs;
+  sincospif(2.0f * uniform24(rb), &sn, &cs);
+  return (lane & 1) ? rho * sn : rho * cs;
+}
+
+constexpr uint32_t STREAM_X = 1, STREAM_EPS = 2, STREAM_V1 = 3;
+
+// ---------------------------------------------------------------- generic kernels
+
+// Y[i] = alpha * sum_e vals[e] X[idx[e]] + beta * Yadd[i], for node blocks of W4
+// float4 values (warp per node).  With (ptr, idx, vals) the CSR of A_hat this is
+// A_hat X; with the canonical CSC and the CSC-ordered values it is A_hat^T X.
+__global__ void __launch_bounds__(256)
+k_spmm_nodes(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ vals,
+             const float4* __restrict__ X, int n, int W4, float alpha, const float4* __restrict__ Yadd,
+             float beta, float4* __restrict__ Y) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = warp; i < n; i += nwarps) {
+    float4 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e0 = ptr[i], e1 = ptr[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int j = __ldg(idx + e);
+      const float a = __ldg(vals + e);
+      const float4* xj = X + (size_t)j * W4;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int f = lane + 32 * k;
+        if (f < W4) {
+          const float4 v = __ldg(xj + f);
+          acc[k].x = fmaf(a, v.x, acc[k].x);
+          acc[k].y = fmaf(a, v.y, acc[k].y);
+          acc[k].z = fmaf(a, v.z, acc[k].z);
+          acc[k].w = fmaf(a, v.w, acc[k].w);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int f = lane + 32 * k;
+      if (f < W4) {
+        float4 o = make_float4(alpha * acc[k].x, alpha * acc[k].y, alpha * acc[k].z, alpha * acc[k].w);
+        if (Yadd) {
+          const float4 a = Yadd[(size_t)i * W4 + f];
+          o.x = fmaf(beta, a.x, o.x);
+          o.y = fmaf(beta, a.y, o.y);
+          o.z = fmaf(beta, a.z, o.z);
+          o.w = fmaf(beta, a.w, o.w);
+        }
+        Y[(size_t)i * W4 + f] = o;
+      }
+    }
+  }
+}
+
+// Values of A_hat in the CSC order (perm[k] = CSR position of CSC entry k).
+__global__ void k_gather_vals(const float* __restrict__ v, const int* __restrict__ perm, long long nnz,
+                              float* __restrict__ out) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nnz;
+       k += (long long)gridDim.x * blockDim.x)
+    out[k] = v[perm[k]];
+}
+
+// tau_k = ||b[:, k]||_2 for the B columns of a node-major batch (B divides 256).
+__global__ void __launch_bounds__(256)
+k_col_norms(const float* __restrict__ b, long long R, int B, double* __restrict__ partials,
+            unsigned* counter, double* __restrict__ tau) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < R;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = b[e];
+    acc += v * v;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if ((int)threadIdx.x < B) {
+    double t = 0.0;
+    for (int k = threadIdx.x; k < 256; k += B) t += sh[k];
+    partials[(size_t)blockIdx.x * B + threadIdx.x] = t;
+  }
+  if (last_block_arrive(counter)) {
+    __shared__ double tot[GNP_MAX_BATCH];
+    reduce_partials(partials, gridDim.x, B, tot);
+    if ((int)threadIdx.x < B) tau[threadIdx.x] = sqrt(tot[threadIdx.x]);
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+// loss = mean |r| over R entries; r <- sign(r) in place (sign(0) = 0).
+__global__ void __launch_bounds__(256)
+k_l1(float* __restrict__ r, long long R, double* __restrict__ partials, unsigned* counter,
+     float* __restrict__ loss) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < R;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float v = r[e];
+    acc += fabs((double)v);
+    r[e] = (v > 0.f) ? 1.f : ((v < 0.f) ? -1.f : 0.f);
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+  if (last_block_arrive(counter)) {
+    __shared__ double tot[1];
+    reduce_partials(partials, gridDim.x, 1, tot);
+    if (threadIdx.x == 0) {
+      *loss = (float)(tot[0] / (double)R);
+      *counter = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- forward kernels
+
+// u = (sqrt(n)/tau_k) b; H0 = W2^T ReLU(W1 u + b1) + b2 (thread per row).
+__global__ void __launch_bounds__(256)
+k_enc_batch(const float* __restrict__ b, const double* __restrict__ tau, long long R, int B, double sqrt_n,
+            const float* __restrict__ w, float* __restrict__ u_out, float* __restrict__ H0) {
+  __shared__ float sw[ENC_COUNT];
+  for (int k = threadIdx.x; k < ENC_COUNT; k += blockDim.x) sw[k] = w[k];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    const double tv = tau[r % B];
+    const float u = (float)(tv > 0.0 ? b[r] * (sqrt_n / tv) : 0.0);
+    u_out[r] = u;
+    float h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = sw[ENC_B2 + c];
+    for (int k = 0; k < 32; ++k) {
+      const float a = fmaxf(fmaf(u, sw[ENC_W1 + k], sw[ENC_B1 + k]), 0.0f);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) h[c] = fmaf(a, sw[ENC_W2 + k * 16 + c], h[c]);
+    }
+    float4* o = reinterpret_cast<float4*>(H0 + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+  }
+}
+
+// One Res-GCONV layer on the batch: AGG = A_hat X (saved), Out = layer(X, AGG).
+// Warp per node (gather of the node block), then lane per batch column.
+template <int FORM>
+__global__ void __launch_bounds__(256)
+k_layer_batch(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ vh,
+              const float* __restrict__ X, float* __restrict__ AGG, float* __restrict__ Out, int n, int B,
+              const float* __restrict__ lw) {
+  extern __shared__ __align__(16) float smf[];
+  float* sU = smf;
+  float* sW = smf + 256;
+  float* sblk = smf + 512;  // per warp: AGG block [B*16] then X block [B*16]
+  for (int k = threadIdx.x; k < 512; k += blockDim.x) smf[k] = lw[k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int W4 = B * 4;
+  float* sA = sblk + (size_t)wl * (2 * B * 16);
+  float* sX = sA + B * 16;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const float4* X4 = reinterpret_cast<const float4*>(X);
+  for (int i = warp; i < n; i += nwarps) {
+    float4 acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int j = __ldg(col + e);
+      const float a = __ldg(vh + e);
+      const float4* xj = X4 + (size_t)j * W4;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int f = lane + 32 * k;
+        if (f < W4) {
+          const float4 v = __ldg(xj + f);
+          acc[k].x = fmaf(a, v.x, acc[k].x);
+          acc[k].y = fmaf(a, v.y, acc[k].y);
+          acc[k].z = fmaf(a, v.z, acc[k].z);
+          acc[k].w = fmaf(a, v.w, acc[k].w);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int f = lane + 32 * k;
+      if (f < W4) {
+        reinterpret_cast<float4*>(AGG)[(size_t)i * W4 + f] = acc[k];
+        reinterpret_cast<float4*>(sA)[f] = acc[k];
+        reinterpret_cast<float4*>(sX)[f] = __ldg(X4 + (size_t)i * W4 + f);
+      }
+    }
+    __syncwarp();
+    for (int bq = lane; bq < B; bq += 32) {
+      const float* xa = sX + bq * 16;
+      const float* ga = sA + bq * 16;
+      float o[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o[k] = 0.f;
+      for (int c = 0; c < 16; ++c) {
+        const float gc = ga[c];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) o[k] = fmaf(gc, sW[c * 16 + k], o[k]);
+      }
+      if (FORM == GNP_LAYER_PAPER) {
+        for (int c = 0; c < 16; ++c) {
+          const float xc = xa[c];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) o[k] = fmaf(xc, sU[c * 16 + k], o[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) o[k] = fmaxf(o[k], 0.f);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) o[k] = xa[k] + fmaxf(o[k], 0.f);
+      }
+      float4* out = reinterpret_cast<float4*>(Out + ((size_t)i * B + bq) * 16);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    }
+    __syncwarp();
+  }
+}
+
+// z = (w2^T ReLU(D1^T h + e1) + e2) * tau_k / sqrt(n) (thread per row).
+__global__ void __launch_bounds__(256)
+k_dec_batch(const float* __restrict__ HL, const double* __restrict__ tau, long long R, int B, double sqrt_n,
+            const float* __restrict__ wd, float* __restrict__ z) {
+  __shared__ float sw[DEC_COUNT];
+  for (int k = threadIdx.x; k < DEC_COUNT; k += blockDim.x) sw[k] = wd[k];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    float h[16];
+    const float4* hp = reinterpret_cast<const float4*>(HL + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = hp[q];
+      h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+    }
+    float o = sw[576];
+    for (int k = 0; k < 32; ++k) {
+      float a = sw[512 + k];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a = fmaf(h[c], sw[c * 32 + k], a);
+      o = fmaf(fmaxf(a, 0.f), sw[544 + k], o);
+    }
+    const double tv = tau[r % B];
+    z[r] = o * (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------- backward kernels
+
+// Decoder backward (thread per row): do, dc1 = dq * 1[c1 > 0], q = ReLU(c1) saved for
+// the weight gradients, dH^L = dc1 D1^T.
+__global__ void __launch_bounds__(256)
+k_dec_bwd(const float* __restrict__ HL, const float* __restrict__ dz, const double* __restrict__ tau,
+          long long R, int B, double sqrt_n, const float* __restrict__ wd, float* __restrict__ do_out,
+          float* __restrict__ q_out, float* __restrict__ dc1_out, float* __restrict__ dH) {
+  __shared__ float sw[DEC_COUNT];
+  for (int k = threadIdx.x; k < DEC_COUNT; k += blockDim.x) sw[k] = wd[k];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    float h[16];
+    const float4* hp = reinterpret_cast<const float4*>(HL + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = hp[q];
+      h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
+    }
+    const double tv = tau[r % B];
+    const float dov = dz[r] * (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+    do_out[r] = dov;
+    float g[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) g[c] = 0.f;
+    for (int k = 0; k < 32; ++k) {
+      float a = sw[512 + k];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) a = fmaf(h[c], sw[c * 32 + k], a);
+      const float dc = a > 0.f ? dov * sw[544 + k] : 0.f;
+      q_out[r * 32 + k] = fmaxf(a, 0.f);
+      dc1_out[r * 32 + k] = dc;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) g[c] = fmaf(dc, sw[c * 32 + k], g[c]);
+    }
+    float4* o = reinterpret_cast<float4*>(dH + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(g[4 * q], g[4 * q + 1], g[4 * q + 2], g[4 * q + 3]);
+  }
+}
+
+// Layer backward, row part: Gp = G * 1[pre > 0] (pre recomputed from X and AGG exactly
+// as the forward did), Y = Gp W^T, local = Gp U^T (paper) or G (residual).
+template <int FORM>
+__global__ void __launch_bounds__(256)
+k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G,
+                 long long R, const float* __restrict__ lw, float* __restrict__ Gp_out,
+                 float* __restrict__ Y_out, float* __restrict__ local_out) {
+  __shared__ float sU[256], sW[256];
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+    sU[k] = lw[k];
+    sW[k] = lw[256 + k];
+  }
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    float x[16], ag[16], g[16], o[16];
+    const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
+    const float4* ap = reinterpret_cast<const float4*>(AGG + r * 16);
+    const float4* gp = reinterpret_cast<const float4*>(G + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float4 v = xp[q];
+      x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+      v = ap[q];
+      ag[4 * q] = v.x; ag[4 * q + 1] = v.y; ag[4 * q + 2] = v.z; ag[4 * q + 3] = v.w;
+      v = gp[q];
+      g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) o[k] = 0.f;
+    for (int c = 0; c < 16; ++c) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) o[k] = fmaf(ag[c], sW[c * 16 + k], o[k]);
+    }
+    if (FORM == GNP_LAYER_PAPER) {
+      for (int c = 0; c < 16; ++c) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) o[k] = fmaf(x[c], sU[c * 16 + k], o[k]);
+      }
+    }
+    float gpv[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) gpv[k] = o[k] > 0.f ? g[k] : 0.f;
+    float y[16], loc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        a = fmaf(gpv[k], sW[c * 16 + k], a);
+        if (FORM == GNP_LAYER_PAPER) b = fmaf(gpv[k], sU[c * 16 + k], b);
+      }
+      y[c] = a;
+      loc[c] = (FORM == GNP_LAYER_PAPER) ? b : g[c];
+    }
+    float4* po = reinterpret_cast<float4*>(Gp_out + r * 16);
+    float4* yo = reinterpret_cast<float4*>(Y_out + r * 16);
+    float4* lo = reinterpret_cast<float4*>(local_out + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      po[q] = make_float4(gpv[4 * q], gpv[4 * q + 1], gpv[4 * q + 2], gpv[4 * q + 3]);
+      yo[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+      lo[q] = make_float4(loc[4 * q], loc[4 * q + 1], loc[4 * q + 2], loc[4 * q + 3]);
+    }
+  }
+}
+
+// Encoder backward (thread per row): r1 = ReLU(a1) and da1 = (dH0 W2^T) * 1[a1 > 0].
+__global__ void __launch_bounds__(256)
+k_enc_bwd(const float* __restrict__ u, const float* __restrict__ dH0, long long R, const float* __restrict__ w,
+          float* __restrict__ r1_out, float* __restrict__ da1_out) {
+  __shared__ float sw[ENC_COUNT];
+  for (int k = threadIdx.x; k < ENC_COUNT; k += blockDim.x) sw[k] = w[k];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
+       r += (long long)gridDim.x * blockDim.x) {
+    float g[16];
+    const float4* gp = reinterpret_cast<const float4*>(dH0 + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 v = gp[q];
+      g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+    }
+    const float uv = u[r];
+    for (int k = 0; k < 32; ++k) {
+      const float a = fmaf(uv, sw[ENC_W1 + k], sw[ENC_B1 + k]);
+      float d = 0.f;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) d = fmaf(g[c], sw[ENC_W2 + k * 16 + c], d);
+      r1_out[r * 32 + k] = fmaxf(a, 0.f);
+      da1_out[r * 32 + k] = a > 0.f ? d : 0.f;
+    }
+  }
+}
+
+// Weight gradient sum_r A[r, :P]^T B[r, :Q] (plus the column sums of B as row P when
+// the bias row is wanted).  Block b reduces rows [b*chunk, (b+1)*chunk) in float32;
+// partials[b][(P+1)*Q].
+constexpr int WG_CHUNK = 4096;
+constexpr int WG_TILE = 32;
+
+__global__ void __launch_bounds__(256)
+k_wgrad(const float* __restrict__ A, int P, const float* __restrict__ Bm, int Q, long long R,
+        float* __restrict__ partials) {
+  __shared__ float sA[WG_TILE][33];
+  __shared__ float sB[WG_TILE][33];
+  const int PQ = (P + 1) * Q;
+  const long long r0 = (long long)blockIdx.x * WG_CHUNK;
+  const long long r1 = min(R, r0 + WG_CHUNK);
+  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (long long rt = r0; rt < r1; rt += WG_TILE) {
+    const int rows = (int)min((long long)WG_TILE, r1 - rt);
+    for (int t = threadIdx.x; t < WG_TILE * 32; t += blockDim.x) {
+      const int rr = t / 32, c = t % 32;
+      float a = 0.f, b = 0.f;
+      if (rr < rows) {
+        if (c < P) a = A[(rt + rr) * P + c];
+        else if (c == P) a = 1.f;
+        if (c < Q) b = Bm[(rt + rr) * Q + c];
+      }
+      sA[rr][c] = a;
+      sB[rr][c] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      const int o = threadIdx.x + 256 * s;
+      if (o < PQ) {
+        const int p = o / Q, q = o % Q;
+        float a = acc[s];
+        if (p < 32) {
+          for (int rr = 0; rr < rows; ++rr) a = fmaf(sA[rr][p], sB[rr][q], a);
+        } else {
+          for (int rr = 0; rr < rows; ++rr) a += sB[rr][q];
+        }
+        acc[s] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int o = threadIdx.x + 256 * s;
+    if (o < PQ) partials[(size_t)blockIdx.x * PQ + o] = acc[s];
+  }
+}
+
+// Fixed-order float64 sum of the partials; rows 0..P-1 -> W (P x Q row-major),
+// row P -> bias (may be null).
+__global__ void k_wgrad_final(const float* __restrict__ partials, int nblocks, int P, int Q,
+                              float* __restrict__ Wout, float* __restrict__ bias) {
+  const int PQ = (P + 1) * Q;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < PQ; o += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += (double)partials[(size_t)b * PQ + o];
+    const int p = o / Q, q = o % Q;
+    if (p < P) Wout[p * Q + q] = (float)s;
+    else if (bias) bias[q] = (float)s;
+  }
+}
+
+// Adam (bias corrected) with the best-loss snapshot of the weights *before* the update.
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ wbest, const float* __restrict__ g,
+                       float* __restrict__ m, float* __restrict__ v, int count, const float* __restrict__ loss,
+                       float* __restrict__ best, int* __restrict__ tstep, float lr, float b1, float b2,
+                       float eps) {
+  __shared__ int improve;
+  __shared__ int t;
+  if (threadIdx.x == 0) {
+    improve = (*loss < *best) ? 1 : 0;
+    t = *tstep + 1;
+  }
+  __syncthreads();
+  const double c1 = 1.0 - pow((double)b1, (double)t);
+  const double c2 = 1.0 - pow((double)b2, (double)t);
+  for (int k = threadIdx.x; k < count; k += blockDim.x) {
+    const float wk = w[k];
+    if (improve) wbest[k] = wk;
+    const float gk = g[k];
+    const float mk = b1 * m[k] + (1.f - b1) * gk;
+    const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    const float mh = (float)(mk / c1);
+    const float vh = (float)(vk / c2);
+    w[k] = wk - lr * mh / (sqrtf(vh) + eps);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (improve) *best = *loss;
+    *tstep = t;
+  }
+}
+
+// ---------------------------------------------------------------- sampler kernels
+
+__global__ void k_philox_words(const uint4* __restrict__ ctr, uint32_t k0, uint32_t k1, int count,
+                               uint4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = philox4x32_10(ctr[i], k0, k1);
+}
+
+__global__ void k_normal_vec(double* __restrict__ out, int n, unsigned long long seed, uint32_t step,
+                             uint32_t stream) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = (double)philox_normal((unsigned long long)i, seed, step, stream);
+}
+
+// One-block one-sided Jacobi SVD (Hestenes) of H_bar ((k+1) x k, column-major, k <= 64):
+// right singular vectors Z, singular values s; then Q = Z S^-1 in the canonical form
+// (descending s, largest-|entry| of each z positive, 1/s = 0 for s < 1e-14 s_max).
+constexpr int SVD_MAX = 64;
+
+__global__ void __launch_bounds__(256)
+k_jacobi_svd(const double* __restrict__ Hbar, int k, double* __restrict__ Qout) {
+  __shared__ double Bm[(SVD_MAX + 1) * SVD_MAX];
+  __shared__ double Zs[SVD_MAX * SVD_MAX];
+  __shared__ double sv[SVD_MAX];
+  __shared__ int order[SVD_MAX];
+  __shared__ int rotated;
+  const int ld = k + 1;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < ld * k; t += blockDim.x) Bm[t] = Hbar[t];
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) Zs[t] = (t / k == t % k) ? 1.0 : 0.0;
+  __syncthreads();
+  const int kk = (k + 1) & ~1;  // players of the round-robin (one dummy when k is odd)
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < kk - 1; ++round) {
+      for (int pr = wid; pr < kk / 2; pr += nw) {
+        auto pos = [&](int x) { return x == 0 ? 0 : ((x - 1 + round) % (kk - 1)) + 1; };
+        int p = pos(pr), q = pos(kk - 1 - pr);
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        if (q >= k) continue;
+        double* bp = Bm + p * ld;
+        double* bq = Bm + q * ld;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int i = lane; i < ld; i += 32) {
+          al += bp[i] * bp[i];
+          be += bq[i] * bq[i];
+          ga += bp[i] * bq[i];
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + tt * tt);
+          const double s = c * tt;
+          for (int i = lane; i < ld; i += 32) {
+            const double a = bp[i], b = bq[i];
+            bp[i] = c * a - s * b;
+            bq[i] = s * a + c * b;
+          }
+          double* zp = Zs + p * k;
+          double* zq = Zs + q * k;
+          for (int i = lane; i < k; i += 32) {
+            const double a = zp[i], b = zq[i];
+            zp[i] = c * a - s * b;
+            zq[i] = s * a + c * b;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // singular values = column norms
+  for (int j = wid; j < k; j += nw) {
+    double s = 0.0;
+    for (int i = lane; i < ld; i += 32) s += Bm[j * ld + i] * Bm[j * ld + i];
+    s = warp_sum(s);
+    if (lane == 0) sv[j] = sqrt(s);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < k; ++j) order[j] = j;
+    for (int a = 1; a < k; ++a) {  // insertion sort, descending
+      int o = order[a];
+      int b = a - 1;
+      while (b >= 0 && sv[order[b]] < sv[o]) {
+        order[b + 1] = order[b];
+        --b;
+      }
+      order[b + 1] = o;
+    }
+  }
+  __syncthreads();
+  const double smax = sv[order[0]];
+  for (int jj = wid; jj < k; jj += nw) {
+    const int j = order[jj];
+    const double* z = Zs + j * k;
+    // canonical sign: the largest-magnitude entry positive (first one on ties)
+    int imax = 0;
+    double vmax = -1.0;
+    if (lane == 0) {
+      for (int i = 0; i < k; ++i)
+        if (fabs(z[i]) > vmax) { vmax = fabs(z[i]); imax = i; }
+    }
+    imax = __shfl_sync(0xffffffffu, imax, 0);
+    const double sg = z[imax] < 0.0 ? -1.0 : 1.0;
+    const double inv = (sv[j] >= 1e-14 * smax && sv[j] > 0.0) ? 1.0 / sv[j] : 0.0;
+    for (int i = lane; i < k; i += 32) Qout[i * k + jj] = sg * z[i] * inv;  // row-major Q[i][jj]
+  }
+}
+
+// C = Q E for the Eq. 5 draws of this step: E[j][c] = normal(j*Ba + c, stream 2).
+__global__ void k_sampler_coef(const double* __restrict__ Q, int mA, int Ba, unsigned long long seed,
+                               uint32_t step, double* __restrict__ C) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < mA * Ba; t += gridDim.x * blockDim.x) {
+    const int j = t / Ba, c = t % Ba;
+    double s = 0.0;
+    for (int l = 0; l < mA; ++l)
+      s += Q[j * mA + l] * (double)philox_normal((unsigned long long)l * Ba + c, seed, step, STREAM_EPS);
+    C[t] = s;
+  }
+}
+
+// x[:, :Ba] = V_m C (float64 sums, float32 store); x[:, Ba:] ~ N(0, I) (stream 1,
+// element (i, c) at index i*Bg + c).
+__global__ void k_sampler_x(const double* __restrict__ V, int n, int mA, const double* __restrict__ C, int B,
+                            int Ba, unsigned long long seed, uint32_t step, float* __restrict__ x) {
+  const int Bg = B - Ba;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * B;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / B), c = (int)(e % B);
+    float val;
+    if (c < Ba) {
+      double s = 0.0;
+      for (int j = 0; j < mA; ++j) s += V[(size_t)j * n + i] * C[j * Ba + c];
+      val = (float)s;
+    } else {
+      val = philox_normal((unsigned long long)i * Bg + (c - Ba), seed, step, STREAM_X);
+    }
+    x[e] = val;
+  }
+}
+
+// ---------------------------------------------------------------- host drivers
+
+static int grid_rows(long long R) {
+  long long b = (R + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 8LL * NUM_SMS_GB300);
+}
+
+static int layer_smem(int B) { return (512 + 8 * 2 * B * 16) * (int)sizeof(float); }
+
+template <int FORM>
+static int set_layer_attr(int bytes) {
+  static int done = 0;
+  if (done >= bytes) return GNP_OK;
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_layer_batch<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = bytes;
+  return GNP_OK;
+}
+
+// Forward on the batch b (device, node-major [n*B]); activations saved in T.
+static int forward_batch(gnp_model* M, const float* b, cudaStream_t st) {
+  TrainState* T = M->train;
+  const gnp_mat* A = M->A;
+  const int n = A->n, B = T->B, L = M->cfg.L;
+  const long long R = T->R;
+  const double sqrt_n = std::sqrt((double)n);
+  const int nb = red_blocks(R);
+  k_col_norms<<<nb, 256, 0, st>>>(b, R, B, T->red.partials, T->red.counter, T->tau);
+  k_enc_batch<<<grid_rows(R), 256, 0, st>>>(b, T->tau, R, B, sqrt_n, M->w_dev, T->u, T->Hs);
+  const int smem = layer_smem(B);
+  const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
+  for (int l = 0; l < L; ++l) {
+    const float* X = T->Hs + (size_t)l * R * 16;
+    float* Out = T->Hs + (size_t)(l + 1) * R * 16;
+    float* AG = T->AGG + (size_t)l * R * 16;
+    const float* lw = M->w_dev + layer_off(l);
+    if (M->cfg.form == GNP_LAYER_PAPER) {
+      GNP_TRY(set_layer_attr<GNP_LAYER_PAPER>(smem));
+      k_layer_batch<GNP_LAYER_PAPER><<<wgrid, 256, smem, st>>>(A->rp, A->col, M->valhat, X, AG, Out, n, B, lw);
+    } else {
+      GNP_TRY(set_layer_attr<GNP_LAYER_RESID>(smem));
+      k_layer_batch<GNP_LAYER_RESID><<<wgrid, 256, smem, st>>>(A->rp, A->col, M->valhat, X, AG, Out, n, B, lw);
+    }
+  }
+  k_dec_batch<<<grid_rows(R), 256, 0, st>>>(T->Hs + (size_t)L * R * 16, T->tau, R, B, sqrt_n,
+                                            M->w_dev + dec_off(L), T->z);
+  return check_launch("forward_batch");
+}
+
+static int wgrad(TrainState* T, const float* A, int P, const float* Bm, int Q, float* Wout, float* bias,
+                 cudaStream_t st) {
+  const int nblk = (int)((T->R + WG_CHUNK - 1) / WG_CHUNK);
+  const int PQ = (P + 1) * Q;
+  if (T->part_cap < nblk * PQ) {
+    if (T->partials) cudaFree(T->partials);
+    T->partials = nullptr;
+    GNP_TRY(dev_alloc(&T->partials, (size_t)nblk * 33 * 32));
+    T->part_cap = nblk * 33 * 32;
+  }
+  k_wgrad<<<nblk, 256, 0, st>>>(A, P, Bm, Q, T->R, T->partials);
+  k_wgrad_final<<<(PQ + 255) / 256, 256, 0, st>>>(T->partials, nblk, P, Q, Wout, bias);
+  return check_launch("wgrad");
+}
+
+// Backward of the saved forward given dL/dz (device [R]); gradient blob -> T->grad.
+static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
+  TrainState* T = M->train;
+  const gnp_mat* A = M->A;
+  const int n = A->n, B = T->B, L = M->cfg.L;
+  const long long R = T->R;
+  const double sqrt_n = std::sqrt((double)n);
+  float* g = T->grad;
+  const float* HL = T->Hs + (size_t)L * R * 16;
+  // decoder: do -> r1, q -> s32a, dc1 -> s32b, dH^L -> g16a
+  k_dec_bwd<<<grid_rows(R), 256, 0, st>>>(HL, dz, T->tau, R, B, sqrt_n, M->w_dev + dec_off(L), T->r1, T->s32a,
+                                          T->s32b, T->g16a);
+  float* gd = g + dec_off(L);
+  GNP_TRY(wgrad(T, HL, 16, T->s32b, 32, gd, gd + 512, st));          // dD1, de1
+  GNP_TRY(wgrad(T, T->s32a, 32, T->r1, 1, gd + 544, gd + 576, st));   // dD2, de2
+  float* G = T->g16a;
+  float* Gn = T->g16b;
+  const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
+  for (int l = L - 1; l >= 0; --l) {
+    const float* X = T->Hs + (size_t)l * R * 16;
+    const float* AG = T->AGG + (size_t)l * R * 16;
+    const float* lw = M->w_dev + layer_off(l);
+    if (M->cfg.form == GNP_LAYER_PAPER)
+      k_layer_bwd_rows<GNP_LAYER_PAPER><<<grid_rows(R), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+    else
+      k_layer_bwd_rows<GNP_LAYER_RESID><<<grid_rows(R), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+    // dX = local + A_hat^T Y (gather through the canonical CSC)
+    k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->csc.ptr, A->csc.idx, M->valhat_t,
+                                        reinterpret_cast<const float4*>(T->y16), n, B * 4, 1.0f,
+                                        reinterpret_cast<const float4*>(Gn), 1.0f, reinterpret_cast<float4*>(Gn));
+    float* gl = g + layer_off(l);
+    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY(wgrad(T, X, 16, T->gp16, 16, gl, nullptr, st));  // dU
+    else GNP_TRY_CUDA(cudaMemsetAsync(gl, 0, sizeof(float) * 256, st));
+    GNP_TRY(wgrad(T, AG, 16, T->gp16, 16, gl + 256, nullptr, st));  // dW
+    std::swap(G, Gn);
+  }
+  // encoder: r1 -> s32a, da1 -> s32b
+  k_enc_bwd<<<grid_rows(R), 256, 0, st>>>(T->u, G, R, M->w_dev, T->s32a, T->s32b);
+  GNP_TRY(wgrad(T, T->s32a, 32, G, 16, g + ENC_W2, g + ENC_B2, st));  // dW2, db2
+  GNP_TRY(wgrad(T, T->u, 1, T->s32b, 32, g + ENC_W1, g + ENC_B1, st)); // dW1, db1
+  return check_launch("backward_batch");
+}
+
+static int sampler_prepare(gnp_model* M, cudaStream_t st) {
+  TrainState* T = M->train;
+  if (T->sampler_ready) return GNP_OK;
+  const int n = M->A->n;
+  const int m = M->cfg.arnoldi_m;
+  GNP_REQUIRE(m >= 1 && m <= SVD_MAX, "arnoldi_m = %d outside [1, %d]", m, SVD_MAX);
+  double* v1 = nullptr;
+  GNP_TRY(dev_alloc(&v1, (size_t)n));
+  k_normal_vec<<<grid_rows(n), 256, 0, st>>>(v1, n, M->cfg.seed, 0u, STREAM_V1);
+  if (!T->V) GNP_TRY(dev_alloc(&T->V, (size_t)n * (m + 1)));
+  std::vector<double> Hh((size_t)(m + 1) * m, 0.0);
+  int k = 0;
+  int s = arnoldi_basis(M->A, v1, m, T->V, Hh.data(), &k, st);
+  dev_free(v1);
+  if (s != GNP_OK) return s;
+  GNP_REQUIRE(k >= 1, "sampler: Arnoldi broke down at the first step");
+  // H_bar of A_hat = H_bar of A / gamma (same basis V); compact to (k+1) x k
+  std::vector<double> Hk((size_t)(k + 1) * k);
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i <= k; ++i) Hk[(size_t)j * (k + 1) + i] = Hh[(size_t)j * (m + 1) + i] / M->gamma;
+  if (T->Hbar) cudaFree(T->Hbar);
+  T->Hbar = nullptr;
+  if (T->Q) cudaFree(T->Q);
+  T->Q = nullptr;
+  GNP_TRY(dev_alloc(&T->Hbar, Hk.size()));
+  GNP_TRY(dev_alloc(&T->Q, (size_t)k * k));
+  GNP_TRY_CUDA(cudaMemcpyAsync(T->Hbar, Hk.data(), sizeof(double) * Hk.size(), cudaMemcpyHostToDevice, st));
+  k_jacobi_svd<<<1, 256, 0, st>>>(T->Hbar, k, T->Q);
+  GNP_TRY(check_launch("k_jacobi_svd"));
+  GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  T->mA = k;
+  T->sampler_ready = true;
+  return GNP_OK;
+}
+
+static int sample_batch(gnp_model* M, int step, float* x, cudaStream_t st) {
+  TrainState* T = M->train;
+  GNP_TRY(sampler_prepare(M, st));
+  const int n = M->A->n, B = T->B, Ba = B / 2, mA = T->mA;
+  if (!T->C) GNP_TRY(dev_alloc(&T->C, (size_t)SVD_MAX * GNP_MAX_BATCH));
+  k_sampler_coef<<<1, 256, 0, st>>>(T->Q, mA, Ba, M->cfg.seed, (uint32_t)step, T->C);
+  k_sampler_x<<<grid_rows((long long)n * B), 256, 0, st>>>(T->V, n, mA, T->C, B, Ba, M->cfg.seed,
+                                                           (uint32_t)step, x);
+  return check_launch("sample_batch");
+}
+
+// b = A_hat x, forward, loss, dz, backward, Adam.  No host synchronisation.
+static int train_pairs(gnp_model* M, const float* x, cudaStream_t st) {
+  TrainState* T = M->train;
+  const gnp_mat* A = M->A;
+  const int n = A->n, B = T->B;
+  const long long R = T->R;
+  const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
+  const int W4 = B / 4;
+  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(x), n, W4, 1.0f,
+                                      nullptr, 0.0f, reinterpret_cast<float4*>(T->bb));
+  GNP_TRY(forward_batch(M, T->bb, st));
+  // r = A_hat z - b; loss = mean |r|; s = sign(r); dz = A_hat^T s / (n B)
+  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(T->z), n, W4,
+                                      1.0f, reinterpret_cast<const float4*>(T->bb), -1.0f,
+                                      reinterpret_cast<float4*>(T->rr));
+  k_l1<<<red_blocks(R), 256, 0, st>>>(T->rr, R, T->red.partials, T->red.counter, T->loss);
+  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->rr),
+                                      n, W4, (float)(1.0 / (double)R), nullptr, 0.0f,
+                                      reinterpret_cast<float4*>(T->dz));
+  GNP_TRY(backward_batch(M, T->dz, st));
+  const int cnt = weight_count(M->cfg.L);
+  k_adam<<<1, 1024, 0, st>>>(M->w_dev, M->w_best, T->grad, T->adam_m, T->adam_v, cnt, T->loss, T->best_loss,
+                             T->adam_t, M->cfg.lr, M->cfg.beta1, M->cfg.beta2, M->cfg.eps);
+  M->host_stale = true;
+  ++M->version;
+  return check_launch("train step");
+}
+
+static int train_prepare(gnp_model* M, int B, cudaStream_t st) {
+  (void)st;
+  return train_ensure(M, B);
+}
+
+}  // namespace gnp
+
+using namespace gnp;
+
+extern "C" {
+
+int gnp_philox4x32_10(const unsigned* ctr_dev, unsigned key0, unsigned key1, int count, unsigned* out_dev,
+                      void* stream) {
+  GNP_REQUIRE(ctr_dev && out_dev && count >= 0, "gnp_philox4x32_10: bad argument");
+  if (count == 0) return GNP_OK;
+  k_philox_words<<<(count + 255) / 256, 256, 0, as_stream(stream)>>>(
+      reinterpret_cast<const uint4*>(ctr_dev), key0, key1, count, reinterpret_cast<uint4*>(out_dev));
+  return check_launch("k_philox_words");
+}
+
+int gnp_set_weights_device(gnp_model* M, const float* w_dev, int count, void* stream) {
+  GNP_REQUIRE(M && w_dev, "gnp_set_weights_device: null argument");
+  GNP_REQUIRE(count == weight_count(M->cfg.L), "gnp_set_weights_device: %d floats, expected %d", count,
+              weight_count(M->cfg.L));
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY_CUDA(cudaMemcpyAsync(M->w_dev, w_dev, sizeof(float) * count, cudaMemcpyDeviceToDevice, st));
+  GNP_TRY_CUDA(cudaMemcpyAsync(M->w_best, w_dev, sizeof(float) * count, cudaMemcpyDeviceToDevice, st));
+  M->host_stale = true;
+  ++M->version;
+  return GNP_OK;
+}
+
+int gnp_forward_batch(gnp_model* M, const float* b_dev, int B, float* z_dev, void* stream) {
+  GNP_REQUIRE(M && b_dev && z_dev, "gnp_forward_batch: null argument");
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY(train_prepare(M, B, st));
+  GNP_TRY(forward_batch(M, b_dev, st));
+  GNP_TRY_CUDA(cudaMemcpyAsync(z_dev, M->train->z, sizeof(float) * M->train->R, cudaMemcpyDeviceToDevice, st));
+  return GNP_OK;
+}
+
+int gnp_backward_batch(gnp_model* M, const float* dz_dev, float* grad_dev, void* stream) {
+  GNP_REQUIRE(M && dz_dev && grad_dev, "gnp_backward_batch: null argument");
+  GNP_REQUIRE(M->train != nullptr, "gnp_backward_batch: no forward_batch before");
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY(backward_batch(M, dz_dev, st));
+  GNP_TRY_CUDA(cudaMemcpyAsync(grad_dev, M->train->grad, sizeof(float) * weight_count(M->cfg.L),
+                               cudaMemcpyDeviceToDevice, st));
+  return GNP_OK;
+}
+
+int gnp_sample_batch(gnp_model* M, int step, float* x_dev, void* stream) {
+  GNP_REQUIRE(M && x_dev, "gnp_sample_batch: null argument");
+  GNP_REQUIRE(step >= 0, "gnp_sample_batch: step < 0");
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY(train_prepare(M, M->cfg.batch, st));
+  return sample_batch(M, step, x_dev, st);
+}
+
+int gnp_train_step_pairs(gnp_model* M, const float* x_dev, int B, float* loss_out, void* stream) {
+  GNP_REQUIRE(M && x_dev, "gnp_train_step_pairs: null argument");
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY(train_prepare(M, B, st));
+  GNP_TRY(train_pairs(M, x_dev, st));
+  if (loss_out) {
+    GNP_TRY_CUDA(cudaMemcpyAsync(loss_out, M->train->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  return GNP_OK;
+}
+
+int gnp_train_step(gnp_model* M, float* loss_out, void* stream) {
+  GNP_REQUIRE(M, "gnp_train_step: null model");
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY(train_prepare(M, M->cfg.batch, st));
+  TrainState* T = M->train;
+  GNP_TRY(sample_batch(M, T->step, T->xb, st));
+  ++T->step;
+  GNP_TRY(train_pairs(M, T->xb, st));
+  if (loss_out) {
+    GNP_TRY_CUDA(cudaMemcpyAsync(loss_out, T->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+    GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  return GNP_OK;
+}
+
+int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream) {
+  GNP_REQUIRE(M && steps >= 0, "gnp_train: bad argument");
+  cudaStream_t st = as_stream(stream);
+  GNP_TRY(train_prepare(M, M->cfg.batch, st));
+  TrainState* T = M->train;
+  GNP_TRY(sampler_prepare(M, st));
+  for (int s = 0; s < steps; ++s) {
+    GNP_TRY(sample_batch(M, T->step, T->xb, st));
+    ++T->step;
+    GNP_TRY(train_pairs(M, T->xb, st));
+  }
+  if (best_loss_out) {
+    GNP_TRY_CUDA(cudaMemcpyAsync(best_loss_out, T->best_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+  }
+  GNP_TRY_CUDA(cudaStreamSynchronize(st));
+  return GNP_OK;
+}
+
+}  // extern "C"

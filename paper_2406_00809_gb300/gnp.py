@@ -1,0 +1,392 @@
+"""Thin Python binding of libgnp.so (declarations in include/gnp.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (contiguous, the dtype each entry
+point documents); streams default to torch's current stream.  A missing library
+raises at the first call, there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgnp.so")
+
+GNP_OK = 0
+STATUS = {0: "GNP_OK", 1: "GNP_ERR_INVALID_ARG", 2: "GNP_ERR_INVALID_CSR", 3: "GNP_ERR_OOM",
+          4: "GNP_ERR_CUDA", 5: "GNP_ERR_BREAKDOWN", 6: "GNP_ERR_STAGNATION",
+          7: "GNP_ERR_RESIDUAL_MISMATCH", 8: "GNP_ERR_NOT_CONVERGED", 9: "GNP_ERR_TIMEOUT",
+          10: "GNP_ERR_NAN", 11: "GNP_ERR_BUSY"}
+LAYER_PAPER, LAYER_RESID = 0, 1
+H_FP32, H_BF16 = 0, 1
+
+
+class GnpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GnpConfig(C.Structure):
+    _fields_ = [("L", C.c_int), ("form", C.c_int), ("hprec", C.c_int), ("batch", C.c_int),
+                ("arnoldi_m", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_ulonglong)]
+
+
+class _SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("status", C.c_int),
+                ("rel_res_est", C.c_double), ("rel_res_true", C.c_double),
+                ("seconds", C.c_double), ("res_history", C.POINTER(C.c_double)),
+                ("res_history_len", C.c_int), ("hessenberg", C.POINTER(C.c_double)),
+                ("hessenberg_cols", C.c_int), ("cycles", C.c_int), ("gconv_launches", C.c_int),
+                ("gconv_ms", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libgnp.so (built in-tree by paper_2406_00809_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2406_00809_gb300.build`")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d, f = C.c_void_p, C.c_int, C.c_double, C.c_float
+    pp = C.POINTER(C.c_void_p)
+    sig = {
+        "gnp_status_string": (C.c_char_p, [i]),
+        "gnp_last_error": (C.c_char_p, []),
+        "gnp_weight_count": (i, [i]),
+        "gnp_mat_create": (i, [i, C.c_longlong, vp, vp, vp, i, vp, pp]),
+        "gnp_mat_destroy": (None, [vp]),
+        "gnp_mat_info": (i, [vp, C.POINTER(i), C.POINTER(C.c_longlong)]),
+        "gnp_gamma": (i, [vp, C.POINTER(d), vp]),
+        "gnp_spmv": (i, [vp, vp, vp, vp]),
+        "gnp_create": (i, [vp, C.POINTER(GnpConfig), vp, pp]),
+        "gnp_destroy": (None, [vp]),
+        "gnp_model_gamma": (i, [vp, C.POINTER(d)]),
+        "gnp_get_weights": (i, [vp, vp, C.POINTER(i)]),
+        "gnp_set_weights": (i, [vp, vp, i]),
+        "gnp_set_hprec": (i, [vp, i]),
+        "gnp_apply": (i, [vp, vp, vp, vp]),
+        "gnp_apply_trace": (i, [vp, vp, vp, vp, vp]),
+        "gnp_forward_batch": (i, [vp, vp, i, vp, vp]),
+        "gnp_backward_batch": (i, [vp, vp, vp, vp]),
+        "gnp_sample_batch": (i, [vp, i, vp, vp]),
+        "gnp_train_step_pairs": (i, [vp, vp, i, C.POINTER(f), vp]),
+        "gnp_train_step": (i, [vp, C.POINTER(f), vp]),
+        "gnp_train": (i, [vp, i, C.POINTER(f), vp]),
+        "gnp_set_weights_device": (i, [vp, vp, i, vp]),
+        "gnp_philox4x32_10": (i, [vp, C.c_uint, C.c_uint, i, vp, vp]),
+        "fgmres_solve": (i, [vp, vp, vp, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
+        "gnp_profile_gconv": (i, [i]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != GNP_OK:
+        raise GnpError(status, lib().gnp_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA torch tensor (checked)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def weight_count(L: int) -> int:
+    return lib().gnp_weight_count(L)
+
+
+def status_string(s: int) -> str:
+    return lib().gnp_status_string(s).decode()
+
+
+# --------------------------------------------------------------------- matrices
+
+class Mat:
+    """Owner of a gnp_mat handle (freed with the object)."""
+
+    def __init__(self, handle, n, nnz):
+        self.h = handle
+        self.n = n
+        self.nnz = nnz
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gnp_mat_destroy(self.h)
+            self.h = None
+
+
+def gnp_mat_create(row_ptr, col, val, stream=None) -> Mat:
+    """CSR (int32 row_ptr/col, float64 val) from numpy arrays or CUDA tensors."""
+    out = C.c_void_p()
+    if isinstance(row_ptr, np.ndarray):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        vl = np.ascontiguousarray(val, dtype=np.float64)
+        n = rp.size - 1
+        nnz = cl.size
+        _check(lib().gnp_mat_create(n, nnz, rp.ctypes.data, cl.ctypes.data, vl.ctypes.data, 0,
+                                    _stream(stream), C.byref(out)))
+    else:
+        import torch
+        n = row_ptr.numel() - 1
+        nnz = col.numel()
+        _check(lib().gnp_mat_create(n, nnz, _dptr(row_ptr, torch.int32, "row_ptr"),
+                                    _dptr(col, torch.int32, "col"), _dptr(val, torch.float64, "val"),
+                                    1, _stream(stream), C.byref(out)))
+    return Mat(out, n, nnz)
+
+
+def mat_from_csr(A) -> Mat:
+    """From an ``inputs.CSR``."""
+    return gnp_mat_create(A.row_ptr, A.col, A.val)
+
+
+def gnp_gamma(A: Mat, stream=None) -> float:
+    g = C.c_double()
+    _check(lib().gnp_gamma(A.h, C.byref(g), _stream(stream)))
+    return g.value
+
+
+def gnp_spmv(A: Mat, x, y, stream=None):
+    import torch
+    _check(lib().gnp_spmv(A.h, _dptr(x, torch.float64, "x"), _dptr(y, torch.float64, "y"), _stream(stream)))
+    return y
+
+
+# --------------------------------------------------------------------- model
+
+def make_config(L=8, form=LAYER_PAPER, hprec=H_FP32, batch=16, arnoldi_m=40, lr=1e-3,
+                beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> GnpConfig:
+    return GnpConfig(L, form, hprec, batch, arnoldi_m, lr, beta1, beta2, eps, seed)
+
+
+class Model:
+    def __init__(self, handle, A: Mat, cfg: GnpConfig):
+        self.h = handle
+        self.A = A  # keep the matrix alive
+        self.cfg = cfg
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gnp_destroy(self.h)
+            self.h = None
+
+
+def gnp_create(A: Mat, cfg: GnpConfig, weights) -> Model:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    if w.size != weight_count(cfg.L):
+        raise ValueError(f"weights: {w.size} floats, expected {weight_count(cfg.L)}")
+    out = C.c_void_p()
+    _check(lib().gnp_create(A.h, C.byref(cfg), w.ctypes.data, C.byref(out)))
+    return Model(out, A, cfg)
+
+
+def gnp_model_gamma(M: Model) -> float:
+    g = C.c_double()
+    _check(lib().gnp_model_gamma(M.h, C.byref(g)))
+    return g.value
+
+
+def gnp_get_weights(M: Model) -> np.ndarray:
+    cnt = C.c_int(0)
+    _check(lib().gnp_get_weights(M.h, None, C.byref(cnt)))
+    w = np.zeros(cnt.value, dtype=np.float32)
+    _check(lib().gnp_get_weights(M.h, w.ctypes.data, C.byref(cnt)))
+    return w
+
+
+def gnp_set_weights(M: Model, weights):
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(lib().gnp_set_weights(M.h, w.ctypes.data, w.size))
+
+
+def gnp_set_hprec(M: Model, hprec: int):
+    _check(lib().gnp_set_hprec(M.h, hprec))
+
+
+def gnp_apply(M: Model, v, z, stream=None):
+    """z (float32 [n]) = M(v) (float64 [n])."""
+    import torch
+    _check(lib().gnp_apply(M.h, _dptr(v, torch.float64, "v"), _dptr(z, torch.float32, "z"),
+                           _stream(stream)))
+    return z
+
+
+def gnp_apply_trace(M: Model, v, z, hidden, stream=None):
+    import torch
+    _check(lib().gnp_apply_trace(M.h, _dptr(v, torch.float64, "v"), _dptr(z, torch.float32, "z"),
+                                 _dptr(hidden, torch.float32, "hidden"), _stream(stream)))
+    return z
+
+
+# --------------------------------------------------------------------- training
+
+def gnp_forward_batch(M: Model, b, z, B=None, stream=None):
+    """z = M(b) for a node-major batch b (float32 [n, B] or flat [n*B])."""
+    import torch
+    if B is None:
+        B = b.shape[1] if b.dim() == 2 else M.cfg.batch
+    _check(lib().gnp_forward_batch(M.h, _dptr(b, torch.float32, "b"), B, _dptr(z, torch.float32, "z"),
+                                   _stream(stream)))
+    return z
+
+
+def gnp_backward_batch(M: Model, dz, grad, stream=None):
+    import torch
+    _check(lib().gnp_backward_batch(M.h, _dptr(dz, torch.float32, "dz"), _dptr(grad, torch.float32, "grad"),
+                                    _stream(stream)))
+    return grad
+
+
+def gnp_sample_batch(M: Model, step: int, x, stream=None):
+    import torch
+    _check(lib().gnp_sample_batch(M.h, step, _dptr(x, torch.float32, "x"), _stream(stream)))
+    return x
+
+
+def gnp_train_step_pairs(M: Model, x, B=None, stream=None) -> float:
+    """One training step on solutions x (float32 [n, B] or flat [n*B], node-major)."""
+    import torch
+    if B is None:
+        B = x.shape[1] if x.dim() == 2 else M.cfg.batch
+    loss = C.c_float(0.0)
+    _check(lib().gnp_train_step_pairs(M.h, _dptr(x, torch.float32, "x"), B, C.byref(loss),
+                                      _stream(stream)))
+    return loss.value
+
+
+def gnp_train_step(M: Model, stream=None) -> float:
+    loss = C.c_float(0.0)
+    _check(lib().gnp_train_step(M.h, C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def gnp_set_weights_device(M: Model, w, stream=None):
+    import torch
+    _check(lib().gnp_set_weights_device(M.h, _dptr(w, torch.float32, "w"), w.numel(), _stream(stream)))
+
+
+def gnp_philox4x32_10(ctr, key0: int, key1: int, out, stream=None):
+    """ctr, out: int32 CUDA tensors of shape [count, 4] (uint32 bit patterns)."""
+    import torch
+    _check(lib().gnp_philox4x32_10(_dptr(ctr, torch.int32, "ctr"), key0, key1, ctr.shape[0],
+                                   _dptr(out, torch.int32, "out"), _stream(stream)))
+    return out
+
+
+def gnp_train(M: Model, steps: int, stream=None) -> float:
+    best = C.c_float(0.0)
+    _check(lib().gnp_train(M.h, steps, C.byref(best), _stream(stream)))
+    return best.value
+
+
+# --------------------------------------------------------------------- solver
+
+def gnp_profile_gconv(on: bool):
+    _check(lib().gnp_profile_gconv(1 if on else 0))
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    restarts: int
+    rel_res_est: float
+    rel_res_true: float
+    seconds: float
+    history: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    hessenberg: np.ndarray | None = None
+    cycles: int = 0
+    gconv_launches: int = 0
+    gconv_ms: float = 0.0
+
+    @property
+    def status_name(self) -> str:
+        return STATUS.get(self.status, str(self.status))
+
+
+def fgmres_solve(A: Mat, b, x, M: Model | None = None, restart=30, rtol=1e-8, maxiters=1000,
+                 stream=None, history=True, hessenberg=False, check=False) -> SolveInfo:
+    """Solve A x = b (float64 CUDA tensors; x holds x0 on entry)."""
+    import torch
+    info = _SolveInfo()
+    hist = np.zeros(maxiters + 1) if history else None
+    hess = np.zeros((restart, restart + 1)) if hessenberg else None
+    if hist is not None:
+        info.res_history = hist.ctypes.data_as(C.POINTER(C.c_double))
+    if hess is not None:
+        info.hessenberg = hess.ctypes.data_as(C.POINTER(C.c_double))
+    st = lib().fgmres_solve(A.h, _dptr(b, torch.float64, "b"), _dptr(x, torch.float64, "x"),
+                            M.h if M is not None else None, restart, rtol, maxiters, C.byref(info),
+                            _stream(stream))
+    if check:
+        _check(st)
+    elif st not in STATUS:
+        _check(st)
+    out = SolveInfo(st, info.iters, info.restarts, info.rel_res_est, info.rel_res_true, info.seconds,
+                    cycles=info.cycles, gconv_launches=info.gconv_launches, gconv_ms=info.gconv_ms)
+    if hist is not None:
+        out.history = hist[:info.res_history_len].copy()
+    if hess is not None:
+        cols = info.hessenberg_cols
+        out.hessenberg = hess.T[:cols + 1, :cols].copy()  # column-major (m+1) x m
+    return out
+
+
+# --------------------------------------------------------------------- autograd
+
+def gnp_function(M: Model):
+    """torch.autograd.Function computing z = M(b) for a node-major batch b [n, B]
+    with the weight blob w (float32 CUDA [count]) as the differentiable input; the
+    backward is the library's hand-written kernel (gnp_backward_batch).  Only the
+    weights receive a gradient (tau = ||b|| carries none, Sec. 2.3)."""
+    import torch
+
+    class GnpFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w, b):
+            gnp_set_weights_device(M, w.detach().contiguous())
+            z = torch.empty_like(b)
+            gnp_forward_batch(M, b.contiguous(), z, B=b.shape[1] if b.dim() == 2 else None)
+            return z
+
+        @staticmethod
+        def backward(ctx, dz):
+            g = torch.empty(weight_count(M.cfg.L), dtype=torch.float32, device=dz.device)
+            gnp_backward_batch(M, dz.contiguous(), g)
+            return g, None
+
+    return GnpFunction

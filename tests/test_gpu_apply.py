@@ -1,0 +1,130 @@
+"""GPU parity of the GNP operator (gamma, A_hat, encoder, Res-GCONV, decoder) against
+the float64 oracle, through the C ABI.  Tolerances: float32 hidden block 1e-5 relative
+L2, bfloat16 hidden block 2e-2 relative L2."""
+import numpy as np
+import pytest
+
+from oracle import gnp_ref as G
+from paper_2406_00809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+BF16_TOL = 2e-2
+
+
+@pytest.fixture(scope="module")
+def gnp():
+    import torch
+    from paper_2406_00809_gb300 import build, gnp as g
+    build.build()
+    assert torch.cuda.is_available()
+    return g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def run_apply(g, A, blob, L, form, hprec, v):
+    import torch
+    M_ = g.mat_from_csr(A)
+    cfg = g.make_config(L=L, form=form, hprec=hprec)
+    M = g.gnp_create(M_, cfg, blob)
+    z = torch.empty(A.n, dtype=torch.float32, device="cuda")
+    g.gnp_apply(M, dev(v, torch.float64), z)
+    torch.cuda.synchronize()
+    return z.cpu().numpy().astype(np.float64), M
+
+
+MATS = {
+    "poisson32": lambda: I.poisson2d(32),                 # n = 1024: 4 full tiles
+    "convdiff45": lambda: I.convdiff2d(45, 100.0),        # n = 2025: ragged last tile
+    "powerlaw12k": lambda: I.powerlaw(12_289, seed=3),    # rows of up to 2000 nnz span slots
+    "aniso9": lambda: I.aniso3d(9, 100.0),
+}
+
+
+@pytest.mark.parametrize("name", list(MATS))
+def test_gamma_matches_oracle(gnp, name):
+    A = MATS[name]()
+    Mt = gnp.mat_from_csr(A)
+    assert abs(gnp.gnp_gamma(Mt) - G.gamma(A.to_scipy())) <= 1e-13 * G.gamma(A.to_scipy())
+
+
+@pytest.mark.parametrize("name", list(MATS))
+def test_spmv_matches_scipy(gnp, name):
+    import torch
+    A = MATS[name]()
+    Mt = gnp.mat_from_csr(A)
+    x = I.gaussian(A.n, seed=1)
+    y = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    gnp.gnp_spmv(Mt, dev(x, torch.float64), y)
+    ref = A.to_scipy() @ x
+    assert rel(y.cpu().numpy(), ref) <= 1e-14
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("L", [0, 1, 4, 8])
+def test_apply_fp32_matches_oracle(gnp, name, form, L):
+    A = MATS[name]()
+    blob = I.init_weights(L, seed=L + 7)
+    blob[32:64] = np.random.default_rng(L).standard_normal(32) * 0.2  # encoder biases
+    v = I.gaussian(A.n, seed=2)
+    z, M = run_apply(gnp, A, blob, L, form, 0, v)
+    Ahat = G.normalise(A.to_scipy())
+    zr = G.forward(Ahat, v, G.unpack(blob, L), form)
+    assert rel(z, zr) <= F32_TOL, (name, form, L, rel(z, zr))
+
+
+@pytest.mark.parametrize("name", ["poisson32", "powerlaw12k"])
+@pytest.mark.parametrize("form", [0, 1])
+def test_apply_bf16_matches_oracle(gnp, name, form):
+    A = MATS[name]()
+    L = 8
+    blob = I.init_weights(L, seed=3)
+    v = I.gaussian(A.n, seed=4)
+    z, _ = run_apply(gnp, A, blob, L, form, 1, v)
+    zr = G.forward(G.normalise(A.to_scipy()), v, G.unpack(blob, L), form)
+    assert rel(z, zr) <= BF16_TOL, rel(z, zr)
+
+
+def test_apply_trace_per_layer(gnp):
+    import torch
+    A = I.convdiff2d(45, 100.0)
+    L = 3
+    blob = I.init_weights(L, seed=1)
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L), blob)
+    v = I.gaussian(A.n, seed=5)
+    z = torch.empty(A.n, dtype=torch.float32, device="cuda")
+    hid = torch.empty((L + 1) * A.n * 16, dtype=torch.float32, device="cuda")
+    gnp.gnp_apply_trace(M, dev(v, torch.float64), z, hid)
+    Hs = G.hidden_trace(G.normalise(A.to_scipy()), v, G.unpack(blob, L), 0)
+    hg = hid.cpu().numpy().reshape(L + 1, A.n, 16)
+    for l in range(L + 1):
+        assert rel(hg[l], Hs[l]) <= F32_TOL, l
+    zr = G.forward(G.normalise(A.to_scipy()), v, G.unpack(blob, L), 0)
+    assert rel(z.cpu().numpy(), zr) <= F32_TOL
+
+
+def test_apply_scale_equivariance_and_zero(gnp):
+    import torch
+    A = I.poisson2d(32)
+    blob = I.init_weights(4, seed=0)
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=4), blob)
+    v = I.gaussian(A.n, seed=6)
+    z1 = torch.empty(A.n, dtype=torch.float32, device="cuda")
+    z2 = torch.empty_like(z1)
+    gnp.gnp_apply(M, dev(v, torch.float64), z1)
+    gnp.gnp_apply(M, dev(1e3 * v, torch.float64), z2)
+    assert rel(z2.cpu().numpy(), 1e3 * z1.cpu().numpy()) <= 1e-6
+    gnp.gnp_apply(M, dev(np.zeros(A.n), torch.float64), z1)
+    assert torch.count_nonzero(z1).item() == 0
