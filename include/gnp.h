@@ -217,6 +217,45 @@ int fgmres_solve(gnp_mat* A, const double* b_dev, double* x_dev, gnp_model* M,
                  int restart, double rtol, int maxiters, gnp_solve_info* info,
                  void* stream);
 
+/* ---------------------------------------------------------------- solve server */
+
+/* Continuous batching of many FGMRES solves on one GPU (Sec. 4: one preconditioner
+ * serves any number of right-hand sides; here also many matrices at once).  A server
+ * thread admits queued requests in FIFO order while fewer than max_active run and their
+ * device-memory footprint (Krylov basis n*(restart+1) float64, directions n*restart
+ * float32, GNP hidden blocks 2*n*16 float32, reduction scratch) fits in max_bytes; each
+ * round launches one CUDA graph holding the next restart cycle of every running
+ * request.  Results are the same as a lone fgmres_solve of the request. */
+typedef struct gnp_server_config {
+  size_t max_bytes; /* device-memory budget for the running requests' workspaces */
+  int max_active;   /* requests running at once (slots) */
+  int restart;      /* FGMRES restart length of every request */
+} gnp_server_config;
+
+typedef struct gnp_server_stats_t {
+  int queued, active;
+  size_t used_bytes;
+  long long rounds, completed, max_active_seen;
+} gnp_server_stats_t;
+
+int gnp_server_create(const gnp_server_config* cfg, gnp_server** out);
+/* Queue a solve of A x = b (x_dev holds x0) preconditioned by M (NULL = identity);
+ * the buffers must stay valid until the ticket is collected.  A and M are read only
+ * while the request runs (do not train M then); one model may serve many requests at
+ * once.  Never blocks; *ticket identifies the request. */
+int gnp_server_submit(gnp_server* S, gnp_mat* A, gnp_model* M, const double* b_dev,
+                      double* x_dev, double rtol, int maxiters, long long* ticket);
+/* GNP_ERR_BUSY while the request is queued or running; otherwise collects it and
+ * returns its solve status (GNP_ERR_OOM if its footprint exceeds max_bytes).  info (may
+ * be NULL) receives iterations, residuals and `seconds` = submit-to-finish latency. */
+int gnp_server_poll(gnp_server* S, long long ticket, gnp_solve_info* info);
+/* Block until the request finishes (then as poll) or timeout_s passes
+ * (GNP_ERR_TIMEOUT; the request keeps running). */
+int gnp_server_wait(gnp_server* S, long long ticket, double timeout_s, gnp_solve_info* info);
+int gnp_server_stats(gnp_server* S, gnp_server_stats_t* out);
+/* Finish the running requests, abandon the queued ones, join the server thread. */
+void gnp_server_destroy(gnp_server* S);
+
 /* Time every Res-GCONV launch of the following solves with CUDA events recorded on
  * the solve's stream around the launch (inside the captured restart cycle); the sums
  * arrive in gnp_solve_info.gconv_ms / gconv_launches.  The event records add a little

@@ -359,7 +359,7 @@ static int set_smem_attrs() {
 
 template <class HT, int FORM>
 static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                      const int* ctl, cudaStream_t st, cudaEvent_t* ev) {
+                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W) {
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
   const double sqrt_n = std::sqrt((double)n);
@@ -368,24 +368,24 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
   if (vscale)
-    k_vnorm<true><<<nb, RED_THREADS, 0, st>>>(v, vscale, ctl, n, M->red.partials, M->red.counter, M->tau);
+    k_vnorm<true><<<nb, RED_THREADS, 0, st>>>(v, vscale, ctl, n, W.red.partials, W.red.counter, W.tau);
   else
-    k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, M->red.partials, M->red.counter, M->tau);
+    k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
   EncW ew;
   DecW dw;
   fill_params(M->w_host, L, ew, dw);
-  HT* H0 = static_cast<HT*>(M->H[0]);
-  HT* H1 = static_cast<HT*>(M->H[1]);
-  k_encode<HT><<<nt, TILE, 0, st>>>(v, M->tau, ctl, n, sqrt_n, H0, ew);
+  HT* H0 = static_cast<HT*>(W.H[0]);
+  HT* H1 = static_cast<HT*>(W.H[1]);
+  k_encode<HT><<<nt, TILE, 0, st>>>(v, W.tau, ctl, n, sqrt_n, H0, ew);
   const long long hcount = (long long)n * 16;
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, hcount);
   const int fused_last = (L > 0 && !trace) ? 1 : 0;
   for (int l = 0; l < L - fused_last; ++l) {
     LayerW lw;
     fill_layer(M->w_host, l, lw);
-    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * l], st));
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
     k_gconv<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
-    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * l + 1], st));
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
     if (trace)
       k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
     std::swap(H0, H1);
@@ -393,26 +393,46 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   if (fused_last) {
     LayerW lw;
     fill_layer(M->w_host, L - 1, lw);
-    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * (L - 1)], st));
-    k_gconv_dec<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, M->tau, sqrt_n, n,
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
+    k_gconv_dec<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, W.tau, sqrt_n, n,
                                                   ctl, lw, dw);
-    if (ev) GNP_TRY_CUDA(cudaEventRecord(ev[2 * (L - 1) + 1], st));
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
-    k_decode<HT><<<nt, TILE, 0, st>>>(H0, z, M->tau, sqrt_n, n, ctl, dw);
+    k_decode<HT><<<nt, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
   }
   return check_launch("gnp apply");
 }
 
 int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                 const int* ctl, cudaStream_t st, cudaEvent_t* ev) {
+                 const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs* ws) {
   GNP_TRY(model_sync_host(M));
+  const ApplyWs& W = ws ? *ws : M->ws;
   const int form = M->cfg.form;
   if (M->hprec == GNP_H_BF16) {
-    return form == GNP_LAYER_PAPER ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev)
-                                   : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev);
+    return form == GNP_LAYER_PAPER
+               ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W)
+               : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W);
   }
-  return form == GNP_LAYER_PAPER ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev)
-                                 : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev);
+  return form == GNP_LAYER_PAPER ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W)
+                                 : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W);
+}
+
+int apply_ws_alloc(ApplyWs& ws, int n) {
+  GNP_TRY(dev_alloc(reinterpret_cast<float**>(&ws.H[0]), (size_t)n * 16));
+  GNP_TRY(dev_alloc(reinterpret_cast<float**>(&ws.H[1]), (size_t)n * 16));
+  GNP_TRY(dev_alloc(&ws.tau, 2));
+  GNP_TRY(red_alloc(ws.red, 4 * NUM_SMS_GB300, 1));
+  return GNP_OK;
+}
+
+void apply_ws_free(ApplyWs& ws) {
+  float* h0 = static_cast<float*>(ws.H[0]);
+  float* h1 = static_cast<float*>(ws.H[1]);
+  dev_free(h0);
+  dev_free(h1);
+  ws.H[0] = ws.H[1] = nullptr;
+  dev_free(ws.tau);
+  red_free(ws.red);
 }
 
 int apply_prepare(gnp_model* M) {
@@ -463,12 +483,9 @@ int gnp_create(const gnp_mat* Ac, const gnp_config* cfg, const float* weights_ho
   double* gdev = nullptr;
   do {
     if ((s = dev_alloc(&M->valhat, (size_t)std::max<long long>(nnz, 1))) != GNP_OK) break;
-    if ((s = dev_alloc(reinterpret_cast<float**>(&M->H[0]), (size_t)n * 16)) != GNP_OK) break;
-    if ((s = dev_alloc(reinterpret_cast<float**>(&M->H[1]), (size_t)n * 16)) != GNP_OK) break;
-    if ((s = dev_alloc(&M->tau, 2)) != GNP_OK) break;
+    if ((s = apply_ws_alloc(M->ws, n)) != GNP_OK) break;
     if ((s = dev_alloc(&M->w_dev, (size_t)cnt)) != GNP_OK) break;
     if ((s = dev_alloc(&M->w_best, (size_t)cnt)) != GNP_OK) break;
-    if ((s = red_alloc(M->red, 4 * NUM_SMS_GB300, 1)) != GNP_OK) break;
     if ((s = dev_alloc(&gdev, 1)) != GNP_OK) break;
     if ((s = gamma_launch(A, gdev, 0)) != GNP_OK) break;
     cudaError_t e = cudaMemcpy(&M->gamma, gdev, sizeof(double), cudaMemcpyDeviceToHost);
@@ -510,14 +527,9 @@ void gnp_destroy(gnp_model* M) {
   M->train = nullptr;
   dev_free(M->valhat);
   dev_free(M->valhat_t);
-  float* h0 = static_cast<float*>(M->H[0]);
-  float* h1 = static_cast<float*>(M->H[1]);
-  dev_free(h0);
-  dev_free(h1);
-  dev_free(M->tau);
+  apply_ws_free(M->ws);
   dev_free(M->w_dev);
   dev_free(M->w_best);
-  red_free(M->red);
   delete M;
 }
 

@@ -33,6 +33,18 @@ struct ColPtr {
 struct TrainState;  // train.cu
 struct Server;      // serve.cu
 
+// Mutable scratch of one GNP application: hidden ping-pong blocks (n x 16 float32 each,
+// also used as bfloat16), the norm tau and the reduction scratch.  A model owns one;
+// a server slot owns another, so that one model may serve several concurrent solves.
+struct ApplyWs {
+  void* H[2] = {nullptr, nullptr};
+  double* tau = nullptr;
+  RedScratch red;
+};
+int apply_ws_alloc(ApplyWs& ws, int n);
+void apply_ws_free(ApplyWs& ws);
+inline size_t apply_ws_bytes(int n) { return (size_t)n * 16 * 4 * 2 + 16 + (size_t)4 * NUM_SMS_GB300 * 8 + 8; }
+
 // CSC (transpose) of a matrix, built on the device once (train and gamma use it).
 int mat_build_csc(gnp_mat* A, cudaStream_t st);
 
@@ -52,9 +64,7 @@ struct gnp_model {
   bool host_stale = false;        // device weights changed by training
   float* w_dev = nullptr;         // [count] training copy
   float* w_best = nullptr;        // [count] best-loss snapshot
-  void* H[2] = {nullptr, nullptr};  // apply ping-pong hidden blocks (n*16 float32 each)
-  double* tau = nullptr;          // device scalar ||v||
-  gnp::RedScratch red;            // apply reductions
+  gnp::ApplyWs ws;                // the model's own apply scratch
   gnp::TrainState* train = nullptr;
   unsigned long long version = 1; // bumped whenever weights or hprec change
 };
@@ -68,7 +78,8 @@ namespace gnp {
 // ev (may be null): 2*L events; ev[2l] / ev[2l+1] are recorded on `st` just before /
 // after the launch of layer l's Res-GCONV kernel (the timing of the hot kernel).
 int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                 const int* ctl, cudaStream_t st, cudaEvent_t* ev = nullptr);
+                 const int* ctl, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                 const ApplyWs* ws = nullptr);
 
 // Make the host copy of the weights current (after training).
 int model_sync_host(gnp_model* M);
@@ -78,6 +89,8 @@ int apply_prepare(gnp_model* M);
 unsigned long long model_version(const gnp_model* M);
 int gamma_launch(gnp_mat* A, double* gamma_dev, cudaStream_t st);
 void solver_free(Solver* s);
+int solver_create(int n, int m, int maxiters, Solver** out);
+size_t solver_bytes(int n, int m, int maxiters);
 void train_reset(TrainState* t);
 void train_free(TrainState* t);
 

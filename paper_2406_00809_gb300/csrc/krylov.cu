@@ -21,67 +21,9 @@
 #include <cmath>
 #include <cstring>
 
-#include "internal.h"
+#include "solver.h"
 
 namespace gnp {
-
-// ---------------------------------------------------------------- device state
-
-enum : int {
-  FL_EST_CONV = 1,
-  FL_BREAKDOWN = 2,
-  FL_DROPPED = 4,
-  FL_NAN = 8,
-  FL_MAXIT = 16,
-  FL_FULL = 32,
-};
-
-struct DevState {
-  int j;        // current Arnoldi step within the cycle   (ctl[0])
-  int active;   // 1 while the cycle runs                    (ctl[1])
-  int iters;    // Arnoldi steps so far
-  int maxiters;
-  int m;        // restart length
-  int jj;       // columns used by the cycle-end update
-  int flags;
-  int last_flags;  // flags of the cycle that just ended (kept by k_residual)
-  int last_jj;     // columns that cycle used
-  int pad;
-  double bnorm, tol, rtol, beta, vscale, wnorm0, hn, res_est;
-};
-
-constexpr double BREAKDOWN_REL = 1e-14;
-
-struct Solver {
-  int n = 0, m_cap = 0, maxit_cap = -1;
-  double* V = nullptr;   // [n*(m+1)] column-major basis
-  float* Z = nullptr;    // [n*m] preconditioned directions
-  double* w = nullptr;   // [n]
-  DevState* st = nullptr;
-  DevState* st_host = nullptr;  // pinned mirror
-  double* H = nullptr;   // [(m+1)*m] unrotated H_bar of the current cycle
-  double* R = nullptr;   // [(m+1)*m] rotated (upper triangular part used)
-  double* cs = nullptr;
-  double* sn = nullptr;
-  double* g = nullptr;   // [m+1]
-  double* h1 = nullptr;  // [m+2]
-  double* h2 = nullptr;  // [m+2]
-  double* hist = nullptr;  // [maxiters+1]
-  RedScratch red;
-  // captured restart cycle
-  cudaGraphExec_t gexec = nullptr;
-  const void* g_model = nullptr;
-  unsigned long long g_version = 0;
-  int g_m = 0, g_hprec = -1;
-  const double* g_b = nullptr;
-  double* g_x = nullptr;
-  cudaStream_t g_stream = nullptr;
-  cudaStream_t own = nullptr;  // used when the caller passes the legacy default stream
-  // optional timing of the Res-GCONV launches: events[(j*L + l)*2 + {0,1}]
-  std::vector<cudaEvent_t> events;
-  int ev_L = 0, ev_m = 0;
-  bool g_prof = false;
-};
 
 static bool g_profile_gconv = false;
 
@@ -117,32 +59,33 @@ void solver_free(Solver* s) {
   delete s;
 }
 
-static int solver_ensure(gnp_mat* A, int m, int maxiters) {
-  Solver* s = A->solver;
-  const int n = A->n;
-  if (s && s->m_cap >= m && s->maxit_cap >= maxiters) return GNP_OK;
-  int m_new = std::max(m, s ? s->m_cap : 0);
-  int it_new = std::max(maxiters, s ? s->maxit_cap : 0);
-  solver_free(s);
-  A->solver = nullptr;
-  s = new Solver();
+size_t solver_bytes(int n, int m, int maxiters) {
+  const size_t maxb = (size_t)std::max(red_blocks(n), (n + TILE - 1) / TILE);
+  return (size_t)n * (m + 1) * 8 + (size_t)n * m * 4 + (size_t)n * 8 + sizeof(DevState) +
+         (size_t)(m + 1) * m * 8 * 2 + (size_t)(4 * m + 8) * 8 + (size_t)(maxiters + 1) * 8 +
+         maxb * (m + 2) * 8 + 8;
+}
+
+int solver_create(int n, int m, int maxiters, Solver** out) {
+  *out = nullptr;
+  Solver* s = new Solver();
   s->n = n;
   int e = GNP_OK;
   do {
-    if ((e = dev_alloc(&s->V, (size_t)n * (m_new + 1))) != GNP_OK) break;
-    if ((e = dev_alloc(&s->Z, (size_t)n * m_new)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->V, (size_t)n * (m + 1))) != GNP_OK) break;
+    if ((e = dev_alloc(&s->Z, (size_t)n * m)) != GNP_OK) break;
     if ((e = dev_alloc(&s->w, (size_t)n)) != GNP_OK) break;
     if ((e = dev_alloc(&s->st, 1)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->H, (size_t)(m_new + 1) * m_new)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->R, (size_t)(m_new + 1) * m_new)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->cs, (size_t)m_new)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->sn, (size_t)m_new)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->g, (size_t)m_new + 1)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->h1, (size_t)m_new + 2)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->h2, (size_t)m_new + 2)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->hist, (size_t)it_new + 1)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->H, (size_t)(m + 1) * m)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->R, (size_t)(m + 1) * m)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->cs, (size_t)m)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->sn, (size_t)m)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->g, (size_t)m + 1)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->h1, (size_t)m + 2)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->h2, (size_t)m + 2)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->hist, (size_t)maxiters + 1)) != GNP_OK) break;
     const int maxb = std::max(red_blocks(n), (n + TILE - 1) / TILE);
-    if ((e = red_alloc(s->red, maxb, m_new + 2)) != GNP_OK) break;
+    if ((e = red_alloc(s->red, maxb, m + 2)) != GNP_OK) break;
     if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) {
       set_error("cudaStreamCreate failed");
       e = GNP_ERR_CUDA;
@@ -158,10 +101,20 @@ static int solver_ensure(gnp_mat* A, int m, int maxiters) {
     solver_free(s);
     return e;
   }
-  s->m_cap = m_new;
-  s->maxit_cap = it_new;
-  A->solver = s;
+  s->m_cap = m;
+  s->maxit_cap = maxiters;
+  *out = s;
   return GNP_OK;
+}
+
+static int solver_ensure(gnp_mat* A, int m, int maxiters) {
+  Solver* s = A->solver;
+  if (s && s->m_cap >= m && s->maxit_cap >= maxiters) return GNP_OK;
+  const int m_new = std::max(m, s ? s->m_cap : 0);
+  const int it_new = std::max(maxiters, s ? s->maxit_cap : 0);
+  solver_free(s);
+  A->solver = nullptr;
+  return solver_create(A->n, m_new, it_new, &A->solver);
 }
 
 // ---------------------------------------------------------------- SpMV traits
@@ -480,8 +433,8 @@ int spmv_launch(const gnp_mat* A, const double* x, const float* xf, double* y, c
 }
 
 // Enqueue one restart cycle: m Arnoldi steps, x update, residual.
-static int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, double* x,
-                        cudaStream_t st, bool prof) {
+int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, double* x,
+                 cudaStream_t st, bool prof, const ApplyWs* ws) {
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
@@ -492,7 +445,7 @@ static int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double
       ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
       ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
       cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
-      GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev));
+      GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws));
       k_spmv_tile<float><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, n, ctl);
     } else {
       k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
@@ -575,6 +528,50 @@ int arnoldi_basis(gnp_mat* A, const double* v1, int m, double* V_out, double* Hb
   return GNP_OK;
 }
 
+int solve_init_launch(const gnp_mat* A, Solver* S, const double* b, double* x, double rtol, int maxiters,
+                      int m, cudaStream_t st) {
+  const int n = A->n;
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  DevState init{};
+  init.maxiters = maxiters;
+  init.m = m;
+  init.rtol = rtol;
+  memcpy(S->st_host, &init, sizeof(DevState));
+  GNP_TRY_CUDA(cudaMemcpyAsync(S->st, S->st_host, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  k_bnorm<<<nb, RED_THREADS, 0, st>>>(b, n, S->st, S->red.partials, S->red.counter);
+  k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
+                                  S->red.partials, S->red.counter);
+  return check_launch("solve init");
+}
+
+bool cycle_after(const DevState& hs, double beta_prev, int maxiters, CycleCtl& c, int* status) {
+  if ((hs.last_flags & FL_NAN) || !std::isfinite(hs.beta)) {
+    *status = GNP_ERR_NAN;
+    return true;
+  }
+  if (hs.beta <= hs.tol) {
+    *status = GNP_OK;
+    return true;
+  }
+  c.mism = (hs.last_flags & FL_EST_CONV) ? c.mism + 1 : 0;
+  c.stagn = (hs.beta >= beta_prev) ? c.stagn + 1 : 0;
+  if (c.mism >= 3) {
+    *status = GNP_ERR_RESIDUAL_MISMATCH;
+    return true;
+  }
+  if (c.stagn >= 2) {
+    *status = GNP_ERR_STAGNATION;
+    return true;
+  }
+  ++c.restarts;
+  if (hs.iters >= maxiters) {
+    *status = GNP_ERR_NOT_CONVERGED;
+    return true;
+  }
+  return false;
+}
+
 static bool graphs_enabled() {
   const char* e = getenv("GNP_NO_GRAPH");
   return !(e && e[0] == '1');
@@ -611,24 +608,14 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
-  DevState init{};
-  init.maxiters = maxiters;
-  init.m = restart;
-  init.rtol = rtol;
-  memcpy(S->st_host, &init, sizeof(DevState));
-  GNP_TRY_CUDA(cudaMemcpyAsync(S->st, S->st_host, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  k_bnorm<<<nb, RED_THREADS, 0, st>>>(b, n, S->st, S->red.partials, S->red.counter);
-  k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
-                                  S->red.partials, S->red.counter);
+  GNP_TRY(solve_init_launch(A, S, b, x, rtol, maxiters, restart, st));
   GNP_TRY(check_launch("fgmres init"));
   GNP_TRY(read_state(S, st));
   int status = GNP_OK;
-  int restarts = 0;
+  CycleCtl ctl_c;
   const bool prof = g_profile_gconv && M != nullptr && M->cfg.L > 0;
   double gconv_ms = 0.0;
   long long gconv_launches = 0;
-  int cycles = 0;
-  int stagn = 0, mism = 0;
   DevState hs = *S->st_host;
   if (hs.bnorm == 0.0) {
     GNP_TRY_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
@@ -650,7 +637,7 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
           S->gexec = nullptr;
           cudaGraph_t graph;
           GNP_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-          int ls = launch_cycle(A, S, M, restart, b, x, st, prof);
+          int ls = launch_cycle(A, S, M, restart, b, x, st, prof, nullptr);
           cudaError_t ce = cudaStreamEndCapture(st, &graph);
           if (ls != GNP_OK) return ls;
           if (ce != cudaSuccess) {
@@ -675,10 +662,10 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
         }
         GNP_TRY_CUDA(cudaGraphLaunch(S->gexec, st));
       } else {
-        GNP_TRY(launch_cycle(A, S, M, restart, b, x, st, prof));
+        GNP_TRY(launch_cycle(A, S, M, restart, b, x, st, prof, nullptr));
       }
       const int iters_before = hs.iters;
-      ++cycles;
+      ++ctl_c.cycles;
       GNP_TRY(read_state(S, st));
       hs = *S->st_host;
       if (prof) {
@@ -692,38 +679,19 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
             ++gconv_launches;
           }
       }
-      if ((hs.last_flags & FL_NAN) || !std::isfinite(hs.beta)) {
-        status = GNP_ERR_NAN;
-        break;
-      }
-      if (hs.beta <= hs.tol) break;
-      mism = (hs.last_flags & FL_EST_CONV) ? mism + 1 : 0;
-      stagn = (hs.beta >= beta_prev) ? stagn + 1 : 0;
-      if (mism >= 3) {
-        status = GNP_ERR_RESIDUAL_MISMATCH;
-        break;
-      }
-      if (stagn >= 2) {
-        status = GNP_ERR_STAGNATION;
-        break;
-      }
-      ++restarts;
-      if (hs.iters >= maxiters) {
-        status = GNP_ERR_NOT_CONVERGED;
-        break;
-      }
+      if (cycle_after(hs, beta_prev, maxiters, ctl_c, &status)) break;
     }
   }
   GNP_TRY_CUDA(cudaStreamSynchronize(st));
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) {
     info->iters = hs.iters;
-    info->restarts = restarts;
+    info->restarts = ctl_c.restarts;
     info->status = status;
     info->seconds = secs;
     info->gconv_ms = gconv_ms;
     info->gconv_launches = (int)gconv_launches;
-    info->cycles = cycles;
+    info->cycles = ctl_c.cycles;
     const double bn = hs.bnorm > 0.0 ? hs.bnorm : 1.0;
     info->rel_res_true = hs.bnorm > 0.0 ? hs.beta / bn : 0.0;
     info->rel_res_est = hs.iters > 0 ? hs.res_est / bn : info->rel_res_true;

@@ -46,6 +46,15 @@ class _SolveInfo(C.Structure):
                 ("gconv_ms", C.c_double)]
 
 
+class _ServerConfig(C.Structure):
+    _fields_ = [("max_bytes", C.c_size_t), ("max_active", C.c_int), ("restart", C.c_int)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("used_bytes", C.c_size_t),
+                ("rounds", C.c_longlong), ("completed", C.c_longlong), ("max_active_seen", C.c_longlong)]
+
+
 _lib = None
 
 
@@ -87,6 +96,12 @@ def lib():
         "gnp_philox4x32_10": (i, [vp, C.c_uint, C.c_uint, i, vp, vp]),
         "fgmres_solve": (i, [vp, vp, vp, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
         "gnp_profile_gconv": (i, [i]),
+        "gnp_server_create": (i, [C.POINTER(_ServerConfig), pp]),
+        "gnp_server_submit": (i, [vp, vp, vp, vp, vp, d, i, C.POINTER(C.c_longlong)]),
+        "gnp_server_poll": (i, [vp, C.c_longlong, C.POINTER(_SolveInfo)]),
+        "gnp_server_wait": (i, [vp, C.c_longlong, d, C.POINTER(_SolveInfo)]),
+        "gnp_server_stats": (i, [vp, C.POINTER(_ServerStats)]),
+        "gnp_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name, None)
@@ -390,3 +405,63 @@ def gnp_function(M: Model):
             return g, None
 
     return GnpFunction
+
+
+# --------------------------------------------------------------------- server
+
+class Server:
+    """Continuous-batching solve server (gnp_server_*).  Keeps the buffers of every
+    submitted request alive until it is collected."""
+
+    def __init__(self, max_bytes: int, max_active: int = 64, restart: int = 30):
+        cfg = _ServerConfig(max_bytes, max_active, restart)
+        out = C.c_void_p()
+        _check(lib().gnp_server_create(C.byref(cfg), C.byref(out)))
+        self.h = out
+        self._keep = {}
+
+    def submit(self, A: Mat, M: "Model | None", b, x, rtol=1e-8, maxiters=1000) -> int:
+        import torch
+        t = C.c_longlong()
+        _check(lib().gnp_server_submit(self.h, A.h, M.h if M is not None else None,
+                                       _dptr(b, torch.float64, "b"), _dptr(x, torch.float64, "x"),
+                                       rtol, maxiters, C.byref(t)))
+        self._keep[t.value] = (A, M, b, x)
+        return t.value
+
+    def _result(self, st, info):
+        return SolveInfo(st, info.iters, info.restarts, info.rel_res_est, info.rel_res_true, info.seconds,
+                         cycles=info.cycles)
+
+    def poll(self, ticket: int):
+        """None while queued or running, else the SolveInfo (seconds = latency)."""
+        info = _SolveInfo()
+        st = lib().gnp_server_poll(self.h, ticket, C.byref(info))
+        if st == 11:  # GNP_ERR_BUSY
+            return None
+        if st == 1:
+            _check(st)
+        self._keep.pop(ticket, None)
+        return self._result(st, info)
+
+    def wait(self, ticket: int, timeout: float = 600.0):
+        info = _SolveInfo()
+        st = lib().gnp_server_wait(self.h, ticket, timeout, C.byref(info))
+        if st in (1, 9):
+            _check(st)
+        self._keep.pop(ticket, None)
+        return self._result(st, info)
+
+    def stats(self) -> dict:
+        s = _ServerStats()
+        _check(lib().gnp_server_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gnp_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()

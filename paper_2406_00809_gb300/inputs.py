@@ -158,9 +158,11 @@ def powerlaw(n: int, mean: float = 12.0, kmax: int = 2000, log10_scale_span: flo
     rows = np.repeat(np.arange(n, dtype=np.int64), off)
     cols = rng.integers(0, n - 1, size=total, dtype=np.int64)
     cols = cols + (cols >= rows)  # skip the diagonal
-    # drop repeated (row, col) pairs
-    key = rows * n + cols
-    key = np.unique(key)
+    # drop repeated (row, col) pairs: sort the keys once, keep first occurrences
+    key = np.sort(rows * n + cols)
+    keep = np.ones(key.size, dtype=bool)
+    keep[1:] = key[1:] != key[:-1]
+    key = key[keep]
     rows = key // n
     cols = key % n
     vals = rng.standard_normal(rows.shape[0])
@@ -172,7 +174,19 @@ def powerlaw(n: int, mean: float = 12.0, kmax: int = 2000, log10_scale_span: flo
     scale = 10.0 ** rng.uniform(0.0, log10_scale_span, size=n)
     vals = vals * scale[rows]
     perm = rng.permutation(n)
-    return _from_coo(n, perm[rows], perm[cols], vals)
+    return _from_coo_fast(n, perm[rows], perm[cols], vals)
+
+
+def _from_coo_fast(n, rows, cols, vals) -> CSR:
+    """CSR from unique (row, col) pairs via one sort of the combined key."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    order = np.argsort(rows * n + cols, kind="stable")
+    rows, cols, vals = rows[order], cols[order], np.asarray(vals, dtype=np.float64)[order]
+    counts = np.bincount(rows, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return CSR(n, row_ptr.astype(np.int32), cols.astype(np.int32), vals)
 
 
 def gaussian(n: int, seed: int, batch: int | None = None) -> np.ndarray:

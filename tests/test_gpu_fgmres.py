@@ -83,10 +83,10 @@ def test_identity_converges_and_status(gnp):
 @pytest.mark.parametrize("kind", ["poisson32", "convdiff32", "powerlaw"])
 def test_gnp_preconditioned_history_matches_oracle(gnp, kind):
     """Untrained (Gaussian-init) GNP: FGMRES runs a fixed budget of steps on GPU and in
-    the oracle.  The first cycle agrees to 1e-5; later the untrained M gives nearly
-    collinear z_j, whose new directions are of the size of float32 rounding, so the
-    histories drift apart by as much as rounding the oracle's own z to float32 does
-    (about 1%): checked at 5e-2."""
+    the oracle.  The first 10 steps agree to 1e-5.  After that the untrained M gives
+    nearly collinear z_j whose new directions are of the size of float32 rounding, so
+    the history is as sensitive as rounding the oracle's own z to float32 makes it; the
+    GPU's deviation must stay within 3x that perturbation's deviation (+1e-3)."""
     import torch
     if kind == "poisson32":
         A, L, m, maxit = I.poisson2d(32), 4, 10, 60
@@ -102,11 +102,16 @@ def test_gnp_preconditioned_history_matches_oracle(gnp, kind):
     info = gnp.fgmres_solve(Mt, dev(b), x, Mg, restart=m, rtol=1e-30, maxiters=maxit)
     Ah = G.normalise(A.to_scipy())
     P = G.unpack(blob, L)
-    xr, ir = K.fgmres(A.to_scipy(), b, lambda v: G.forward(Ah, v, P, 0), m=m, rtol=1e-30, maxiters=maxit)
+    M64 = lambda v: G.forward(Ah, v, P, 0)  # noqa: E731
+    M32 = lambda v: G.forward(Ah, v, P, 0).astype(np.float32).astype(np.float64)  # noqa: E731
+    xr, ir = K.fgmres(A.to_scipy(), b, M64, m=m, rtol=1e-30, maxiters=maxit)
+    _, i32 = K.fgmres(A.to_scipy(), b, M32, m=m, rtol=1e-30, maxiters=maxit)
     assert info.status == ir["status"]
     assert info.iters == ir["iters"]
     h = np.asarray(ir["history"])
-    np.testing.assert_allclose(info.history[:m + 1], h[:m + 1], rtol=1e-5)
-    np.testing.assert_allclose(info.history, h, rtol=5e-2)
+    np.testing.assert_allclose(info.history[:11], h[:11], rtol=1e-5)
+    sens = float(np.max(np.abs(np.asarray(i32["history"]) - h) / h))
+    dev_gpu = float(np.max(np.abs(info.history - h) / h))
+    assert dev_gpu <= 3 * sens + 1e-3, (dev_gpu, sens)
     r = b - A.to_scipy() @ x.cpu().numpy()
     assert abs(np.linalg.norm(r) / np.linalg.norm(b) - info.rel_res_true) <= 1e-10
