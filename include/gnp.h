@@ -193,6 +193,11 @@ int gnp_train_step(gnp_model* M, float* loss_out, void* stream);
  * (host, may be NULL) receives the best loss seen.  Synchronous. */
 int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream);
 
+/* Free the training state (saved activations, optimiser, sampler; about
+ * (2L + 10) * n * B * 64 bytes) after copying the best-loss weights to the applied
+ * set.  Training again starts a fresh optimiser.  Synchronous. */
+int gnp_train_release(gnp_model* M);
+
 /* Replace the training weights from device memory (float32 [count], count =
  * gnp_weight_count(L)); also becomes the applied (best) snapshot.  Asynchronous. */
 int gnp_set_weights_device(gnp_model* M, const float* w_dev, int count, void* stream);

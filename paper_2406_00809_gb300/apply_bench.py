@@ -86,15 +86,16 @@ def main():
             info = gnp.fgmres_solve(Mt, b, x, M, restart=min(50, a.iters), rtol=1e-30, maxiters=a.iters,
                                     stream=stream, history=False)
             gnp.gnp_profile_gconv(False)
-            g_us = info.gconv_ms / max(info.gconv_launches, 1) * 1e3
+            g_us = info.gconv_ms / info.gconv_launches * 1e3 if info.gconv_launches else None
             # plain layers move `layer` bytes; the decoder-fused last layer fewer
             last = layer - n * 16 * hb + 4 * n
             avg_bytes = ((L - 1) * layer + last) / L
+            g_gbs = avg_bytes / (g_us * 1e-6) / 1e9 if g_us else None
             out = {"workload": a.workload, "n": n, "nnz": nnz, "L": L, "hprec": p,
                    "apply_ms": t_apply * 1e3, "apply_GBs": tot / t_apply / 1e9,
                    "apply_frac": tot / t_apply / 1e9 / peak,
-                   "gconv_us": g_us, "gconv_GBs": avg_bytes / (g_us * 1e-6) / 1e9,
-                   "gconv_frac": avg_bytes / (g_us * 1e-6) / 1e9 / peak,
+                   "gconv_us": g_us, "gconv_GBs": g_gbs,
+                   "gconv_frac": g_gbs / peak if g_gbs else None,
                    "gconv_launches": info.gconv_launches, "layer_bytes": layer,
                    "peak_GBs": peak, "gen_s": gen_s}
             print(json.dumps(out), flush=True)

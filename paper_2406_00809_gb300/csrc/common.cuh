@@ -67,6 +67,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // ------------------------------------------------------------ tiling constants
 
 constexpr int TILE = 256;            // rows per tile = threads per tile-kernel block
+constexpr int NNZ_PAD = 4;           // index/value arrays carry 4 spare (zero) entries
 constexpr int RED_THREADS = 256;     // threads of the streaming reduction kernels
 constexpr int NUM_SMS_GB300 = 152;
 
@@ -81,9 +82,11 @@ struct RedScratch {
 int red_alloc(RedScratch& r, int max_blocks, int max_k);
 void red_free(RedScratch& r);
 
-// Number of blocks of the grid-stride reduction kernels for a vector of length n.
+// Number of blocks of the grid-stride reduction kernels for a vector of length n: one
+// row per thread up to four blocks per SM, so that small vectors still spread over
+// every SM (latency, not bandwidth, bounds them).
 inline int red_blocks(long long n) {
-  long long per = (long long)RED_THREADS * 4;
+  long long per = (long long)RED_THREADS;
   long long b = (n + per - 1) / per;
   if (b < 1) b = 1;
   if (b > 4 * NUM_SMS_GB300) b = 4 * NUM_SMS_GB300;
@@ -194,27 +197,34 @@ __device__ __forceinline__ void reduce_partials(const double* partials, int nblo
 // W = G*NV entries), STRIDE = smem row stride of s_agg, scalar acc type `acc`,
 // value type `val_t`, and a loader TR::load(X, c, q, out[NV]) of lane q's part of x_c.
 
-template <class TR>
+// ROWS rows per tile (<= TILE, the block's thread count): fewer rows than threads give
+// each slot fewer nonzeros, i.e. a shorter chain of dependent loads per block.
+template <class TR, int ROWS = TILE>
 struct TileSmem {
   static constexpr int G = TR::G;
   static constexpr int NV = TR::NV;
   static constexpr int S = TILE / G;
   static constexpr int W = G * NV;
+  static constexpr int R = ROWS;
   using acc = typename TR::acc;
-  int rp[TILE + 1];
+  int rp[ROWS + 1];
   int firstrow[S];
   acc cf[S][W];
   acc cl[S][W];
-  acc agg[TILE * TR::STRIDE];
+  acc agg[ROWS * TR::STRIDE];
 };
 
+// Slot of nonzero e: the largest s with floor(s E / S) <= e - E0 (32-bit arithmetic
+// whenever E * S fits, which is every tile of fewer than 2^24 nonzeros).
 __device__ __forceinline__ int slot_of(int e, int E0, int E, int S) {
-  long long ep = (long long)(e - E0) + 1;
-  return (int)((ep * S + E - 1) / E) - 1;
+  const unsigned ep = (unsigned)(e - E0) + 1u;
+  if ((unsigned long long)E * (unsigned)S < (1ull << 32))
+    return (int)((ep * (unsigned)S + (unsigned)E - 1u) / (unsigned)E) - 1;
+  return (int)(((unsigned long long)ep * S + E - 1) / E) - 1;
 }
 
-template <class TR>
-__device__ __forceinline__ void tile_flush(TileSmem<TR>& sm, int s, int q, int fr, int r, int rstart,
+template <class TR, class SM>
+__device__ __forceinline__ void tile_flush(SM& sm, int s, int q, int fr, int r, int rstart,
                                            int rend, int a, int b,
                                            const typename TR::acc (&acc)[TR::NV]) {
   typename TR::acc* dst;
@@ -230,8 +240,8 @@ __device__ __forceinline__ void tile_flush(TileSmem<TR>& sm, int s, int q, int f
 
 // Requires sm.rp[0..rows] loaded and a __syncthreads() before the call.  Ends with
 // no barrier; the caller syncs before reading agg/cf/cl.
-template <class TR>
-__device__ __forceinline__ void tile_gather(TileSmem<TR>& sm, int rows, const int* __restrict__ col,
+template <class TR, class SM>
+__device__ __forceinline__ void tile_gather(SM& sm, int rows, const int* __restrict__ col,
                                             const typename TR::val_t* __restrict__ val,
                                             const typename TR::x_t* __restrict__ X) {
   constexpr int G = TR::G, NV = TR::NV, S = TILE / G;
@@ -261,7 +271,7 @@ __device__ __forceinline__ void tile_gather(TileSmem<TR>& sm, int rows, const in
 
   auto step = [&](int e, typename TR::val_t v, const A (&h)[NV]) {
     while (e >= rnext) {
-      tile_flush<TR>(sm, s, q, fr, r, rstart, rnext, a, b, acc);
+      tile_flush<TR, SM>(sm, s, q, fr, r, rstart, rnext, a, b, acc);
 #pragma unroll
       for (int k = 0; k < NV; ++k) acc[k] = A(0);
       ++r;
@@ -272,20 +282,42 @@ __device__ __forceinline__ void tile_gather(TileSmem<TR>& sm, int rows, const in
     for (int k = 0; k < NV; ++k) acc[k] = fma(A(v), h[k], acc[k]);
   };
 
+  // groups of 4 nonzeros; the next group's column indices and values are loaded while
+  // the current group's neighbour rows are in flight (one dependent round trip less)
   int e = a;
+  int cn[4];
+  typename TR::val_t vn[4];
+  if (e + 4 <= b) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      cn[u] = __ldg(col + e + u);
+      vn[u] = __ldg(val + e + u);
+    }
+  }
   for (; e + 4 <= b; e += 4) {
-    int c0 = __ldg(col + e), c1 = __ldg(col + e + 1), c2 = __ldg(col + e + 2), c3 = __ldg(col + e + 3);
-    typename TR::val_t v0 = __ldg(val + e), v1 = __ldg(val + e + 1), v2 = __ldg(val + e + 2),
-                       v3 = __ldg(val + e + 3);
+    int c[4];
+    typename TR::val_t v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = cn[u];
+      v[u] = vn[u];
+    }
+    if (e + 8 <= b) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cn[u] = __ldg(col + e + 4 + u);
+        vn[u] = __ldg(val + e + 4 + u);
+      }
+    }
     A h0[NV], h1[NV], h2[NV], h3[NV];
-    TR::load(X, c0, q, h0);
-    TR::load(X, c1, q, h1);
-    TR::load(X, c2, q, h2);
-    TR::load(X, c3, q, h3);
-    step(e, v0, h0);
-    step(e + 1, v1, h1);
-    step(e + 2, v2, h2);
-    step(e + 3, v3, h3);
+    TR::load(X, c[0], q, h0);
+    TR::load(X, c[1], q, h1);
+    TR::load(X, c[2], q, h2);
+    TR::load(X, c[3], q, h3);
+    step(e, v[0], h0);
+    step(e + 1, v[1], h1);
+    step(e + 2, v[2], h2);
+    step(e + 3, v[3], h3);
   }
   for (; e < b; ++e) {
     int c0 = __ldg(col + e);
@@ -294,13 +326,13 @@ __device__ __forceinline__ void tile_gather(TileSmem<TR>& sm, int rows, const in
     TR::load(X, c0, q, h0);
     step(e, v0, h0);
   }
-  tile_flush<TR>(sm, s, q, fr, r, rstart, rnext, a, b, acc);
+  tile_flush<TR, SM>(sm, s, q, fr, r, rstart, rnext, a, b, acc);
 }
 
 // After the gather and a __syncthreads(): the complete sum of row t (W entries) for
 // the epilogue thread t < rows.  Entries [k0, k0+cnt) are returned in out.
-template <class TR, int CNT>
-__device__ __forceinline__ void tile_row_sum(const TileSmem<TR>& sm, int t, int k0,
+template <class TR, int CNT, class SM>
+__device__ __forceinline__ void tile_row_sum(const SM& sm, int t, int k0,
                                              typename TR::acc (&out)[CNT]) {
   using A = typename TR::acc;
   constexpr int S = TILE / TR::G;
@@ -310,7 +342,7 @@ __device__ __forceinline__ void tile_row_sum(const TileSmem<TR>& sm, int t, int 
   if (rs == re) return;
   const int E0 = sm.rp[0];
   // rows is implied by the caller; E from the last row pointer of the tile
-  const int E = sm.rp[TILE] - E0;  // caller pads rp beyond `rows` with the last value
+  const int E = sm.rp[SM::R] - E0;  // caller pads rp beyond `rows` with the last value
   const int s_lo = slot_of(rs, E0, E, S);
   const int s_hi = slot_of(re - 1, E0, E, S);
   if (s_lo == s_hi) {
@@ -329,10 +361,10 @@ __device__ __forceinline__ void tile_row_sum(const TileSmem<TR>& sm, int t, int 
 
 // Load the row pointers of the tile into smem, padding entries past `rows` with the
 // tile's last pointer so that sm.rp[TILE] is the end of the tile's nnz range.
-template <class TR>
-__device__ __forceinline__ void tile_load_rp(TileSmem<TR>& sm, const int* __restrict__ rp, int r0,
+template <class TR, class SM>
+__device__ __forceinline__ void tile_load_rp(SM& sm, const int* __restrict__ rp, int r0,
                                              int rows) {
-  for (int i = threadIdx.x; i <= TILE; i += blockDim.x)
+  for (int i = threadIdx.x; i <= SM::R; i += blockDim.x)
     sm.rp[i] = __ldg(rp + r0 + (i < rows ? i : rows));
 }
 

@@ -15,6 +15,7 @@
 // Hidden blocks are node-major (16 contiguous values per node), float32 or bfloat16.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 
 #include "internal.h"
@@ -161,20 +162,35 @@ __device__ __forceinline__ void tile_copy(uint32_t* stile, HT* g, int r0, int ro
 
 // ---------------------------------------------------------------- k_encode
 
+// Standalone apply: u = (sqrt(n)/tau) v with tau from k_vnorm.  Inside FGMRES
+// (vscale != null): v_j = w / h is unit-norm by construction, so the encoder divides the
+// stored w by the device scalar h, writes v_j back in place and uses tau = 1 (it stores
+// tau = 1 for the decoder's back-scaling).
 template <class HT>
 __global__ void __launch_bounds__(TILE)
-k_encode(ColPtr vp, const double* __restrict__ tau, const int* __restrict__ ctl, int n,
-         double sqrt_n, HT* __restrict__ H, const __grid_constant__ EncW ew) {
+k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau, const int* __restrict__ ctl,
+         int n, double sqrt_n, HT* __restrict__ H, const __grid_constant__ EncW ew) {
   if (ctl && !ctl[1]) return;
   __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
-  const double* v = static_cast<const double*>(colptr(vp));
+  double* v = static_cast<double*>(colptr(vp));
   const int r0 = blockIdx.x * TILE;
   const int rows = min(TILE, n - r0);
   const int t = threadIdx.x;
-  const double tv = *tau;
-  const double f = tv > 0.0 ? sqrt_n / tv : 0.0;
+  double f;
+  if (vscale) {
+    f = sqrt_n;
+    if (blockIdx.x == 0 && t == 0) *tau = 1.0;
+  } else {
+    const double tv = *tau;
+    f = tv > 0.0 ? sqrt_n / tv : 0.0;
+  }
   if (t < rows) {
-    float u = (float)(v[r0 + t] * f);
+    double x = v[r0 + t];
+    if (vscale) {
+      x = x / *vscale;
+      v[r0 + t] = x;
+    }
+    float u = (float)(x * f);
     float h[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) h[c] = ew.b2[c];
@@ -191,11 +207,23 @@ k_encode(ColPtr vp, const double* __restrict__ tau, const int* __restrict__ ctl,
 }
 
 // ---------------------------------------------------------------- k_gconv
+//
+// One block per 256 consecutive rows.  Its nonzeros are split evenly over slots of G
+// lanes (4 for float32 rows of 64 bytes, 2 for bfloat16 rows of 32 bytes); a slot walks
+// its nonzero range loading each neighbour's row with one 16-byte load per lane, four
+// nonzeros in flight; rows split between slots leave partial sums that the epilogue adds
+// in slot order (common.cuh, tile_gather).  The block's own hidden rows come in with one
+// coalesced tile copy.  Epilogue: one thread per row, U and W as uniform constant-bank
+// operands; the row is staged in shared memory and the tile written back with coalesced
+// stores, or (last layer) the decoder and tau/sqrt(n) produce z directly.
+
+// Rows per Res-GCONV block (its TILE threads form TILE/G slots over these rows' nonzeros).
+constexpr int GROWS = 256;
 
 template <class HT>
 struct GconvSmem {
-  TileSmem<typename HTraits<HT>::TR> g;
-  __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
+  TileSmem<typename HTraits<HT>::TR, GROWS> g;
+  __align__(16) uint32_t stile[GROWS * HTraits<HT>::SROW];
 };
 
 // Layer epilogue for one row: out = ReLU(h U + agg W) (paper) or h + ReLU(agg W).
@@ -252,8 +280,8 @@ k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __
   if (ctl && !ctl[1]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   GconvSmem<HT>& sm = *reinterpret_cast<GconvSmem<HT>*>(smraw);
-  const int r0 = blockIdx.x * TILE;
-  const int rows = min(TILE, n - r0);
+  const int r0 = blockIdx.x * GROWS;
+  const int rows = min(GROWS, n - r0);
   float o[16];
   gconv_body<HT, FORM>(sm, rp, col, valhat, Hin, r0, rows, lw, o);
   // own row was read from stile by this thread only: safe to overwrite in place
@@ -284,8 +312,8 @@ k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float
   if (ctl && !ctl[1]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   GconvSmem<HT>& sm = *reinterpret_cast<GconvSmem<HT>*>(smraw);
-  const int r0 = blockIdx.x * TILE;
-  const int rows = min(TILE, n - r0);
+  const int r0 = blockIdx.x * GROWS;
+  const int rows = min(GROWS, n - r0);
   float o[16];
   gconv_body<HT, FORM>(sm, rp, col, valhat, Hin, r0, rows, lw, o);
   if (threadIdx.x < rows) {
@@ -366,17 +394,16 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   GNP_TRY((set_smem_attrs<HT, FORM>()));
   const int smem = (int)sizeof(GconvSmem<HT>);
   const int nt = (n + TILE - 1) / TILE;
+  const int ntg = (n + GROWS - 1) / GROWS;
   const int nb = red_blocks(n);
-  if (vscale)
-    k_vnorm<true><<<nb, RED_THREADS, 0, st>>>(v, vscale, ctl, n, W.red.partials, W.red.counter, W.tau);
-  else
+  if (!vscale)
     k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
   EncW ew;
   DecW dw;
   fill_params(M->w_host, L, ew, dw);
   HT* H0 = static_cast<HT*>(W.H[0]);
   HT* H1 = static_cast<HT*>(W.H[1]);
-  k_encode<HT><<<nt, TILE, 0, st>>>(v, W.tau, ctl, n, sqrt_n, H0, ew);
+  k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, H0, ew);
   const long long hcount = (long long)n * 16;
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, hcount);
   const int fused_last = (L > 0 && !trace) ? 1 : 0;
@@ -384,7 +411,7 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
     LayerW lw;
     fill_layer(M->w_host, l, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
-    k_gconv<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
+    k_gconv<HT, FORM><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
     if (trace)
       k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
@@ -394,8 +421,8 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
     LayerW lw;
     fill_layer(M->w_host, L - 1, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
-    k_gconv_dec<HT, FORM><<<nt, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, W.tau, sqrt_n, n,
-                                                  ctl, lw, dw);
+    k_gconv_dec<HT, FORM><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, W.tau, sqrt_n, n, ctl,
+                                                   lw, dw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
     k_decode<HT><<<nt, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
@@ -482,7 +509,7 @@ int gnp_create(const gnp_mat* Ac, const gnp_config* cfg, const float* weights_ho
   const long long nnz = A->nnz;
   double* gdev = nullptr;
   do {
-    if ((s = dev_alloc(&M->valhat, (size_t)std::max<long long>(nnz, 1))) != GNP_OK) break;
+    if ((s = dev_alloc(&M->valhat, (size_t)nnz + NNZ_PAD)) != GNP_OK) break;
     if ((s = apply_ws_alloc(M->ws, n)) != GNP_OK) break;
     if ((s = dev_alloc(&M->w_dev, (size_t)cnt)) != GNP_OK) break;
     if ((s = dev_alloc(&M->w_best, (size_t)cnt)) != GNP_OK) break;
@@ -507,6 +534,7 @@ int gnp_create(const gnp_mat* Ac, const gnp_config* cfg, const float* weights_ho
     return s;
   }
   // A_hat = A / gamma in float32 (Eq. 6)
+  cudaMemset(M->valhat + nnz, 0, sizeof(float) * NNZ_PAD);
   if (nnz > 0) k_scale_values<<<4 * NUM_SMS_GB300, 256>>>(A->val, nnz, M->gamma, M->valhat);
   s = check_launch("k_scale_values");
   if (s == GNP_OK && cudaDeviceSynchronize() != cudaSuccess) {

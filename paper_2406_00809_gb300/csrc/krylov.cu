@@ -66,8 +66,23 @@ size_t solver_bytes(int n, int m, int maxiters) {
          maxb * (m + 2) * 8 + 8;
 }
 
+template <class ZT>
+__global__ void k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevState* st,
+                          const double* __restrict__ R, const double* __restrict__ g);
+
+static int xupdate_attrs() {
+  static bool done = false;
+  if (done) return GNP_OK;
+  const int bytes = (int)sizeof(double) * GNP_MAX_RESTART * GNP_MAX_RESTART;
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_xupdate<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_xupdate<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done = true;
+  return GNP_OK;
+}
+
 int solver_create(int n, int m, int maxiters, Solver** out) {
   *out = nullptr;
+  GNP_TRY(xupdate_attrs());
   Solver* s = new Solver();
   s->n = n;
   int e = GNP_OK;
@@ -155,6 +170,84 @@ k_spmv_tile(const int* __restrict__ rp, const int* __restrict__ col, const doubl
     tile_row_sum<TR, 1>(sm, threadIdx.x, 0, s);
     y[r0 + threadIdx.x] = s[0];
   }
+}
+
+// Block-wide sum of KC values per thread, added into the block accumulators acc[k0..].
+__device__ __forceinline__ void block_accumulate(double (&a)[8], double (*sh)[32], double* acc, int kvalid);
+
+// w = A z (tile gather) fused with CGS2 pass 1: h1 = V_j^T w and ||w||^2.  Blocks loop
+// over tiles and keep their dot sums in shared memory, so the partials stay one row
+// per block (at most 4 per SM) however large n is.
+template <class XT>
+__global__ void __launch_bounds__(TILE)
+k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+           ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
+           double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
+  if (!st->active) return;
+  using TR = TrSpmv<XT>;
+  __shared__ TileSmem<TR> sm;
+  __shared__ double sacc[GNP_MAX_RESTART + 2];
+  __shared__ double shred[8][32];
+  const int j = st->j;
+  const int K = j + 2;  // h1[0..j] and ||w||^2
+  const size_t ld = (size_t)n;
+  const XT* x = static_cast<const XT*>(colptr_c(xp));
+  for (int k = threadIdx.x; k < K; k += blockDim.x) sacc[k] = 0.0;
+  const int nt = (n + TILE - 1) / TILE;
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int r0 = tile * TILE;
+    const int rows = min(TILE, n - r0);
+    __syncthreads();
+    tile_load_rp<TR>(sm, rp, r0, rows);
+    __syncthreads();
+    tile_gather<TR>(sm, rows, col, val, x);
+    __syncthreads();
+    const int t = threadIdx.x;
+    double wr = 0.0;
+    if (t < rows) {
+      double s1[1];
+      tile_row_sum<TR, 1>(sm, t, 0, s1);
+      wr = s1[0];
+      w[r0 + t] = wr;
+    }
+    for (int k0 = 0; k0 < K; k0 += 8) {
+      double a[8];
+#pragma unroll
+      for (int kc = 0; kc < 8; ++kc) {
+        const int k = k0 + kc;
+        double vk = 0.0;
+        if (t < rows && k < K) vk = (k == j + 1) ? wr : V[k * ld + r0 + t];
+        a[kc] = vk * wr;
+      }
+      block_accumulate(a, shred, sacc + k0, min(8, K - k0));
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) partials[(size_t)blockIdx.x * K + k] = sacc[k];
+  if (!last_block_arrive(counter)) return;
+  __shared__ double shtot[GNP_MAX_RESTART + 2];
+  reduce_partials(partials, gridDim.x, K, shtot);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k <= j; ++k) h1[k] = shtot[k];
+    st->wnorm0 = sqrt(shtot[j + 1]);
+    *counter = 0;
+  }
+}
+
+__device__ __forceinline__ void block_accumulate(double (&a)[8], double (*sh)[32], double* acc, int kvalid) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int kc = 0; kc < 8; ++kc) {
+    const double v = warp_sum(a[kc]);
+    if (lane == 0) sh[kc][w] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < kvalid) {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += sh[threadIdx.x][k];
+    acc[threadIdx.x] += t;
+  }
+  __syncthreads();
 }
 
 // r = b - A x -> V[:, 0], beta = ||r||; the last block restarts the cycle state.
@@ -259,8 +352,8 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
       double* __restrict__ partials, unsigned* counter) {
   if (!st->active) return;
   __shared__ double shh[GNP_MAX_RESTART + 2];
-  __shared__ double shred[KC][32];
-  __shared__ double shtot[GNP_MAX_RESTART + 2];
+  __shared__ double shred[KC][32];  // KC*32 = 256 >= GNP_MAX_RESTART: reused for sines
+  __shared__ double shtot[GNP_MAX_RESTART + 4];
   const int j = st->j;
   const size_t ld = (size_t)n;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -312,6 +405,18 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   if (!last_block_arrive(counter)) return;
   const int K = (PASS == 1) ? j + 2 : (PASS == 2 ? j + 1 : 1);
   reduce_partials(partials, gridDim.x, K, shtot);
+  if (PASS == 3) {
+    // stage the Givens inputs with all threads: column j = h1 + h2, the previous
+    // rotations (reuse shh for the cosines, shred for the sines)
+    double* scs = shh;
+    double* ssn = &shred[0][0];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) shtot[1 + i] = h1[i] + h2[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      scs[i] = cs[i];
+      ssn[i] = sn[i];
+    }
+    __syncthreads();
+  }
   if (threadIdx.x != 0) return;
   *counter = 0;
   if (PASS == 1) {
@@ -329,17 +434,16 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   const int ldh = m + 1;
   const double hn = sqrt(shtot[0]);
   st->hn = hn;
-  double col[GNP_MAX_RESTART + 2];
+  double* col = shtot + 1;  // column j, rotated in place in shared memory
+  const double* scs = shh;
+  const double* ssn = &shred[0][0];
   bool finite = isfinite(hn);
-  for (int i = 0; i <= j; ++i) {
-    col[i] = h1[i] + h2[i];
-    H[(size_t)j * ldh + i] = col[i];
-  }
+  for (int i = 0; i <= j; ++i) H[(size_t)j * ldh + i] = col[i];
   col[j + 1] = hn;
   H[(size_t)j * ldh + j + 1] = hn;
   for (int i = 0; i < j; ++i) {
-    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
-    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
+    col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
     col[i] = t;
   }
   for (int i = 0; i <= j + 1; ++i) finite = finite && isfinite(col[i]);
@@ -396,16 +500,25 @@ __global__ void __launch_bounds__(RED_THREADS)
 k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevState* st,
           const double* __restrict__ R, const double* __restrict__ g) {
   __shared__ double y[GNP_MAX_RESTART];
+  __shared__ double sg[GNP_MAX_RESTART];
+  extern __shared__ double sR[];  // jj x jj upper triangle of R, column-major, ld = jj
   const int jj = st->jj;
   if (jj == 0) return;
   const int ldh = st->m + 1;
+  // stage R and g with all threads, then one warp back-substitutes from shared memory
+  for (int t = threadIdx.x; t < jj * jj; t += blockDim.x) {
+    const int c = t / jj, r = t % jj;
+    sR[t] = (r <= c) ? R[(size_t)c * ldh + r] : 0.0;
+  }
+  for (int t = threadIdx.x; t < jj; t += blockDim.x) sg[t] = g[t];
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = jj - 1; i >= 0; --i) {
       double part = 0.0;
-      for (int k = i + 1 + lane; k < jj; k += 32) part += R[(size_t)k * ldh + i] * y[k];
+      for (int k = i + 1 + lane; k < jj; k += 32) part += sR[k * jj + i] * y[k];
       part = warp_sum(part);
-      if (lane == 0) y[i] = (g[i] - part) / R[(size_t)i * ldh + i];
+      if (lane == 0) y[i] = (sg[i] - part) / sR[i * jj + i];
       __syncwarp();
     }
   }
@@ -438,6 +551,7 @@ int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, do
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
+  const int ndot = std::min(nt, 4 * NUM_SMS_GB300);
   const int* ctl = reinterpret_cast<const int*>(S->st);
   const int* jptr = ctl;
   for (int j = 0; j < m; ++j) {
@@ -446,23 +560,24 @@ int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, do
       ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
       cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
       GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws));
-      k_spmv_tile<float><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, n, ctl);
+      k_spmv_dot<float><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st, S->h1,
+                                               S->red.partials, S->red.counter);
     } else {
       k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
       ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
-      k_spmv_tile<double><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, n, ctl);
+      k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, S->V, n, S->st, S->h1,
+                                                S->red.partials, S->red.counter);
     }
-    k_cgs<1><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->red.partials, S->red.counter);
     k_cgs<2><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
                                          S->g, S->hist, S->red.partials, S->red.counter);
     k_cgs<3><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
                                          S->g, S->hist, S->red.partials, S->red.counter);
   }
+  const int xsm = (int)sizeof(double) * m * m;
   if (M)
-    k_xupdate<float><<<nb, RED_THREADS, 0, st>>>(S->Z, x, n, S->st, S->R, S->g);
+    k_xupdate<float><<<nb, RED_THREADS, xsm, st>>>(S->Z, x, n, S->st, S->R, S->g);
   else
-    k_xupdate<double><<<nb, RED_THREADS, 0, st>>>(S->V, x, n, S->st, S->R, S->g);
+    k_xupdate<double><<<nb, RED_THREADS, xsm, st>>>(S->V, x, n, S->st, S->R, S->g);
   k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
                                   S->red.partials, S->red.counter);
   return check_launch("fgmres cycle");

@@ -243,13 +243,15 @@ int gnp_mat_create(int n, long long nnz, const int* row_ptr, const int* col, con
   cudaGetDevice(&A->device);
   int s = GNP_OK;
   if ((s = dev_alloc(&A->rp, (size_t)n + 1)) != GNP_OK ||
-      (s = dev_alloc(&A->col, (size_t)std::max<long long>(nnz, 1))) != GNP_OK ||
-      (s = dev_alloc(&A->val, (size_t)std::max<long long>(nnz, 1))) != GNP_OK) {
+      (s = dev_alloc(&A->col, (size_t)nnz + NNZ_PAD)) != GNP_OK ||
+      (s = dev_alloc(&A->val, (size_t)nnz + NNZ_PAD)) != GNP_OK) {
     gnp_mat_destroy(A);
     return s;
   }
   cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaError_t e = cudaMemcpyAsync(A->rp, row_ptr, sizeof(int) * (n + 1), kind, st);
+  cudaError_t e = cudaMemsetAsync(A->col + nnz, 0, sizeof(int) * NNZ_PAD, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->val + nnz, 0, sizeof(double) * NNZ_PAD, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A->rp, row_ptr, sizeof(int) * (n + 1), kind, st);
   if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->col, col, sizeof(int) * nnz, kind, st);
   if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->val, val, sizeof(double) * nnz, kind, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -1108,6 +1108,14 @@ int gnp_train_step(gnp_model* M, float* loss_out, void* stream) {
   return GNP_OK;
 }
 
+int gnp_train_release(gnp_model* M) {
+  GNP_REQUIRE(M, "gnp_train_release: null model");
+  GNP_TRY(model_sync_host(M));
+  train_free(M->train);
+  M->train = nullptr;
+  return GNP_OK;
+}
+
 int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream) {
   GNP_REQUIRE(M && steps >= 0, "gnp_train: bad argument");
   cudaStream_t st = as_stream(stream);

@@ -93,6 +93,7 @@ def lib():
         "gnp_train_step": (i, [vp, C.POINTER(f), vp]),
         "gnp_train": (i, [vp, i, C.POINTER(f), vp]),
         "gnp_set_weights_device": (i, [vp, vp, i, vp]),
+        "gnp_train_release": (i, [vp]),
         "gnp_philox4x32_10": (i, [vp, C.c_uint, C.c_uint, i, vp, vp]),
         "fgmres_solve": (i, [vp, vp, vp, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
         "gnp_profile_gconv": (i, [i]),
@@ -307,6 +308,10 @@ def gnp_train_step(M: Model, stream=None) -> float:
     loss = C.c_float(0.0)
     _check(lib().gnp_train_step(M.h, C.byref(loss), _stream(stream)))
     return loss.value
+
+
+def gnp_train_release(M: Model):
+    _check(lib().gnp_train_release(M.h))
 
 
 def gnp_set_weights_device(M: Model, w, stream=None):
