@@ -261,6 +261,26 @@ int gnp_server_stats(gnp_server* S, gnp_server_stats_t* out);
 /* Finish the running requests, abandon the queued ones, join the server thread. */
 void gnp_server_destroy(gnp_server* S);
 
+/* ---------------------------------------------------------------- allocation-free gamma */
+
+/* gamma of Eq. 6 for a CSR matrix the caller already holds on the device (row_ptr_dev
+ * int32 [n+1], col_dev int32 [nnz], val_dev float64 [nnz], the conventions of
+ * gnp_mat_create; only column indices are checked, on the device), written to the
+ * device scalar *gamma_dev (NaN if a column index lies outside [0, n)).  The paper has
+ * no counterpart of this call: it serves callers that cannot allocate device memory
+ * when they call in -- code running while a CUDA graph is being captured, applications
+ * whose device memory belongs to their own pool or arena, loops that cannot take the
+ * implicit synchronisation of cudaMalloc/cudaFree.  It allocates nothing: its scratch
+ * (column sums, block partials, a counter) is a fixed 8 MiB + 10 KiB array inside the
+ * library, held by every GPU that loads the library until the process exits, so
+ * n <= 1,048,576 (larger n gives GNP_ERR_INVALID_ARG).  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call clears the scratch it uses and shares the one
+ * array: calls that overlap on the GPU (other streams, other threads) race.
+ * Asynchronous on `stream`. */
+int gnp_gamma_noalloc(int n, long long nnz, const int* row_ptr_dev, const int* col_dev,
+                      const double* val_dev, double* gamma_dev, void* stream);
+
 /* Time every Res-GCONV launch of the following solves with CUDA events recorded on
  * the solve's stream around the launch (inside the captured restart cycle); the sums
  * arrive in gnp_solve_info.gconv_ms / gconv_launches.  The event records add a little

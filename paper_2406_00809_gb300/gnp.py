@@ -97,6 +97,7 @@ def lib():
         "gnp_philox4x32_10": (i, [vp, C.c_uint, C.c_uint, i, vp, vp]),
         "fgmres_solve": (i, [vp, vp, vp, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
         "gnp_profile_gconv": (i, [i]),
+        "gnp_gamma_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp, vp]),
         "gnp_server_create": (i, [C.POINTER(_ServerConfig), pp]),
         "gnp_server_submit": (i, [vp, vp, vp, vp, vp, d, i, C.POINTER(C.c_longlong)]),
         "gnp_server_poll": (i, [vp, C.c_longlong, C.POINTER(_SolveInfo)]),
@@ -194,6 +195,17 @@ def gnp_gamma(A: Mat, stream=None) -> float:
     g = C.c_double()
     _check(lib().gnp_gamma(A.h, C.byref(g), _stream(stream)))
     return g.value
+
+
+def gnp_gamma_noalloc(row_ptr, col, val, gamma_out, stream=None):
+    """gamma (Eq. 6) of a device CSR into the device scalar gamma_out, allocating
+    nothing (scratch is a fixed array inside the library; n <= 2^20)."""
+    import torch
+    n = row_ptr.numel() - 1
+    _check(lib().gnp_gamma_noalloc(n, col.numel(), _dptr(row_ptr, torch.int32, "row_ptr"),
+                                   _dptr(col, torch.int32, "col"), _dptr(val, torch.float64, "val"),
+                                   _dptr(gamma_out, torch.float64, "gamma_out"), _stream(stream)))
+    return gamma_out
 
 
 def gnp_spmv(A: Mat, x, y, stream=None):
