@@ -62,7 +62,7 @@ typedef enum {
   GNP_ERR_RESIDUAL_MISMATCH = 7, /* Givens residual met tol three cycles running while
                                     the true residual did not (Sec. 4 "solution failure") */
   GNP_ERR_NOT_CONVERGED = 8,     /* maxiters reached before rtol */
-  GNP_ERR_TIMEOUT = 9,           /* a bounded wait expired */
+  GNP_ERR_TIMEOUT = 9,           /* a bounded wait or a solve's time limit expired */
   GNP_ERR_NAN = 10,              /* a NaN/Inf appeared in the iteration */
   GNP_ERR_BUSY = 11              /* server: no capacity for the request right now */
 } gnp_status;
@@ -78,6 +78,13 @@ typedef enum {
                      accumulation and weights */
 } gnp_hprec;
 
+typedef enum {
+  GNP_PRECOND_IDENTITY = 0, /* z = v (plain GMRES) */
+  GNP_PRECOND_GNP = 1,      /* z = M(v), the graph neural preconditioner (Sec. 2.3) */
+  GNP_PRECOND_JACOBI = 2,   /* z = D^-1 v, D = diag(A) (Sec. 3 "Compared methods") */
+  GNP_PRECOND_GMRES = 3     /* z = GMRES(A, v): inner GMRES as a preconditioner (Sec. 3) */
+} gnp_precond_kind;
+
 typedef struct gnp_config {
   int L;            /* Res-GCONV layers, 0..GNP_MAX_LAYERS (paper: 8) */
   int form;         /* gnp_layer_form */
@@ -87,6 +94,11 @@ typedef struct gnp_config {
   float lr;         /* Adam learning rate (paper: 1e-3) */
   float beta1, beta2, eps; /* Adam constants (0.9, 0.999, 1e-8) */
   unsigned long long seed; /* Philox key of all training draws */
+  /* Ablations of Sec. 4 ("Are the proposed training-data generation and the
+   * scale-equivariance design necessary?"); zero = the paper's method: */
+  int sample_mode;  /* 0: B/2 Eq. 5 pairs + B/2 with x ~ N(0, I);  1: x ~ N(0, I) for all B;
+                       2: b ~ N(0, I) for all B (the loss then needs no x) */
+  int no_scale;     /* 1: drop the scaling s of Eq. 8 (u = b, z = network output) */
 } gnp_config;
 
 typedef struct gnp_solve_info {
@@ -105,11 +117,17 @@ typedef struct gnp_solve_info {
   int cycles;           /* restart cycles launched */
   int gconv_launches;   /* Res-GCONV launches timed (gnp_profile_gconv on), else 0 */
   double gconv_ms;      /* their summed CUDA-event time in milliseconds */
+  double* time_history; /* optional, caller-owned [maxiters+1] (may be NULL): elapsed
+                           seconds of the solve at each iteration, read from the device
+                           clock (%globaltimer) by the kernel that ends the iteration;
+                           entry 0 = when the initial residual was known; the t_i of the
+                           Time-AUC metric (Sec. 3 "Evaluation metrics") */
 } gnp_solve_info;
 
 typedef struct gnp_mat gnp_mat;
 typedef struct gnp_model gnp_model;
 typedef struct gnp_server gnp_server;
+typedef struct gnp_precond gnp_precond;
 
 /* ---------------------------------------------------------------- diagnostics */
 
@@ -178,7 +196,8 @@ int gnp_forward_batch(gnp_model* M, const float* b_dev, int B, float* z_dev, voi
 int gnp_backward_batch(gnp_model* M, const float* dz_dev, float* grad_dev, void* stream);
 /* Training pairs of step `step` (Sec. 3: the first B/2 columns x = V_m Z S^-1 eps of
  * Eq. 5, the rest x ~ N(0, I)), written node-major to x_dev float32 [n*B] with
- * B = cfg.batch.  The first call runs the sampler's Arnoldi process and SVD. */
+ * B = cfg.batch.  The first call runs the sampler's Arnoldi process and SVD.  With
+ * cfg.sample_mode 1 all B columns are x ~ N(0, I); with 2 they are b ~ N(0, I). */
 int gnp_sample_batch(gnp_model* M, int step, float* x_dev, void* stream);
 /* One optimisation step on given solutions x (float32 [n*B] node-major): b = A_hat x,
  * z = M(b), loss = mean |A_hat z - b| (Sec. 3), backward, Adam, best-loss snapshot.
@@ -192,6 +211,9 @@ int gnp_train_step(gnp_model* M, float* loss_out, void* stream);
 /* Run `steps` training steps back to back (no per-step host sync); *best_loss_out
  * (host, may be NULL) receives the best loss seen.  Synchronous. */
 int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream);
+/* As gnp_train, and losses_out (host float [steps], may be NULL) receives every step's
+ * loss (before its update), for loss curves (Sec. 4, Fig. 6). */
+int gnp_train_history(gnp_model* M, int steps, float* losses_out, float* best_loss_out, void* stream);
 
 /* Free the training state (saved activations, optimiser, sampler; about
  * (2L + 10) * n * B * 64 bytes) after copying the best-loss weights to the applied
@@ -221,6 +243,51 @@ int gnp_philox4x32_10(const unsigned* ctr_dev, unsigned key0, unsigned key1, int
 int fgmres_solve(gnp_mat* A, const double* b_dev, double* x_dev, gnp_model* M,
                  int restart, double rtol, int maxiters, gnp_solve_info* info,
                  void* stream);
+/* As fgmres_solve with a time limit as well (Sec. 3 "Stopping criteria": the timed
+ * comparison stops by rtol or timeout).  timeout_s > 0: the first Arnoldi step that
+ * ends at or after timeout_s seconds of device time (counted from the solve's first
+ * kernel) ends its cycle; x is formed from the steps so far and the solve returns
+ * GNP_ERR_TIMEOUT unless the true residual meets rtol.  timeout_s = 0: no limit
+ * (identical to fgmres_solve).  maxiters still bounds the steps (and sizes the history
+ * buffers); pass a large value to let the time limit decide.  timeout_s < 0 or
+ * >= 1e9 is GNP_ERR_INVALID_ARG. */
+int fgmres_solve_timeout(gnp_mat* A, const double* b_dev, double* x_dev, gnp_model* M,
+                         int restart, double rtol, int maxiters, double timeout_s,
+                         gnp_solve_info* info, void* stream);
+
+/* A right preconditioner for fgmres_solve_precond (the GNP and the simple baselines
+ * the paper compares it with, Sec. 3 "Compared methods"):
+ *   GNP_PRECOND_IDENTITY  M and the inner arguments are ignored;
+ *   GNP_PRECOND_GNP       M (not owned, must outlive P, built on A) is applied;
+ *   GNP_PRECOND_JACOBI    z = v / a_ii; a row with a_ii = 0 (or no stored diagonal) uses
+ *                         1 (that row passes v_i through);
+ *   GNP_PRECOND_GMRES     z = one cycle of at most inner_iters (1..GNP_MAX_RESTART) GMRES
+ *                         steps on A z = v from z0 = 0 (float64, CGS2, Givens), ended
+ *                         early when the Givens residual estimate reaches
+ *                         inner_rtol * ||v|| (paper: 10 steps, 1e-6).  Owns its own
+ *                         Krylov workspace ((inner_iters + 1) * n float64 and more).
+ * The library owns *out (gnp_precond_destroy).  P is bound to A. */
+int gnp_precond_create(gnp_mat* A, int kind, gnp_model* M, int inner_iters, double inner_rtol,
+                       gnp_precond** out);
+void gnp_precond_destroy(gnp_precond* P);
+/* z = P(v) for one vector: v_dev, z_dev float64 [n] device arrays (distinct).
+ * Asynchronous on `stream`. */
+int gnp_precond_apply(gnp_precond* P, const double* v_dev, double* z_dev, void* stream);
+/* fgmres_solve_timeout with any preconditioner P (NULL = identity).  With the GNP the
+ * directions Z are float32 (the network's output precision); with Jacobi and inner
+ * GMRES they are float64. */
+int fgmres_solve_precond(gnp_mat* A, const double* b_dev, double* x_dev, gnp_precond* P,
+                         int restart, double rtol, int maxiters, double timeout_s,
+                         gnp_solve_info* info, void* stream);
+
+/* The paper's convergence metrics (Sec. 3 "Evaluation metrics"), computed on the host
+ * from a solve's histories (len = res_history_len = iters + 1 entries):
+ *   Iter-AUC = sum_{i=0}^{iters} (log10 r_i - log10 rtol),
+ *   Time-AUC = sum_{i=1}^{iters} (log10 r_i - log10 rtol) (t_i - t_{i-1}).
+ * r_i <= 0 counts as the smallest normal double (2.2e-308).  len < 1, rtol <= 0 or a
+ * NULL array gives NaN.  Pure host functions: no device work. */
+double gnp_iter_auc(const double* res_history, int len, double rtol);
+double gnp_time_auc(const double* res_history, const double* time_history, int len, double rtol);
 
 /* ---------------------------------------------------------------- solve server */
 

@@ -16,6 +16,10 @@ gnp_ref      gamma normalisation (Eq. 6), scaling s (Eq. 8), MLP encoder/decoder
 krylov_ref   FGMRES with a nonlinear M (Algorithm 1, Eq. 1) with MGS or CGS2
              orthogonalisation and Givens least squares; a separate textbook GMRES for
              pinning; the Arnoldi process (Eq. 4) and the training-pair sampler (Eq. 5).
+precond_ref  the Jacobi and inner-GMRES preconditioners the paper compares with
+             (Sec. 3 "Compared methods").
+metrics_ref  the Iter-AUC and Time-AUC convergence metrics (Sec. 3 "Evaluation
+             metrics").
 philox_ref   Philox4x32-10 counter-based generator (Salmon et al., SC'11) and the
              Box-Muller transform, used for the random draws of training.
 

@@ -113,16 +113,21 @@ def scale(b: np.ndarray):
 
 
 def forward(Ahat: sp.csr_matrix, b: np.ndarray, P: dict, form: int = FORM_PAPER,
-            keep: bool = False):
+            keep: bool = False, scaled: bool = True):
     """z = M(b) for b of shape [n] or [n, B] (Sec. 2.3, Fig. 1, Eqs. 6-8).
 
     s -> encoder (1 -> 32, ReLU, -> 16) -> L x Res-GCONV -> decoder (16 -> 32, ReLU,
     -> 1) -> s^{-1}.  With keep=True also returns the saved activations for backward.
+    scaled=False is the ablation of Sec. 4 without s: the network sees b itself and its
+    output is z.
     """
     vec = b.ndim == 1
     bb = b[:, None] if vec else b
     n = bb.shape[0]
-    u, tau = scale(bb)
+    if scaled:
+        u, tau = scale(bb)
+    else:
+        u, tau = bb.copy(), np.full(bb.shape[1], np.sqrt(n))
     a1 = u[:, :, None] * P["enc_W1"][0][None, None, :] + P["enc_b1"]   # [n,B,32]
     r1 = relu(a1)
     H = r1 @ P["enc_W2"] + P["enc_b2"]                                  # [n,B,16]
@@ -242,15 +247,17 @@ class Adam:
         return w - self.lr * mh / (np.sqrt(vh) + self.eps)
 
 
-def train_step(Ahat, w_blob, L, form, x, opt: Adam):
-    """One training step on given solution vectors x [n, B] (b = A_hat x).
+def train_step(Ahat, w_blob, L, form, x, opt: Adam, scaled: bool = True, b=None):
+    """One training step on given solution vectors x [n, B] (b = A_hat x), or on given
+    right-hand sides b [n, B] when x is None (the b ~ N(0, I) ablation of Sec. 4).
 
     The system used for training is the prescaled one, A <- A / gamma (Sec. 3
     "Problems"), which equals A_hat.  Returns (new blob, loss before the update).
     """
-    b = np.asarray(Ahat @ x)
+    if x is not None:
+        b = np.asarray(Ahat @ x)
     P = unpack(w_blob, L)
-    z, cache = forward(Ahat, b, P, form, keep=True)
+    z, cache = forward(Ahat, b, P, form, keep=True, scaled=scaled)
     loss, dz = l1_loss(Ahat, z, b)
     G = backward(Ahat, P, cache, dz)
     g = pack(G)

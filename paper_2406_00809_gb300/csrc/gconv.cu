@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -165,11 +166,12 @@ __device__ __forceinline__ void tile_copy(uint32_t* stile, HT* g, int r0, int ro
 // Standalone apply: u = (sqrt(n)/tau) v with tau from k_vnorm.  Inside FGMRES
 // (vscale != null): v_j = w / h is unit-norm by construction, so the encoder divides the
 // stored w by the device scalar h, writes v_j back in place and uses tau = 1 (it stores
-// tau = 1 for the decoder's back-scaling).
+// tau = 1 for the decoder's back-scaling).  noscale (the ablation without s): u = v, and
+// tau = sqrt(n) is stored so that the decoder's factor tau/sqrt(n) is 1.
 template <class HT>
 __global__ void __launch_bounds__(TILE)
 k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau, const int* __restrict__ ctl,
-         int n, double sqrt_n, HT* __restrict__ H, const __grid_constant__ EncW ew) {
+         int n, double sqrt_n, int noscale, HT* __restrict__ H, const __grid_constant__ EncW ew) {
   if (ctl && !ctl[1]) return;
   __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
   double* v = static_cast<double*>(colptr(vp));
@@ -177,7 +179,10 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
   const int rows = min(TILE, n - r0);
   const int t = threadIdx.x;
   double f;
-  if (vscale) {
+  if (noscale) {
+    f = 1.0;
+    if (blockIdx.x == 0 && t == 0) *tau = sqrt_n;
+  } else if (vscale) {
     f = sqrt_n;
     if (blockIdx.x == 0 && t == 0) *tau = 1.0;
   } else {
@@ -208,86 +213,141 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
 
 // ---------------------------------------------------------------- k_gconv
 //
-// One block per 256 consecutive rows.  Its nonzeros are split evenly over slots of G
-// lanes (4 for float32 rows of 64 bytes, 2 for bfloat16 rows of 32 bytes); a slot walks
-// its nonzero range loading each neighbour's row with one 16-byte load per lane, four
-// nonzeros in flight; rows split between slots leave partial sums that the epilogue adds
-// in slot order (common.cuh, tile_gather).  The block's own hidden rows come in with one
-// coalesced tile copy.  Epilogue: one thread per row, U and W as uniform constant-bank
-// operands; the row is staged in shared memory and the tile written back with coalesced
-// stores, or (last layer) the decoder and tau/sqrt(n) produce z directly.
+// One block of TILE threads per ROWS consecutive rows (ROWS = 256: one epilogue thread per
+// row; ROWS = 128: two, each computing 8 of the 16 outputs, which halves every thread's
+// share of the gather and of the epilogue for matrices too small to fill the GPU with
+// 256-row tiles).  The tile's nonzeros are split evenly over slots of G lanes (4 for
+// float32 rows of 64 bytes, 2 for bfloat16 rows of 32 bytes); a slot walks its nonzero
+// range loading each neighbour's row with one 16-byte load per lane, four nonzeros in
+// flight; rows split between slots leave partial sums that the epilogue adds in slot
+// order (common.cuh, tile_gather).  The block's own hidden rows come in with one
+// coalesced tile copy.  Epilogue: U and W as uniform constant-bank operands; the output
+// rows are staged in shared memory and the tile written back with coalesced stores, or
+// (last layer) the decoder and tau/sqrt(n) produce z directly.
 
-// Rows per Res-GCONV block (its TILE threads form TILE/G slots over these rows' nonzeros).
-constexpr int GROWS = 256;
-
-template <class HT>
+template <class HT, int ROWS>
 struct GconvSmem {
-  TileSmem<typename HTraits<HT>::TR, GROWS> g;
-  __align__(16) uint32_t stile[GROWS * HTraits<HT>::SROW];
+  TileSmem<typename HTraits<HT>::TR, ROWS> g;
+  __align__(16) uint32_t stile[ROWS * HTraits<HT>::SROW];
+  float zpart[ROWS];  // second half of the decoder sum (two threads per row)
 };
 
-// Layer epilogue for one row: out = ReLU(h U + agg W) (paper) or h + ReLU(agg W).
-template <int FORM>
-__device__ __forceinline__ void layer_rows(const float (&h)[16], const float (&agg)[16],
-                                           const LayerW& lw, float (&o)[16]) {
+// Outputs [K0, K0+OPT) of one row: ReLU(h U + agg W) (paper) or h + ReLU(agg W).
+template <int FORM, int K0, int OPT>
+__device__ __forceinline__ void layer_part(const float (&h)[16], const float (&agg)[16],
+                                           const LayerW& lw, float (&o)[OPT]) {
 #pragma unroll
-  for (int k = 0; k < 16; ++k) o[k] = 0.0f;
+  for (int k = 0; k < OPT; ++k) o[k] = 0.0f;
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) o[k] = fmaf(agg[c], lw.W[c * 16 + k], o[k]);
+    for (int k = 0; k < OPT; ++k) o[k] = fmaf(agg[c], lw.W[c * 16 + K0 + k], o[k]);
   }
   if (FORM == GNP_LAYER_PAPER) {
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) o[k] = fmaf(h[c], lw.U[c * 16 + k], o[k]);
+      for (int k = 0; k < OPT; ++k) o[k] = fmaf(h[c], lw.U[c * 16 + K0 + k], o[k]);
     }
 #pragma unroll
-    for (int k = 0; k < 16; ++k) o[k] = fmaxf(o[k], 0.0f);
+    for (int k = 0; k < OPT; ++k) o[k] = fmaxf(o[k], 0.0f);
   } else {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) o[k] = h[k] + fmaxf(o[k], 0.0f);
+    for (int k = 0; k < OPT; ++k) o[k] = h[K0 + k] + fmaxf(o[k], 0.0f);
   }
 }
 
-// Gather + per-row layer; leaves the layer output of row t in `o` (valid for t < rows).
-template <class HT, int FORM>
-__device__ __forceinline__ void gconv_body(GconvSmem<HT>& sm, const int* __restrict__ rp,
-                                           const int* __restrict__ col, const float* __restrict__ valhat,
-                                           const HT* __restrict__ Hin, int r0, int rows,
-                                           const LayerW& lw, float (&o)[16]) {
+// Store outputs [K0, K0+OPT) of row t into the staging tile (the row's own slot).
+template <class HT, int K0, int OPT>
+__device__ __forceinline__ void stage_part(uint32_t* stile, int t, const float (&o)[OPT]) {
+  if constexpr (OPT == 16) {
+    stage_row<HT>(stile, t, o);
+  } else if constexpr (sizeof(HT) == 4) {
+    float4* d = reinterpret_cast<float4*>(stile + t * HTraits<HT>::SROW + K0);
+#pragma unroll
+    for (int q = 0; q < OPT / 4; ++q) d[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+  } else {
+    static_assert(OPT == 8, "bfloat16 halves are 8 values (16 bytes)");
+    uint4* d = reinterpret_cast<uint4*>(stile + t * HTraits<HT>::SROW + K0 / 2);
+    d[0] = make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                      pack_bf16x2(o[6], o[7]));
+  }
+}
+
+// Gather + this thread's share of the layer for row t = threadIdx.x % ROWS; `part`
+// (threadIdx.x / ROWS, warp-uniform) selects the outputs.  Leaves the outputs in `o`.
+template <class HT, int FORM, int ROWS, int K0, int OPT>
+__device__ __forceinline__ void gconv_part(GconvSmem<HT, ROWS>& sm, int t, int rows, const LayerW& lw,
+                                           float (&o)[OPT]) {
+  using TR = typename HTraits<HT>::TR;
+  if (t < rows) {
+    float h[16], agg[16];
+    unstage_row<HT>(sm.stile, t, h);
+    tile_row_sum<TR, 16>(sm.g, t, 0, agg);
+    layer_part<FORM, K0, OPT>(h, agg, lw, o);
+  }
+}
+
+template <class HT, int ROWS>
+__device__ __forceinline__ void gconv_load_gather(GconvSmem<HT, ROWS>& sm, const int* __restrict__ rp,
+                                                  const int* __restrict__ col, const float* __restrict__ valhat,
+                                                  const HT* __restrict__ Hin, int r0, int rows) {
   using TR = typename HTraits<HT>::TR;
   tile_load_rp<TR>(sm.g, rp, r0, rows);
   tile_copy<HT, false>(sm.stile, const_cast<HT*>(Hin), r0, rows);
   __syncthreads();
   tile_gather<TR>(sm.g, rows, col, valhat, Hin);
   __syncthreads();
-  const int t = threadIdx.x;
-  if (t < rows) {
-    float h[16], agg[16];
-    unstage_row<HT>(sm.stile, t, h);
-    tile_row_sum<TR, 16>(sm.g, t, 0, agg);
-    layer_rows<FORM>(h, agg, lw, o);
-  }
 }
 
-template <class HT, int FORM>
-__global__ void __launch_bounds__(TILE, 3)
+template <int ROWS> struct GconvBounds { static constexpr int MIN_BLOCKS = 3; };
+template <> struct GconvBounds<128> { static constexpr int MIN_BLOCKS = 4; };
+
+template <class HT, int FORM, int ROWS>
+__global__ void __launch_bounds__(TILE, GconvBounds<ROWS>::MIN_BLOCKS)
 k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
         const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
         const __grid_constant__ LayerW lw) {
+  static_assert(ROWS == TILE || 2 * ROWS == TILE, "one or two epilogue threads per row");
   if (ctl && !ctl[1]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  GconvSmem<HT>& sm = *reinterpret_cast<GconvSmem<HT>*>(smraw);
-  const int r0 = blockIdx.x * GROWS;
-  const int rows = min(GROWS, n - r0);
-  float o[16];
-  gconv_body<HT, FORM>(sm, rp, col, valhat, Hin, r0, rows, lw, o);
-  // own row was read from stile by this thread only: safe to overwrite in place
-  if (threadIdx.x < rows) stage_row<HT>(sm.stile, threadIdx.x, o);
+  GconvSmem<HT, ROWS>& sm = *reinterpret_cast<GconvSmem<HT, ROWS>*>(smraw);
+  const int r0 = blockIdx.x * ROWS;
+  const int rows = min(ROWS, n - r0);
+  gconv_load_gather<HT, ROWS>(sm, rp, col, valhat, Hin, r0, rows);
+  const int t = threadIdx.x % ROWS;
+  if constexpr (ROWS == TILE) {
+    float o[16];
+    gconv_part<HT, FORM, ROWS, 0, 16>(sm, t, rows, lw, o);
+    // own row was read from stile by this thread only: safe to overwrite in place
+    if (t < rows) stage_part<HT, 0, 16>(sm.stile, t, o);
+  } else {
+    float o[8];
+    const bool hi = threadIdx.x >= ROWS;
+    if (hi) gconv_part<HT, FORM, ROWS, 8, 8>(sm, t, rows, lw, o);
+    else gconv_part<HT, FORM, ROWS, 0, 8>(sm, t, rows, lw, o);
+    __syncthreads();  // both threads of a row have read its input from stile
+    if (t < rows) {
+      if (hi) stage_part<HT, 8, 8>(sm.stile, t, o);
+      else stage_part<HT, 0, 8>(sm.stile, t, o);
+    }
+  }
   __syncthreads();
   tile_copy<HT, true>(sm.stile, Hout, r0, rows);
+}
+
+// Decoder hidden units [K0, K0+KC) of one row: sum_k w2_k ReLU(D1^T o + e1)_k.
+template <int K0, int KC>
+__device__ __forceinline__ float decode_part(const float (&o)[16], const DecW& dw) {
+  float z = 0.0f;
+#pragma unroll
+  for (int k = K0; k < K0 + KC; ++k) {
+    float a = dw.b1[k];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a = fmaf(o[c], dw.W1[c * 32 + k], a);
+    z = fmaf(fmaxf(a, 0.0f), dw.W2[k], z);
+  }
+  return z;
 }
 
 // Decoder for one row: (w2^T ReLU(D1^T h + e1) + e2) * back.
@@ -303,24 +363,52 @@ __device__ __forceinline__ float decode_row(const float (&o)[16], const DecW& dw
   return z;
 }
 
-template <class HT, int FORM>
-__global__ void __launch_bounds__(TILE, 3)
+template <class HT, int FORM, int ROWS>
+__global__ void __launch_bounds__(TILE, GconvBounds<ROWS>::MIN_BLOCKS)
 k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
             const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n,
             int n, const int* __restrict__ ctl, const __grid_constant__ LayerW lw,
             const __grid_constant__ DecW dw) {
   if (ctl && !ctl[1]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  GconvSmem<HT>& sm = *reinterpret_cast<GconvSmem<HT>*>(smraw);
-  const int r0 = blockIdx.x * GROWS;
-  const int rows = min(GROWS, n - r0);
-  float o[16];
-  gconv_body<HT, FORM>(sm, rp, col, valhat, Hin, r0, rows, lw, o);
-  if (threadIdx.x < rows) {
-    const double tv = *tau;
-    const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
-    float* z = static_cast<float*>(colptr(zp));
-    z[r0 + threadIdx.x] = decode_row(o, dw) * back;
+  GconvSmem<HT, ROWS>& sm = *reinterpret_cast<GconvSmem<HT, ROWS>*>(smraw);
+  const int r0 = blockIdx.x * ROWS;
+  const int rows = min(ROWS, n - r0);
+  gconv_load_gather<HT, ROWS>(sm, rp, col, valhat, Hin, r0, rows);
+  const int t = threadIdx.x % ROWS;
+  const double tv = *tau;
+  const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+  float* z = static_cast<float*>(colptr(zp));
+  if constexpr (ROWS == TILE) {
+    float o[16];
+    gconv_part<HT, FORM, ROWS, 0, 16>(sm, t, rows, lw, o);
+    if (t < rows) z[r0 + t] = decode_row(o, dw) * back;
+  } else {
+    // the two halves of each output row meet in float32 in the (no longer needed)
+    // aggregate area; each thread then evaluates half of the decoder's hidden units
+    float o[8];
+    const bool hi = threadIdx.x >= ROWS;
+    if (hi) gconv_part<HT, FORM, ROWS, 8, 8>(sm, t, rows, lw, o);
+    else gconv_part<HT, FORM, ROWS, 0, 8>(sm, t, rows, lw, o);
+    using TR = typename HTraits<HT>::TR;
+    constexpr int ST = TR::STRIDE;
+    static_assert(ST >= 16, "aggregate rows hold 16 floats");
+    __syncthreads();  // every thread is done with the aggregates
+    if (t < rows) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sm.g.agg[t * ST + (hi ? 8 : 0) + k] = o[k];
+    }
+    __syncthreads();
+    float zp_part = 0.0f;
+    if (t < rows) {
+      float full[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) full[k] = sm.g.agg[t * ST + k];
+      zp_part = hi ? decode_part<16, 16>(full, dw) : decode_part<0, 16>(full, dw);
+      if (hi) sm.zpart[t] = zp_part;
+    }
+    __syncthreads();
+    if (!hi && t < rows) z[r0 + t] = ((dw.b2 + zp_part) + sm.zpart[t]) * back;
   }
 }
 
@@ -374,44 +462,83 @@ static void fill_layer(const std::vector<float>& w, int l, LayerW& lw) {
   memcpy(lw.W, p + 256, sizeof(lw.W));
 }
 
-template <class HT, int FORM>
+template <class HT, int FORM, int ROWS>
 static int set_smem_attrs() {
   static bool done = false;
   if (done) return GNP_OK;
-  const int bytes = (int)sizeof(GconvSmem<HT>);
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  const int bytes = (int)sizeof(GconvSmem<HT, ROWS>);
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    bytes));
   done = true;
   return GNP_OK;
 }
 
+static int env_int(const char* name, int dflt) {
+  const char* e = getenv(name);
+  return e ? atoi(e) : dflt;
+}
+
+// Rows per Res-GCONV tile: 256-row tiles (one epilogue thread per row) at three
+// resident blocks per SM were the fastest shape for both hidden-block precisions on both
+// the 65,536-row and the 2^20-row workloads; 128-row tiles (two threads per row) are kept
+// for tuning.  GNP_GCONV_ROWS=128|256 in the environment forces one.
+template <class HT>
+static int gconv_rows() {
+  const int forced = env_int("GNP_GCONV_ROWS", 0);
+  if (forced == 128 || forced == 256) return forced;
+  return 256;
+}
+
+// Resident Res-GCONV blocks per SM.  The shared memory the blocks take comes out of the
+// same 256 KB per SM as the L1 cache that serves the neighbour-row gathers, so the
+// carveout is set to fit exactly this many blocks (more blocks, less L1).
+// GNP_GCONV_BLOCKS=1..8 in the environment overrides it (for tuning).
+template <class HT, int ROWS>
+static int gconv_blocks() {
+  const int forced = env_int("GNP_GCONV_BLOCKS", 0);
+  if (forced >= 1 && forced <= 8) return forced;
+  return ROWS == 256 ? 3 : 4;
+}
+
+template <class HT, int FORM, int ROWS>
+static int set_carveout() {
+  static int applied = -1;
+  const int blocks = gconv_blocks<HT, ROWS>();
+  const int per_block = (int)sizeof(GconvSmem<HT, ROWS>) + 1024;  // + the runtime's reserved 1 KB
+  const int pct = std::min(100, (blocks * per_block * 100 + 228 * 1024 - 1) / (228 * 1024));
+  if (pct == applied) return GNP_OK;
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM, ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM, ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    pct));
+  applied = pct;
+  return GNP_OK;
+}
+
 template <class HT, int FORM>
-static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W) {
+static int set_smem_attrs_all() {
+  GNP_TRY((set_smem_attrs<HT, FORM, 128>()));
+  GNP_TRY((set_smem_attrs<HT, FORM, 256>()));
+  GNP_TRY((set_carveout<HT, FORM, 128>()));
+  GNP_TRY((set_carveout<HT, FORM, 256>()));
+  return GNP_OK;
+}
+
+// Layers 0..L-1 (the last one fused with the decoder unless tracing), ROWS-row tiles.
+template <class HT, int FORM, int ROWS>
+static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, const int* ctl,
+                         cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const DecW& dw, double sqrt_n) {
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
-  const double sqrt_n = std::sqrt((double)n);
-  GNP_TRY((set_smem_attrs<HT, FORM>()));
-  const int smem = (int)sizeof(GconvSmem<HT>);
-  const int nt = (n + TILE - 1) / TILE;
-  const int ntg = (n + GROWS - 1) / GROWS;
-  const int nb = red_blocks(n);
-  if (!vscale)
-    k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
-  EncW ew;
-  DecW dw;
-  fill_params(M->w_host, L, ew, dw);
-  HT* H0 = static_cast<HT*>(W.H[0]);
-  HT* H1 = static_cast<HT*>(W.H[1]);
-  k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, H0, ew);
+  const int smem = (int)sizeof(GconvSmem<HT, ROWS>);
+  const int ntg = (n + ROWS - 1) / ROWS;
   const long long hcount = (long long)n * 16;
-  if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, hcount);
   const int fused_last = (L > 0 && !trace) ? 1 : 0;
   for (int l = 0; l < L - fused_last; ++l) {
     LayerW lw;
     fill_layer(M->w_host, l, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
-    k_gconv<HT, FORM><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
+    k_gconv<HT, FORM, ROWS><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
     if (trace)
       k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
@@ -421,12 +548,38 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
     LayerW lw;
     fill_layer(M->w_host, L - 1, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
-    k_gconv_dec<HT, FORM><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, W.tau, sqrt_n, n, ctl,
-                                                   lw, dw);
+    k_gconv_dec<HT, FORM, ROWS><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, W.tau, sqrt_n, n,
+                                                         ctl, lw, dw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
-    k_decode<HT><<<nt, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
+    k_decode<HT><<<(n + TILE - 1) / TILE, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
   }
+  return GNP_OK;
+}
+
+template <class HT, int FORM>
+static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
+                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W) {
+  const gnp_mat* A = M->A;
+  const int n = A->n, L = M->cfg.L;
+  const double sqrt_n = std::sqrt((double)n);
+  GNP_TRY((set_smem_attrs_all<HT, FORM>()));
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  const int noscale = M->cfg.no_scale ? 1 : 0;
+  if (!vscale && !noscale)
+    k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
+  EncW ew;
+  DecW dw;
+  fill_params(M->w_host, L, ew, dw);
+  HT* H0 = static_cast<HT*>(W.H[0]);
+  HT* H1 = static_cast<HT*>(W.H[1]);
+  k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
+  if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, (long long)n * 16);
+  if (gconv_rows<HT>() == 128)
+    GNP_TRY((launch_layers<HT, FORM, 128>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));
+  else
+    GNP_TRY((launch_layers<HT, FORM, 256>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));
   return check_launch("gnp apply");
 }
 
@@ -465,11 +618,11 @@ void apply_ws_free(ApplyWs& ws) {
 int apply_prepare(gnp_model* M) {
   GNP_TRY(model_sync_host(M));
   if (M->hprec == GNP_H_BF16) {
-    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((set_smem_attrs<uint16_t, GNP_LAYER_PAPER>()));
-    else GNP_TRY((set_smem_attrs<uint16_t, GNP_LAYER_RESID>()));
+    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((set_smem_attrs_all<uint16_t, GNP_LAYER_PAPER>()));
+    else GNP_TRY((set_smem_attrs_all<uint16_t, GNP_LAYER_RESID>()));
   } else {
-    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((set_smem_attrs<float, GNP_LAYER_PAPER>()));
-    else GNP_TRY((set_smem_attrs<float, GNP_LAYER_RESID>()));
+    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((set_smem_attrs_all<float, GNP_LAYER_PAPER>()));
+    else GNP_TRY((set_smem_attrs_all<float, GNP_LAYER_RESID>()));
   }
   return GNP_OK;
 }
@@ -497,6 +650,8 @@ int gnp_create(const gnp_mat* Ac, const gnp_config* cfg, const float* weights_ho
   GNP_REQUIRE(cfg->L >= 0 && cfg->L <= GNP_MAX_LAYERS, "gnp_create: L = %d out of range", cfg->L);
   GNP_REQUIRE(cfg->form == GNP_LAYER_PAPER || cfg->form == GNP_LAYER_RESID, "gnp_create: bad form");
   GNP_REQUIRE(cfg->hprec == GNP_H_FP32 || cfg->hprec == GNP_H_BF16, "gnp_create: bad hprec");
+  GNP_REQUIRE(cfg->sample_mode >= 0 && cfg->sample_mode <= 2, "gnp_create: sample_mode %d", cfg->sample_mode);
+  GNP_REQUIRE(cfg->no_scale == 0 || cfg->no_scale == 1, "gnp_create: no_scale %d", cfg->no_scale);
   gnp_mat* A = const_cast<gnp_mat*>(Ac);
   gnp_model* M = new gnp_model();
   M->A = A;

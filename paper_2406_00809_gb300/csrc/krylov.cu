@@ -27,6 +27,11 @@ namespace gnp {
 
 static bool g_profile_gconv = false;
 
+__device__ __forceinline__ void* colptr_k(const ColPtr& p) {
+  const int j = p.jptr ? *p.jptr : 0;
+  return static_cast<char*>(p.base) + (size_t)(j + p.off) * p.stride;
+}
+
 static int ensure_events(Solver* S, int m, int L) {
   if ((int)S->events.size() >= 2 * m * L && S->ev_L == L) return GNP_OK;
   for (cudaEvent_t e : S->events) cudaEventDestroy(e);
@@ -55,6 +60,7 @@ void solver_free(Solver* s) {
   dev_free(s->h1);
   dev_free(s->h2);
   dev_free(s->hist);
+  dev_free(s->thist);
   red_free(s->red);
   delete s;
 }
@@ -62,7 +68,7 @@ void solver_free(Solver* s) {
 size_t solver_bytes(int n, int m, int maxiters) {
   const size_t maxb = (size_t)std::max(red_blocks(n), (n + TILE - 1) / TILE);
   return (size_t)n * (m + 1) * 8 + (size_t)n * m * 4 + (size_t)n * 8 + sizeof(DevState) +
-         (size_t)(m + 1) * m * 8 * 2 + (size_t)(4 * m + 8) * 8 + (size_t)(maxiters + 1) * 8 +
+         (size_t)(m + 1) * m * 8 * 2 + (size_t)(4 * m + 8) * 8 + (size_t)(maxiters + 1) * 16 +
          maxb * (m + 2) * 8 + 8;
 }
 
@@ -99,6 +105,7 @@ int solver_create(int n, int m, int maxiters, Solver** out) {
     if ((e = dev_alloc(&s->h1, (size_t)m + 2)) != GNP_OK) break;
     if ((e = dev_alloc(&s->h2, (size_t)m + 2)) != GNP_OK) break;
     if ((e = dev_alloc(&s->hist, (size_t)maxiters + 1)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->thist, (size_t)maxiters + 1)) != GNP_OK) break;
     const int maxb = std::max(red_blocks(n), (n + TILE - 1) / TILE);
     if ((e = red_alloc(s->red, maxb, m + 2)) != GNP_OK) break;
     if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) {
@@ -145,11 +152,6 @@ struct TrSpmv {
   }
 };
 
-__device__ __forceinline__ const void* colptr_c(const ColPtr& p) {
-  int j = p.jptr ? *p.jptr : 0;
-  return static_cast<const char*>(p.base) + (size_t)(j + p.off) * p.stride;
-}
-
 // y = A x.  x: float64 or float32 column (ColPtr); y float64.
 template <class XT>
 __global__ void __launch_bounds__(TILE)
@@ -158,7 +160,7 @@ k_spmv_tile(const int* __restrict__ rp, const int* __restrict__ col, const doubl
   if (ctl && !ctl[1]) return;
   using TR = TrSpmv<XT>;
   __shared__ TileSmem<TR> sm;
-  const XT* x = static_cast<const XT*>(colptr_c(xp));
+  const XT* x = static_cast<const XT*>(colptr_k(xp));
   const int r0 = blockIdx.x * TILE;
   const int rows = min(TILE, n - r0);
   tile_load_rp<TR>(sm, rp, r0, rows);
@@ -172,8 +174,44 @@ k_spmv_tile(const int* __restrict__ rp, const int* __restrict__ col, const doubl
   }
 }
 
-// Block-wide sum of KC values per thread, added into the block accumulators acc[k0..].
-__device__ __forceinline__ void block_accumulate(double (&a)[8], double (*sh)[32], double* acc, int kvalid);
+// Grid of the CGS2 kernels: one block per SM while the rows are few enough that L2
+// latency, not bandwidth, bounds the basis reads (each block then reduces once per
+// column chunk, and the float64 pipes of all SMs share the work evenly); up to four per
+// SM on larger systems for memory parallelism.  Never more than red_blocks(n), the
+// capacity of the partial-sum scratch.
+static int dot_blocks(int n) {
+  const int per = (n + NUM_SMS_GB300 * RED_THREADS * 2 - 1) / (NUM_SMS_GB300 * RED_THREADS * 2);
+  return std::min(red_blocks(n), NUM_SMS_GB300 * std::max(1, std::min(4, per)));
+}
+
+constexpr int KC = 8;  // basis columns per register chunk
+constexpr int RSTRIDE = RED_THREADS + 8;  // row stride of the reduction transpose (doubles)
+static_assert(RED_THREADS == TILE && RED_THREADS / 32 == KC, "one warp per chunk column");
+
+// Block-wide sums of KC values per thread (256 threads): the values are transposed
+// through shared memory (sh: KC * RSTRIDE doubles) so that warp w adds column w's 256
+// values with 8 sequential adds per lane and one 5-level shuffle tree, instead of one
+// tree per value per warp.  GB300 executes float64 adds at 2 per SM per cycle, so
+// the number of tree levels, not the memory traffic, decides these kernels' cost.
+// ACC: dst[w] += sum (shared accumulators); else dst[w] = sum.  Fixed order.
+template <bool ACC>
+__device__ __forceinline__ void block_reduce_kc(const double (&a)[KC], double* sh, double* dst, int kvalid) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+#pragma unroll
+  for (int kc = 0; kc < KC; ++kc) sh[kc * RSTRIDE + t] = a[kc];
+  __syncthreads();
+  if (w < kvalid) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < RED_THREADS / 32; ++i) s += sh[w * RSTRIDE + lane + 32 * i];
+    s = warp_sum(s);
+    if (lane == 0) {
+      if (ACC) dst[w] += s;
+      else dst[w] = s;
+    }
+  }
+  __syncthreads();
+}
 
 // w = A z (tile gather) fused with CGS2 pass 1: h1 = V_j^T w and ||w||^2.  Blocks loop
 // over tiles and keep their dot sums in shared memory, so the partials stay one row
@@ -187,11 +225,11 @@ k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double
   using TR = TrSpmv<XT>;
   __shared__ TileSmem<TR> sm;
   __shared__ double sacc[GNP_MAX_RESTART + 2];
-  __shared__ double shred[8][32];
+  __shared__ double sred[KC * RSTRIDE];
   const int j = st->j;
   const int K = j + 2;  // h1[0..j] and ||w||^2
   const size_t ld = (size_t)n;
-  const XT* x = static_cast<const XT*>(colptr_c(xp));
+  const XT* x = static_cast<const XT*>(colptr_k(xp));
   for (int k = threadIdx.x; k < K; k += blockDim.x) sacc[k] = 0.0;
   const int nt = (n + TILE - 1) / TILE;
   for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
@@ -219,7 +257,7 @@ k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double
         if (t < rows && k < K) vk = (k == j + 1) ? wr : V[k * ld + r0 + t];
         a[kc] = vk * wr;
       }
-      block_accumulate(a, shred, sacc + k0, min(8, K - k0));
+      block_reduce_kc<true>(a, sred, sacc + k0, min(8, K - k0));
     }
   }
   __syncthreads();
@@ -234,28 +272,12 @@ k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double
   }
 }
 
-__device__ __forceinline__ void block_accumulate(double (&a)[8], double (*sh)[32], double* acc, int kvalid) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int kc = 0; kc < 8; ++kc) {
-    const double v = warp_sum(a[kc]);
-    if (lane == 0) sh[kc][w] = v;
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < kvalid) {
-    double t = 0.0;
-    for (int k = 0; k < nw; ++k) t += sh[threadIdx.x][k];
-    acc[threadIdx.x] += t;
-  }
-  __syncthreads();
-}
-
 // r = b - A x -> V[:, 0], beta = ||r||; the last block restarts the cycle state.
 __global__ void __launch_bounds__(TILE)
 k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
            const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ V0, int n,
            DevState* st, double* __restrict__ g, double* __restrict__ hist,
-           double* __restrict__ partials, unsigned* counter) {
+           unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
   using TR = TrSpmv<double>;
   __shared__ TileSmem<TR> sm;
   __shared__ double sh[32];
@@ -281,7 +303,10 @@ k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double
     if (threadIdx.x == 0) {
       const double beta = sqrt(tot[0]);
       st->beta = beta;
-      if (st->iters == 0) hist[0] = beta / st->bnorm;
+      if (st->iters == 0) {
+        hist[0] = beta / st->bnorm;
+        thist[0] = global_ns() - st->t0;
+      }
       st->last_flags = st->flags;
       st->last_jj = st->jj;
       st->j = 0;
@@ -299,6 +324,7 @@ k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double
 __global__ void __launch_bounds__(RED_THREADS)
 k_bnorm(const double* __restrict__ b, int n, DevState* st, double* __restrict__ partials, unsigned* counter) {
   __shared__ double sh[32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->t0 = global_ns();  // the solve's clock starts here
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += b[i] * b[i];
   double t = block_sum(acc, sh);
@@ -325,34 +351,16 @@ k_vscale(double* __restrict__ V, int n, const DevState* st) {
 
 // ---------------------------------------------------------------- CGS2 passes
 
-constexpr int KC = 8;  // basis columns per register chunk
-
-// Sum KC per-thread values over the block; thread kc < KC writes partial kc.
-__device__ __forceinline__ void block_sum_store(double (&a)[KC], double (*sh)[32], double* dst, int kvalid) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int kc = 0; kc < KC; ++kc) {
-    double v = warp_sum(a[kc]);
-    if (lane == 0) sh[kc][w] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kvalid) {
-    double t = 0.0;
-    for (int k = 0; k < nw; ++k) t += sh[threadIdx.x][k];
-    dst[threadIdx.x] = t;
-  }
-  __syncthreads();
-}
-
 template <int PASS>
 __global__ void __launch_bounds__(RED_THREADS)
 k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, double* __restrict__ h1,
       double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
       double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
-      double* __restrict__ partials, unsigned* counter) {
+      unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
   if (!st->active) return;
   __shared__ double shh[GNP_MAX_RESTART + 2];
   __shared__ double shred[KC][32];  // KC*32 = 256 >= GNP_MAX_RESTART: reused for sines
+  __shared__ double sred[PASS == 3 ? 1 : KC * RSTRIDE];
   __shared__ double shtot[GNP_MAX_RESTART + 4];
   const int j = st->j;
   const size_t ld = (size_t)n;
@@ -399,7 +407,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
           }
         }
       }
-      block_sum_store(acc, shred, partials + (size_t)blockIdx.x * K + k0, min(KC, K - k0));
+      block_reduce_kc<false>(acc, sred, partials + (size_t)blockIdx.x * K + k0, min(KC, K - k0));
     }
   }
   if (!last_block_arrive(counter)) return;
@@ -456,6 +464,8 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   }
   const int iters = st->iters + 1;
   st->iters = iters;
+  const unsigned long long elapsed = global_ns() - st->t0;
+  thist[iters] = elapsed;
   const double wn0 = st->wnorm0;
   int flags = 0;
   int jj;
@@ -482,6 +492,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
     if (hn <= BREAKDOWN_REL * wn0) flags |= FL_BREAKDOWN;
     else if (res <= st->tol) flags |= FL_EST_CONV;
     else if (iters >= st->maxiters) flags |= FL_MAXIT;
+    else if (st->timeout_ns != 0ull && elapsed >= st->timeout_ns) flags |= FL_TIMEOUT;
     else if (j + 1 >= m) flags |= FL_FULL;
   }
   st->jj = jj;
@@ -545,42 +556,156 @@ int spmv_launch(const gnp_mat* A, const double* x, const float* xf, double* y, c
   return check_launch("k_spmv_tile");
 }
 
+int solver_ensure_zd(Solver* S, int m) {
+  if (S->Zd && S->zd_m >= m) return GNP_OK;
+  dev_free(S->Zd);
+  S->zd_m = 0;
+  GNP_TRY(dev_alloc(&S->Zd, (size_t)S->n * m));
+  S->zd_m = m;
+  return GNP_OK;
+}
+
 // Enqueue one restart cycle: m Arnoldi steps, x update, residual.
-int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, double* x,
+int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, double* x,
                  cudaStream_t st, bool prof, const ApplyWs* ws) {
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
+  const int ncg = dot_blocks(n);
   const int ndot = std::min(nt, 4 * NUM_SMS_GB300);
   const int* ctl = reinterpret_cast<const int*>(S->st);
   const int* jptr = ctl;
+  const bool f64z = P.kind == GNP_PRECOND_JACOBI || P.kind == GNP_PRECOND_GMRES;
+  if (f64z) GNP_REQUIRE(S->Zd && S->zd_m >= m, "launch_cycle: float64 directions not allocated");
   for (int j = 0; j < m; ++j) {
-    if (M) {
-      ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
+    ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
+    if (P.kind == GNP_PRECOND_GNP) {
+      gnp_model* M = P.M;
       ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
       cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
       GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws));
       k_spmv_dot<float><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st, S->h1,
                                                S->red.partials, S->red.counter);
+    } else if (f64z) {
+      ColPtr z{S->Zd, sizeof(double) * (size_t)n, jptr, 0};
+      if (P.kind == GNP_PRECOND_JACOBI)
+        GNP_TRY(jacobi_launch(P.dinv, v, S->st, z, n, st));
+      else
+        GNP_TRY(inner_gmres_launch(A, P.inner, v, S->st, z, st));
+      k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st, S->h1,
+                                                S->red.partials, S->red.counter);
     } else {
       k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
-      ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
       k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, S->V, n, S->st, S->h1,
                                                 S->red.partials, S->red.counter);
     }
-    k_cgs<2><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->red.partials, S->red.counter);
-    k_cgs<3><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->red.partials, S->red.counter);
+    k_cgs<2><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+    k_cgs<3><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
   }
   const int xsm = (int)sizeof(double) * m * m;
-  if (M)
+  if (P.kind == GNP_PRECOND_GNP)
     k_xupdate<float><<<nb, RED_THREADS, xsm, st>>>(S->Z, x, n, S->st, S->R, S->g);
   else
-    k_xupdate<double><<<nb, RED_THREADS, xsm, st>>>(S->V, x, n, S->st, S->R, S->g);
+    k_xupdate<double><<<nb, RED_THREADS, xsm, st>>>(f64z ? S->Zd : S->V, x, n, S->st, S->R, S->g);
   k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
-                                  S->red.partials, S->red.counter);
+                                  S->thist, S->red.partials, S->red.counter);
   return check_launch("fgmres cycle");
+}
+
+// ---------------------------------------------------------------- inner GMRES
+
+// Start of one inner solve: b = v (divided by outer->vscale and written back when an
+// outer FGMRES step owns v), x = 0, and the inner state reset.  When the outer step is
+// inactive the inner solve gets maxiters = 0, so all its kernels fall through.
+__global__ void __launch_bounds__(RED_THREADS)
+k_inner_begin(ColPtr vp, DevState* outer, double* __restrict__ b, double* __restrict__ x, int n,
+              DevState* st, int iters, double rtol) {
+  const bool act = outer == nullptr || outer->active;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->j = 0;
+    st->active = 0;
+    st->iters = 0;
+    st->maxiters = act ? iters : 0;
+    st->m = iters;
+    st->jj = 0;
+    st->flags = 0;
+    st->rtol = rtol;
+    st->timeout_ns = 0ull;
+  }
+  if (!act) return;
+  double* v = static_cast<double*>(colptr_k(vp));
+  const double s = outer ? outer->vscale : 1.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double t = v[i];
+    if (outer) {
+      t = t / s;
+      v[i] = t;
+    }
+    b[i] = t;
+    x[i] = 0.0;
+  }
+}
+
+// z = x at the end of the inner solve (skipped when the outer step is inactive).
+__global__ void __launch_bounds__(RED_THREADS)
+k_inner_end(const double* __restrict__ x, const DevState* outer, ColPtr zp, int n) {
+  if (outer && !outer->active) return;
+  double* z = static_cast<double*>(colptr_k(zp));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) z[i] = x[i];
+}
+
+int inner_gmres_create(int n, int iters, double rtol, InnerGmres** out) {
+  *out = nullptr;
+  InnerGmres* G = new InnerGmres();
+  G->iters = iters;
+  G->rtol = rtol;
+  int e = solver_create(n, iters, iters, &G->S);
+  if (e == GNP_OK) e = dev_alloc(&G->b, (size_t)n);
+  if (e == GNP_OK) e = dev_alloc(&G->x, (size_t)n);
+  if (e != GNP_OK) {
+    inner_gmres_free(G);
+    return e;
+  }
+  *out = G;
+  return GNP_OK;
+}
+
+void inner_gmres_free(InnerGmres* G) {
+  if (!G) return;
+  solver_free(G->S);
+  dev_free(G->b);
+  dev_free(G->x);
+  delete G;
+}
+
+int inner_gmres_launch(gnp_mat* A, InnerGmres* G, ColPtr v, DevState* outer, ColPtr z, cudaStream_t st) {
+  Solver* S = G->S;
+  const int n = A->n;
+  const int k = G->iters;
+  const int nt = (n + TILE - 1) / TILE;
+  const int nb = red_blocks(n);
+  const int ncg = dot_blocks(n);
+  const int ndot = std::min(nt, 4 * NUM_SMS_GB300);
+  const int* jptr = reinterpret_cast<const int*>(S->st);
+  k_inner_begin<<<nb, RED_THREADS, 0, st>>>(v, outer, G->b, G->x, n, S->st, k, G->rtol);
+  k_bnorm<<<nb, RED_THREADS, 0, st>>>(G->b, n, S->st, S->red.partials, S->red.counter);
+  k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, G->x, G->b, S->V, n, S->st, S->g, S->hist,
+                                  S->thist, S->red.partials, S->red.counter);
+  for (int j = 0; j < k; ++j) {
+    k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
+    ColPtr vj{S->V, sizeof(double) * (size_t)n, jptr, 0};
+    k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, vj, S->w, S->V, n, S->st, S->h1,
+                                              S->red.partials, S->red.counter);
+    k_cgs<2><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+    k_cgs<3><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+  }
+  k_xupdate<double><<<nb, RED_THREADS, (int)sizeof(double) * k * k, st>>>(S->V, G->x, n, S->st, S->R, S->g);
+  k_inner_end<<<nb, RED_THREADS, 0, st>>>(G->x, outer, z, n);
+  return check_launch("inner gmres");
 }
 
 static int read_state(Solver* S, cudaStream_t st) {
@@ -604,6 +729,7 @@ int arnoldi_basis(gnp_mat* A, const double* v1, int m, double* V_out, double* Hb
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
+  const int ncg = dot_blocks(n);
   DevState init{};
   init.maxiters = m;
   init.m = m;
@@ -611,20 +737,22 @@ int arnoldi_basis(gnp_mat* A, const double* v1, int m, double* V_out, double* Hb
   memcpy(S->st_host, &init, sizeof(DevState));
   GNP_TRY_CUDA(cudaMemcpyAsync(S->st, S->st_host, sizeof(DevState), cudaMemcpyHostToDevice, st));
   GNP_TRY_CUDA(cudaMemsetAsync(S->w, 0, sizeof(double) * n, st));  // x0 = 0
+  // entries of H_bar below the subdiagonal are never written: clear stale values
+  GNP_TRY_CUDA(cudaMemsetAsync(S->H, 0, sizeof(double) * (size_t)(m + 1) * m, st));
   k_bnorm<<<nb, RED_THREADS, 0, st>>>(v1, n, S->st, S->red.partials, S->red.counter);
   k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, S->w, v1, S->V, n, S->st, S->g, S->hist,
-                                  S->red.partials, S->red.counter);
+                                  S->thist, S->red.partials, S->red.counter);
   const int* jptr = reinterpret_cast<const int*>(S->st);
   for (int j = 0; j < m; ++j) {
     k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
     ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
     k_spmv_tile<double><<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, n, jptr);
-    k_cgs<1><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->red.partials, S->red.counter);
-    k_cgs<2><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->red.partials, S->red.counter);
-    k_cgs<3><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->red.partials, S->red.counter);
+    k_cgs<1><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+    k_cgs<2><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+    k_cgs<3><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
   }
   GNP_TRY(check_launch("arnoldi"));
   GNP_TRY(read_state(S, st));
@@ -644,7 +772,7 @@ int arnoldi_basis(gnp_mat* A, const double* v1, int m, double* V_out, double* Hb
 }
 
 int solve_init_launch(const gnp_mat* A, Solver* S, const double* b, double* x, double rtol, int maxiters,
-                      int m, cudaStream_t st) {
+                      int m, double timeout_s, cudaStream_t st) {
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
@@ -652,11 +780,14 @@ int solve_init_launch(const gnp_mat* A, Solver* S, const double* b, double* x, d
   init.maxiters = maxiters;
   init.m = m;
   init.rtol = rtol;
+  init.timeout_ns = timeout_s > 0.0 ? (unsigned long long)std::max(1.0, timeout_s * 1e9) : 0ull;
   memcpy(S->st_host, &init, sizeof(DevState));
   GNP_TRY_CUDA(cudaMemcpyAsync(S->st, S->st_host, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  // entries of H_bar below the subdiagonal are never written: clear stale values
+  GNP_TRY_CUDA(cudaMemsetAsync(S->H, 0, sizeof(double) * (size_t)(m + 1) * m, st));
   k_bnorm<<<nb, RED_THREADS, 0, st>>>(b, n, S->st, S->red.partials, S->red.counter);
   k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
-                                  S->red.partials, S->red.counter);
+                                  S->thist, S->red.partials, S->red.counter);
   return check_launch("solve init");
 }
 
@@ -667,6 +798,10 @@ bool cycle_after(const DevState& hs, double beta_prev, int maxiters, CycleCtl& c
   }
   if (hs.beta <= hs.tol) {
     *status = GNP_OK;
+    return true;
+  }
+  if (hs.last_flags & FL_TIMEOUT) {
+    *status = GNP_ERR_TIMEOUT;
     return true;
   }
   c.mism = (hs.last_flags & FL_EST_CONV) ? c.mism + 1 : 0;
@@ -701,18 +836,24 @@ extern "C" int gnp_profile_gconv(int on) {
   return GNP_OK;
 }
 
-extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M, int restart,
-                            double rtol, int maxiters, gnp_solve_info* info, void* stream) {
+namespace gnp {
+
+static int solve_impl(gnp_mat* A, const double* b, double* x, const Prec& P, int restart, double rtol,
+                      int maxiters, double timeout_s, gnp_solve_info* info, void* stream) {
+  gnp_model* M = P.kind == GNP_PRECOND_GNP ? P.M : nullptr;
   GNP_REQUIRE(A && b && x, "fgmres_solve: null argument");
+  GNP_REQUIRE(timeout_s >= 0.0 && timeout_s < 1e9, "fgmres_solve: timeout %g out of [0, 1e9) s", timeout_s);
   GNP_REQUIRE(restart >= 1 && restart <= GNP_MAX_RESTART, "fgmres_solve: restart %d out of [1, %d]",
               restart, GNP_MAX_RESTART);
   GNP_REQUIRE(maxiters >= 0, "fgmres_solve: maxiters < 0");
   GNP_REQUIRE(rtol >= 0.0, "fgmres_solve: rtol < 0");
   GNP_REQUIRE(!M || M->A == A, "fgmres_solve: the preconditioner was built for another matrix");
+  GNP_REQUIRE(P.kind != GNP_PRECOND_GNP || M, "fgmres_solve: GNP preconditioner without a model");
   cudaStream_t st = as_stream(stream);
   const auto t0 = std::chrono::steady_clock::now();
   GNP_TRY(solver_ensure(A, restart, maxiters));
   Solver* S = A->solver;
+  if (P.kind == GNP_PRECOND_JACOBI || P.kind == GNP_PRECOND_GMRES) GNP_TRY(solver_ensure_zd(S, restart));
   if (st == nullptr || st == cudaStreamLegacy) {
     // graphs cannot be captured on the legacy default stream: order the caller's
     // earlier work, then run the (synchronous) solve on the solver's own stream
@@ -723,7 +864,7 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
   const int n = A->n;
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
-  GNP_TRY(solve_init_launch(A, S, b, x, rtol, maxiters, restart, st));
+  GNP_TRY(solve_init_launch(A, S, b, x, rtol, maxiters, restart, timeout_s, st));
   GNP_TRY(check_launch("fgmres init"));
   GNP_TRY(read_state(S, st));
   int status = GNP_OK;
@@ -745,14 +886,14 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
       const double beta_prev = hs.beta;
       if (use_graph) {
         const unsigned long long ver = M ? model_version(M) : 0ull;
-        if (!S->gexec || S->g_model != M || S->g_version != ver || S->g_m != restart ||
+        if (!S->gexec || S->g_model != P.key || S->g_kind != P.kind || S->g_version != ver || S->g_m != restart ||
             S->g_hprec != (M ? M->hprec : -1) || S->g_b != b || S->g_x != x || S->g_stream != st ||
             S->g_prof != prof) {
           if (S->gexec) cudaGraphExecDestroy(S->gexec);
           S->gexec = nullptr;
           cudaGraph_t graph;
           GNP_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-          int ls = launch_cycle(A, S, M, restart, b, x, st, prof, nullptr);
+          int ls = launch_cycle(A, S, P, restart, b, x, st, prof, nullptr);
           cudaError_t ce = cudaStreamEndCapture(st, &graph);
           if (ls != GNP_OK) return ls;
           if (ce != cudaSuccess) {
@@ -766,7 +907,8 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
             S->gexec = nullptr;
             return GNP_ERR_CUDA;
           }
-          S->g_model = M;
+          S->g_model = P.key;
+          S->g_kind = P.kind;
           S->g_version = ver;
           S->g_m = restart;
           S->g_hprec = M ? M->hprec : -1;
@@ -777,7 +919,7 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
         }
         GNP_TRY_CUDA(cudaGraphLaunch(S->gexec, st));
       } else {
-        GNP_TRY(launch_cycle(A, S, M, restart, b, x, st, prof, nullptr));
+        GNP_TRY(launch_cycle(A, S, P, restart, b, x, st, prof, nullptr));
       }
       const int iters_before = hs.iters;
       ++ctl_c.cycles;
@@ -819,6 +961,16 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
       }
       info->res_history_len = cnt;
     }
+    if (info->time_history) {
+      const int cnt = hs.bnorm > 0.0 ? hs.iters + 1 : 1;
+      if (hs.bnorm > 0.0) {
+        std::vector<unsigned long long> ns(cnt);
+        GNP_TRY_CUDA(cudaMemcpy(ns.data(), S->thist, sizeof(unsigned long long) * cnt, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < cnt; ++i) info->time_history[i] = 1e-9 * (double)ns[i];
+      } else {
+        info->time_history[0] = 0.0;
+      }
+    }
     if (info->hessenberg) {
       const int cols = hs.iters > 0 ? hs.last_jj : 0;
       GNP_TRY_CUDA(cudaMemcpy(info->hessenberg, S->H, sizeof(double) * (size_t)(restart + 1) * restart,
@@ -827,4 +979,33 @@ extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M
     }
   }
   return status;
+}
+
+}  // namespace gnp
+
+static Prec model_prec(gnp_model* M) {
+  Prec P;
+  P.kind = M ? GNP_PRECOND_GNP : GNP_PRECOND_IDENTITY;
+  P.M = M;
+  P.key = M;
+  return P;
+}
+
+extern "C" int fgmres_solve_timeout(gnp_mat* A, const double* b, double* x, gnp_model* M, int restart,
+                                    double rtol, int maxiters, double timeout_s, gnp_solve_info* info,
+                                    void* stream) {
+  return solve_impl(A, b, x, model_prec(M), restart, rtol, maxiters, timeout_s, info, stream);
+}
+
+extern "C" int fgmres_solve(gnp_mat* A, const double* b, double* x, gnp_model* M, int restart,
+                            double rtol, int maxiters, gnp_solve_info* info, void* stream) {
+  return solve_impl(A, b, x, model_prec(M), restart, rtol, maxiters, 0.0, info, stream);
+}
+
+extern "C" int fgmres_solve_precond(gnp_mat* A, const double* b, double* x, gnp_precond* P, int restart,
+                                    double rtol, int maxiters, double timeout_s, gnp_solve_info* info,
+                                    void* stream) {
+  if (!P) return solve_impl(A, b, x, model_prec(nullptr), restart, rtol, maxiters, timeout_s, info, stream);
+  GNP_REQUIRE(precond_matrix(P) == A, "fgmres_solve_precond: the preconditioner was built for another matrix");
+  return solve_impl(A, b, x, precond_view(P), restart, rtol, maxiters, timeout_s, info, stream);
 }

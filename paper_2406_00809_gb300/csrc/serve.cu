@@ -104,7 +104,7 @@ static bool setup(Server* sv, Request* r) {
     s = GNP_ERR_OOM;
   }
   if (s == GNP_OK && r->M) s = apply_prepare(r->M);
-  if (s == GNP_OK) s = solve_init_launch(r->A, r->S, r->b, r->x, r->rtol, r->maxiters, r->m, sv->stream);
+  if (s == GNP_OK) s = solve_init_launch(r->A, r->S, r->b, r->x, r->rtol, r->maxiters, r->m, 0.0, sv->stream);
   if (s == GNP_OK && cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost,
                                      sv->stream) != cudaSuccess)
     s = GNP_ERR_CUDA;
@@ -144,7 +144,11 @@ static bool setup(Server* sv, Request* r) {
     finish(sv, r, GNP_ERR_CUDA);
     return false;
   }
-  s = launch_cycle(r->A, r->S, r->M, r->m, r->b, r->x, sv->stream, false, r->M ? &r->ws : nullptr);
+  Prec P;
+  P.kind = r->M ? GNP_PRECOND_GNP : GNP_PRECOND_IDENTITY;
+  P.M = r->M;
+  P.key = r->M;
+  s = launch_cycle(r->A, r->S, P, r->m, r->b, r->x, sv->stream, false, r->M ? &r->ws : nullptr);
   cudaError_t ce = cudaStreamEndCapture(sv->stream, &r->cycle);
   if (s != GNP_OK || ce != cudaSuccess) {
     if (ce != cudaSuccess) set_error("server: capture failed: %s", cudaGetErrorString(ce));
@@ -346,9 +350,11 @@ static int collect(Server* sv, std::map<long long, Request*>::iterator it, gnp_s
   if (info) {
     double* hist = info->res_history;
     double* hess = info->hessenberg;
+    double* times = info->time_history;
     *info = r->info;
     info->res_history = hist;
     info->hessenberg = hess;
+    info->time_history = times;
     info->res_history_len = 0;
     info->hessenberg_cols = 0;
   }

@@ -14,6 +14,7 @@ enum : int {
   FL_NAN = 8,
   FL_MAXIT = 16,
   FL_FULL = 32,
+  FL_TIMEOUT = 64,
 };
 
 struct DevState {
@@ -28,7 +29,16 @@ struct DevState {
   int last_jj;     // columns that cycle used
   int pad;
   double bnorm, tol, rtol, beta, vscale, wnorm0, hn, res_est;
+  unsigned long long t0;          // %globaltimer (ns) when the solve began
+  unsigned long long timeout_ns;  // 0: no time limit
 };
+
+// Device clock in nanoseconds (the PTX %globaltimer register, common to all SMs).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 constexpr double BREAKDOWN_REL = 1e-14;
 
@@ -46,11 +56,15 @@ struct Solver {
   double* g = nullptr;   // [m+1]
   double* h1 = nullptr;  // [m+2]
   double* h2 = nullptr;  // [m+2]
+  double* Zd = nullptr;   // [n*m] float64 directions (Jacobi and inner-GMRES preconditioners)
+  int zd_m = 0;
   double* hist = nullptr;  // [maxiters+1]
+  unsigned long long* thist = nullptr;  // [maxiters+1] ns since DevState::t0 at each iteration
   RedScratch red;
   // captured restart cycle
   cudaGraphExec_t gexec = nullptr;
-  const void* g_model = nullptr;
+  const void* g_model = nullptr;  // the preconditioner the graph was captured for
+  int g_kind = -1;
   unsigned long long g_version = 0;
   int g_m = 0, g_hprec = -1;
   const double* g_b = nullptr;
@@ -64,12 +78,47 @@ struct Solver {
 };
 
 
+// Inner GMRES used as a preconditioner (Sec. 3 "Compared methods"): one cycle of at most
+// `iters` Arnoldi steps from x0 = 0, ended early when the Givens estimate reaches
+// rtol * ||v||.  Owns its Krylov workspace, so it can run inside an outer FGMRES step.
+struct InnerGmres {
+  Solver* S = nullptr;
+  double* b = nullptr;  // [n] right-hand side (the outer basis vector)
+  double* x = nullptr;  // [n] iterate
+  int iters = 10;
+  double rtol = 1e-6;
+};
+
+// The right preconditioner of a solve.
+struct Prec {
+  int kind = GNP_PRECOND_IDENTITY;
+  gnp_model* M = nullptr;         // GNP
+  const double* dinv = nullptr;   // Jacobi: 1 / a_ii (1 where a_ii = 0)
+  InnerGmres* inner = nullptr;    // GMRES
+  const void* key = nullptr;      // identity of the object (graph cache)
+};
+
+// z = P(v) for P = Jacobi: v (read through ColPtr) is first divided by outer->vscale and
+// written back when outer is non-null (the outer step's normalisation of v_j); every
+// kernel returns at once when outer->active == 0.  z: float64 column.
+int jacobi_launch(const double* dinv, ColPtr v, DevState* outer, ColPtr z, int n, cudaStream_t st);
+// The same for P = inner GMRES (krylov.cu).
+int inner_gmres_launch(gnp_mat* A, InnerGmres* G, ColPtr v, DevState* outer, ColPtr z, cudaStream_t st);
+int inner_gmres_create(int n, int iters, double rtol, InnerGmres** out);
+void inner_gmres_free(InnerGmres* G);
+
+// The solver-side view of a gnp_precond handle (precond.cu).
+Prec precond_view(gnp_precond* P);
+const gnp_mat* precond_matrix(const gnp_precond* P);
+
 // Enqueue ||b||, the initial residual and the state reset of a solve on `st`.
 int solve_init_launch(const gnp_mat* A, Solver* S, const double* b, double* x, double rtol, int maxiters,
-                      int m, cudaStream_t st);
+                      int m, double timeout_s, cudaStream_t st);
 // Enqueue one restart cycle (m Arnoldi steps, x update, residual).
-int launch_cycle(gnp_mat* A, Solver* S, gnp_model* M, int m, const double* b, double* x,
+int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, double* x,
                  cudaStream_t st, bool prof, const ApplyWs* ws);
+// Float64 direction storage for the Jacobi / inner-GMRES preconditioners.
+int solver_ensure_zd(Solver* S, int m);
 
 // Host bookkeeping between cycles (the stopping rules of the oracle's documentation).
 struct CycleCtl {

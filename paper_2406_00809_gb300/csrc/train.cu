@@ -297,6 +297,12 @@ k_col_norms(const float* __restrict__ b, long long R, int B, double* __restrict_
   }
 }
 
+// tau_k = sqrt(n) for every column: the ablation without the scaling s makes both
+// factors of Eq. 8 one.
+__global__ void k_fill_tau(double* __restrict__ tau, int B, double sqrt_n) {
+  for (int k = threadIdx.x; k < B; k += blockDim.x) tau[k] = sqrt_n;
+}
+
 // loss = mean |r| over R entries; r <- sign(r) in place (sign(0) = 0).
 __global__ void __launch_bounds__(256)
 k_l1(float* __restrict__ r, long long R, double* __restrict__ partials, unsigned* counter,
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(256)
 k_dec_bwd(const float* __restrict__ HL, const float* __restrict__ dz, const double* __restrict__ tau,
           long long R, int B, double sqrt_n, const float* __restrict__ wd, float* __restrict__ do_out,
           float* __restrict__ q_out, float* __restrict__ dc1_out, float* __restrict__ dH) {
-  __shared__ float sw[DEC_COUNT];
+  __shared__ __align__(16) float sw[DEC_COUNT + 3];
   for (int k = threadIdx.x; k < DEC_COUNT; k += blockDim.x) sw[k] = wd[k];
   __syncthreads();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
@@ -484,15 +490,33 @@ k_dec_bwd(const float* __restrict__ HL, const float* __restrict__ dz, const doub
     float g[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) g[c] = 0.f;
-    for (int k = 0; k < 32; ++k) {
-      float a = sw[512 + k];
+    float4* qo = reinterpret_cast<float4*>(q_out + r * 32);
+    float4* dco = reinterpret_cast<float4*>(dc1_out + r * 32);
+    // four hidden units at a time: one 16-byte weight load serves four FMAs
+#pragma unroll 2
+    for (int k4 = 0; k4 < 8; ++k4) {
+      float4 a = *reinterpret_cast<const float4*>(sw + 512 + 4 * k4);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) a = fmaf(h[c], sw[c * 32 + k], a);
-      const float dc = a > 0.f ? dov * sw[544 + k] : 0.f;
-      q_out[r * 32 + k] = fmaxf(a, 0.f);
-      dc1_out[r * 32 + k] = dc;
+      for (int c = 0; c < 16; ++c) {
+        const float4 w = *reinterpret_cast<const float4*>(sw + c * 32 + 4 * k4);
+        a.x = fmaf(h[c], w.x, a.x);
+        a.y = fmaf(h[c], w.y, a.y);
+        a.z = fmaf(h[c], w.z, a.z);
+        a.w = fmaf(h[c], w.w, a.w);
+      }
+      const float4 w2 = *reinterpret_cast<const float4*>(sw + 544 + 4 * k4);
+      const float4 dc = make_float4(a.x > 0.f ? dov * w2.x : 0.f, a.y > 0.f ? dov * w2.y : 0.f,
+                                    a.z > 0.f ? dov * w2.z : 0.f, a.w > 0.f ? dov * w2.w : 0.f);
+      qo[k4] = make_float4(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f), fmaxf(a.z, 0.f), fmaxf(a.w, 0.f));
+      dco[k4] = dc;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) g[c] = fmaf(dc, sw[c * 32 + k], g[c]);
+      for (int c = 0; c < 16; ++c) {
+        const float4 w = *reinterpret_cast<const float4*>(sw + c * 32 + 4 * k4);
+        g[c] = fmaf(dc.x, w.x, g[c]);
+        g[c] = fmaf(dc.y, w.y, g[c]);
+        g[c] = fmaf(dc.z, w.z, g[c]);
+        g[c] = fmaf(dc.w, w.w, g[c]);
+      }
     }
     float4* o = reinterpret_cast<float4*>(dH + r * 16);
 #pragma unroll
@@ -501,69 +525,101 @@ k_dec_bwd(const float* __restrict__ HL, const float* __restrict__ dz, const doub
 }
 
 // Layer backward, row part: Gp = G * 1[pre > 0] (pre recomputed from X and AGG exactly
-// as the forward did), Y = Gp W^T, local = Gp U^T (paper) or G (residual).
+// as the forward did), Y = Gp W^T, local = Gp U^T (paper) or G (residual).  Four threads
+// per row, thread j owning columns 4j..4j+3: it forms those four pre-activations (a
+// 16 x 4 slice of W and of U), its quarter of Gp, and its partial sums of Y and local over
+// its four columns, which a two-step shuffle tree (fixed order) completes; thread j then
+// writes entries 4j..4j+3 of every output row.  (One thread per row needs all 512
+// weights at once and spills.)
 template <int FORM>
 __global__ void __launch_bounds__(256)
 k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G,
                  long long R, const float* __restrict__ lw, float* __restrict__ Gp_out,
                  float* __restrict__ Y_out, float* __restrict__ local_out) {
-  __shared__ float sU[256], sW[256];
+  __shared__ __align__(16) float sU[256];
+  __shared__ __align__(16) float sW[256];
   for (int k = threadIdx.x; k < 256; k += blockDim.x) {
     sU[k] = lw[k];
     sW[k] = lw[256 + k];
   }
   __syncthreads();
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
-       r += (long long)gridDim.x * blockDim.x) {
-    float x[16], ag[16], g[16], o[16];
-    const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int j = (int)(tid & 3);
+  // lanes past the last row stay for the shuffles with a clamped row and store nothing
+  const bool ok = (tid >> 2) < R;
+  const long long r = ok ? (tid >> 2) : R - 1;
+  const float4* W4 = reinterpret_cast<const float4*>(sW);
+  const float4* U4 = reinterpret_cast<const float4*>(sU);
+  float ag[16];
+  {
     const float4* ap = reinterpret_cast<const float4*>(AGG + r * 16);
-    const float4* gp = reinterpret_cast<const float4*>(G + r * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float4 v = xp[q];
-      x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
-      v = ap[q];
+      const float4 v = __ldg(ap + q);
       ag[4 * q] = v.x; ag[4 * q + 1] = v.y; ag[4 * q + 2] = v.z; ag[4 * q + 3] = v.w;
-      v = gp[q];
-      g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
     }
+  }
+  float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) o[k] = 0.f;
-    for (int c = 0; c < 16; ++c) {
-#pragma unroll
-      for (int k = 0; k < 16; ++k) o[k] = fmaf(ag[c], sW[c * 16 + k], o[k]);
-    }
-    if (FORM == GNP_LAYER_PAPER) {
-      for (int c = 0; c < 16; ++c) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) o[k] = fmaf(x[c], sU[c * 16 + k], o[k]);
-      }
-    }
-    float gpv[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) gpv[k] = o[k] > 0.f ? g[k] : 0.f;
-    float y[16], loc[16];
-#pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      float a = 0.f, b = 0.f;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        a = fmaf(gpv[k], sW[c * 16 + k], a);
-        if (FORM == GNP_LAYER_PAPER) b = fmaf(gpv[k], sU[c * 16 + k], b);
-      }
-      y[c] = a;
-      loc[c] = (FORM == GNP_LAYER_PAPER) ? b : g[c];
-    }
-    float4* po = reinterpret_cast<float4*>(Gp_out + r * 16);
-    float4* yo = reinterpret_cast<float4*>(Y_out + r * 16);
-    float4* lo = reinterpret_cast<float4*>(local_out + r * 16);
+  for (int c = 0; c < 16; ++c) {
+    const float4 w = W4[c * 4 + j];
+    pre.x = fmaf(ag[c], w.x, pre.x);
+    pre.y = fmaf(ag[c], w.y, pre.y);
+    pre.z = fmaf(ag[c], w.z, pre.z);
+    pre.w = fmaf(ag[c], w.w, pre.w);
+  }
+  if (FORM == GNP_LAYER_PAPER) {
+    float x[16];
+    const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      po[q] = make_float4(gpv[4 * q], gpv[4 * q + 1], gpv[4 * q + 2], gpv[4 * q + 3]);
-      yo[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-      lo[q] = make_float4(loc[4 * q], loc[4 * q + 1], loc[4 * q + 2], loc[4 * q + 3]);
+      const float4 v = __ldg(xp + q);
+      x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
     }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float4 u = U4[c * 4 + j];
+      pre.x = fmaf(x[c], u.x, pre.x);
+      pre.y = fmaf(x[c], u.y, pre.y);
+      pre.z = fmaf(x[c], u.z, pre.z);
+      pre.w = fmaf(x[c], u.w, pre.w);
+    }
+  }
+  const float4 g = __ldg(reinterpret_cast<const float4*>(G + r * 16) + j);
+  const float4 gp = make_float4(pre.x > 0.f ? g.x : 0.f, pre.y > 0.f ? g.y : 0.f, pre.z > 0.f ? g.z : 0.f,
+                                pre.w > 0.f ? g.w : 0.f);
+  if (ok) reinterpret_cast<float4*>(Gp_out + r * 16)[j] = gp;
+  // partial Y[c] (and local[c]) over this thread's four columns, then the quad sum
+  float y[16], loc[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    const float4 w = W4[c * 4 + j];
+    y[c] = fmaf(gp.x, w.x, fmaf(gp.y, w.y, fmaf(gp.z, w.z, gp.w * w.w)));
+    if (FORM == GNP_LAYER_PAPER) {
+      const float4 u = U4[c * 4 + j];
+      loc[c] = fmaf(gp.x, u.x, fmaf(gp.y, u.y, fmaf(gp.z, u.z, gp.w * u.w)));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    y[c] += __shfl_xor_sync(0xffffffffu, y[c], 1);
+    y[c] += __shfl_xor_sync(0xffffffffu, y[c], 2);
+    if (FORM == GNP_LAYER_PAPER) {
+      loc[c] += __shfl_xor_sync(0xffffffffu, loc[c], 1);
+      loc[c] += __shfl_xor_sync(0xffffffffu, loc[c], 2);
+    }
+  }
+  float4 yo, lo;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q == j) {
+      yo = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+      lo = FORM == GNP_LAYER_PAPER ? make_float4(loc[4 * q], loc[4 * q + 1], loc[4 * q + 2], loc[4 * q + 3]) : g;
+    }
+  }
+  if (ok) {
+    reinterpret_cast<float4*>(Y_out + r * 16)[j] = yo;
+    reinterpret_cast<float4*>(local_out + r * 16)[j] = lo;
   }
 }
 
@@ -571,7 +627,7 @@ k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, con
 __global__ void __launch_bounds__(256)
 k_enc_bwd(const float* __restrict__ u, const float* __restrict__ dH0, long long R, const float* __restrict__ w,
           float* __restrict__ r1_out, float* __restrict__ da1_out) {
-  __shared__ float sw[ENC_COUNT];
+  __shared__ __align__(16) float sw[ENC_COUNT];
   for (int k = threadIdx.x; k < ENC_COUNT; k += blockDim.x) sw[k] = w[k];
   __syncthreads();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < R;
@@ -584,77 +640,160 @@ k_enc_bwd(const float* __restrict__ u, const float* __restrict__ dH0, long long 
       g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
     }
     const float uv = u[r];
-    for (int k = 0; k < 32; ++k) {
-      const float a = fmaf(uv, sw[ENC_W1 + k], sw[ENC_B1 + k]);
-      float d = 0.f;
+    float4* ro = reinterpret_cast<float4*>(r1_out + r * 32);
+    float4* dao = reinterpret_cast<float4*>(da1_out + r * 32);
+#pragma unroll 2
+    for (int k4 = 0; k4 < 8; ++k4) {
+      float a[4], d[4];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) d = fmaf(g[c], sw[ENC_W2 + k * 16 + c], d);
-      r1_out[r * 32 + k] = fmaxf(a, 0.f);
-      da1_out[r * 32 + k] = a > 0.f ? d : 0.f;
-    }
-  }
-}
-
-// Weight gradient sum_r A[r, :P]^T B[r, :Q] (plus the column sums of B as row P when
-// the bias row is wanted).  Block b reduces rows [b*chunk, (b+1)*chunk) in float32;
-// partials[b][(P+1)*Q].
-constexpr int WG_CHUNK = 4096;
-constexpr int WG_TILE = 32;
-
-__global__ void __launch_bounds__(256)
-k_wgrad(const float* __restrict__ A, int P, const float* __restrict__ Bm, int Q, long long R,
-        float* __restrict__ partials) {
-  __shared__ float sA[WG_TILE][33];
-  __shared__ float sB[WG_TILE][33];
-  const int PQ = (P + 1) * Q;
-  const long long r0 = (long long)blockIdx.x * WG_CHUNK;
-  const long long r1 = min(R, r0 + WG_CHUNK);
-  float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (long long rt = r0; rt < r1; rt += WG_TILE) {
-    const int rows = (int)min((long long)WG_TILE, r1 - rt);
-    for (int t = threadIdx.x; t < WG_TILE * 32; t += blockDim.x) {
-      const int rr = t / 32, c = t % 32;
-      float a = 0.f, b = 0.f;
-      if (rr < rows) {
-        if (c < P) a = A[(rt + rr) * P + c];
-        else if (c == P) a = 1.f;
-        if (c < Q) b = Bm[(rt + rr) * Q + c];
-      }
-      sA[rr][c] = a;
-      sB[rr][c] = b;
-    }
-    __syncthreads();
+      for (int j = 0; j < 4; ++j) {
+        const int k = 4 * k4 + j;
+        a[j] = fmaf(uv, sw[ENC_W1 + k], sw[ENC_B1 + k]);
+        float dd = 0.f;
 #pragma unroll
-    for (int s = 0; s < 5; ++s) {
-      const int o = threadIdx.x + 256 * s;
-      if (o < PQ) {
-        const int p = o / Q, q = o % Q;
-        float a = acc[s];
-        if (p < 32) {
-          for (int rr = 0; rr < rows; ++rr) a = fmaf(sA[rr][p], sB[rr][q], a);
-        } else {
-          for (int rr = 0; rr < rows; ++rr) a += sB[rr][q];
+        for (int q = 0; q < 4; ++q) {
+          const float4 wv = *reinterpret_cast<const float4*>(sw + ENC_W2 + k * 16 + 4 * q);
+          dd = fmaf(g[4 * q], wv.x, dd);
+          dd = fmaf(g[4 * q + 1], wv.y, dd);
+          dd = fmaf(g[4 * q + 2], wv.z, dd);
+          dd = fmaf(g[4 * q + 3], wv.w, dd);
         }
-        acc[s] = a;
+        d[j] = dd;
       }
+      ro[k4] = make_float4(fmaxf(a[0], 0.f), fmaxf(a[1], 0.f), fmaxf(a[2], 0.f), fmaxf(a[3], 0.f));
+      dao[k4] = make_float4(a[0] > 0.f ? d[0] : 0.f, a[1] > 0.f ? d[1] : 0.f, a[2] > 0.f ? d[2] : 0.f,
+                            a[3] > 0.f ? d[3] : 0.f);
     }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int o = threadIdx.x + 256 * s;
-    if (o < PQ) partials[(size_t)blockIdx.x * PQ + o] = acc[s];
   }
 }
 
-// Fixed-order float64 sum of the partials; rows 0..P-1 -> W (P x Q row-major),
-// row P -> bias (may be null).
-__global__ void k_wgrad_final(const float* __restrict__ partials, int nblocks, int P, int Q,
-                              float* __restrict__ Wout, float* __restrict__ bias) {
+// Weight gradient C = sum_r A'[r]^T B[r] over the R rows, A' = [A[r, :P], 1] (the ones
+// column gives the bias row P, the column sums of B).  A split-K reduction: block b owns
+// rows [b*WG_CHUNK, (b+1)*WG_CHUNK) and streams them through shared memory in tiles of
+// WG_KT rows, the next tile's loads in flight while the current one is used.  Thread
+// (g, p, q0) accumulates outputs (p, q0..q0+TN) over the rows g, g+RG, ... of every
+// tile (TN = 4 columns per thread: one broadcast A load and one 16-byte B load per four
+// FMAs); the RG row-group partials are added in a fixed order at the end, and
+// k_wgrad_final adds the block partials in float64, also in a fixed order.
+constexpr int WG_CHUNK = 2048;
+constexpr int WG_KT = 64;
+
+template <int P, int Q>
+struct WgShape {
+  static constexpr int TN = Q >= 4 ? 4 : 1;
+  static constexpr int NQ = Q / TN;
+  static constexpr int NP = P + 1;
+  static constexpr int TPG = NP * NQ;  // threads per row group
+  static constexpr int RG = 256 / TPG;
+  static_assert(RG >= 1 && Q % TN == 0, "output tile larger than a block");
+  static constexpr int A4 = WG_KT * P / 4;  // float4 per tile of A
+  static constexpr int B4 = WG_KT * Q / 4;
+  static constexpr int LA = (A4 + 255) / 256;  // float4 loads per thread
+  static constexpr int LB = (B4 + 255) / 256;
+};
+
+template <int P, int Q>
+__global__ void __launch_bounds__(256)
+k_wgrad(const float* __restrict__ A, const float* __restrict__ Bm, long long R, float* __restrict__ partials) {
+  using S = WgShape<P, Q>;
+  constexpr int TN = S::TN, NQ = S::NQ, NP = S::NP, TPG = S::TPG, RG = S::RG;
+  __shared__ __align__(16) float sA[WG_KT * P + 4];
+  __shared__ __align__(16) float sB[WG_KT * Q];
+  __shared__ float sred[RG > 1 ? RG * NP * Q : 1];
+  const int t = threadIdx.x;
+  const int g = t / TPG, o = t % TPG;
+  const int p = o / NQ, q0 = (o % NQ) * TN;
+  const bool active = g < RG;
+  const long long r0 = (long long)blockIdx.x * WG_CHUNK;
+  const int rows = (int)min((long long)WG_CHUNK, R - r0);  // a multiple of 4 (R = n B, B >= 4)
+  const int ntiles = (rows + WG_KT - 1) / WG_KT;
+  float acc[TN];
+#pragma unroll
+  for (int k = 0; k < TN; ++k) acc[k] = 0.f;
+  float4 ra[S::LA], rb[S::LB];
+  auto load = [&](int kt) {
+    const int nr = min(WG_KT, rows - kt * WG_KT);
+    const float4* a4 = reinterpret_cast<const float4*>(A + (r0 + (long long)kt * WG_KT) * P);
+    const float4* b4 = reinterpret_cast<const float4*>(Bm + (r0 + (long long)kt * WG_KT) * Q);
+#pragma unroll
+    for (int u = 0; u < S::LA; ++u) {
+      const int i = t + 256 * u;
+      ra[u] = (i < S::A4 && i < nr * P / 4) ? __ldg(a4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < S::LB; ++u) {
+      const int i = t + 256 * u;
+      rb[u] = (i < S::B4 && i < nr * Q / 4) ? __ldg(b4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  load(0);
+  for (int kt = 0; kt < ntiles; ++kt) {
+    __syncthreads();  // the previous tile is consumed
+#pragma unroll
+    for (int u = 0; u < S::LA; ++u) {
+      const int i = t + 256 * u;
+      if (i < S::A4) reinterpret_cast<float4*>(sA)[i] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < S::LB; ++u) {
+      const int i = t + 256 * u;
+      if (i < S::B4) reinterpret_cast<float4*>(sB)[i] = rb[u];
+    }
+    __syncthreads();
+    if (kt + 1 < ntiles) load(kt + 1);
+    // rows past the end of the chunk were loaded as zeros: they add nothing, except to
+    // the bias row, whose A' entry is 1 but whose B row is zero
+    if (active) {
+#pragma unroll 4
+      for (int rr = g; rr < WG_KT; rr += RG) {
+        const float av = p < P ? sA[rr * P + p] : 1.0f;
+        if constexpr (TN == 4) {
+          const float4 bv = *reinterpret_cast<const float4*>(sB + rr * Q + q0);
+          acc[0] = fmaf(av, bv.x, acc[0]);
+          acc[1] = fmaf(av, bv.y, acc[1]);
+          acc[2] = fmaf(av, bv.z, acc[2]);
+          acc[3] = fmaf(av, bv.w, acc[3]);
+        } else {
+          acc[0] = fmaf(av, sB[rr * Q + q0], acc[0]);
+        }
+      }
+    }
+  }
+  float* out = partials + (size_t)blockIdx.x * NP * Q;
+  if constexpr (RG == 1) {
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < TN; ++k) out[p * Q + q0 + k] = acc[k];
+    }
+  } else {
+    if (active) {
+#pragma unroll
+      for (int k = 0; k < TN; ++k) sred[g * NP * Q + p * Q + q0 + k] = acc[k];
+    }
+    __syncthreads();
+    for (int e = t; e < NP * Q; e += 256) {
+      float v = 0.f;
+#pragma unroll
+      for (int gg = 0; gg < RG; ++gg) v += sred[gg * NP * Q + e];
+      out[e] = v;
+    }
+  }
+}
+
+// Fixed-order float64 sum of the block partials, one warp per output (lanes stride the
+// blocks, then a fixed shuffle tree); rows 0..P-1 -> W (P x Q row-major), row P -> bias
+// (may be null).
+__global__ void __launch_bounds__(256)
+k_wgrad_final(const float* __restrict__ partials, int nblocks, int P, int Q, float* __restrict__ Wout,
+              float* __restrict__ bias) {
   const int PQ = (P + 1) * Q;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < PQ; o += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += (double)partials[(size_t)b * PQ + o];
+  const int lane = threadIdx.x & 31;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (o >= PQ) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += (double)partials[(size_t)b * PQ + o];
+  s = warp_sum(s);
+  if (lane == 0) {
     const int p = o / Q, q = o % Q;
     if (p < P) Wout[p * Q + q] = (float)s;
     else if (bias) bias[q] = (float)s;
@@ -868,7 +1007,10 @@ static int forward_batch(gnp_model* M, const float* b, cudaStream_t st) {
   const long long R = T->R;
   const double sqrt_n = std::sqrt((double)n);
   const int nb = red_blocks(R);
-  k_col_norms<<<nb, 256, 0, st>>>(b, R, B, T->red.partials, T->red.counter, T->tau);
+  if (M->cfg.no_scale)
+    k_fill_tau<<<1, 64, 0, st>>>(T->tau, B, sqrt_n);  // u = b, z = network output
+  else
+    k_col_norms<<<nb, 256, 0, st>>>(b, R, B, T->red.partials, T->red.counter, T->tau);
   k_enc_batch<<<grid_rows(R), 256, 0, st>>>(b, T->tau, R, B, sqrt_n, M->w_dev, T->u, T->Hs);
   const int smem = layer_smem(B);
   const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
@@ -890,18 +1032,18 @@ static int forward_batch(gnp_model* M, const float* b, cudaStream_t st) {
   return check_launch("forward_batch");
 }
 
-static int wgrad(TrainState* T, const float* A, int P, const float* Bm, int Q, float* Wout, float* bias,
-                 cudaStream_t st) {
+template <int P, int Q>
+static int wgrad(TrainState* T, const float* A, const float* Bm, float* Wout, float* bias, cudaStream_t st) {
   const int nblk = (int)((T->R + WG_CHUNK - 1) / WG_CHUNK);
   const int PQ = (P + 1) * Q;
-  if (T->part_cap < nblk * PQ) {
+  if (T->part_cap < nblk * 33 * 32) {
     if (T->partials) cudaFree(T->partials);
     T->partials = nullptr;
     GNP_TRY(dev_alloc(&T->partials, (size_t)nblk * 33 * 32));
     T->part_cap = nblk * 33 * 32;
   }
-  k_wgrad<<<nblk, 256, 0, st>>>(A, P, Bm, Q, T->R, T->partials);
-  k_wgrad_final<<<(PQ + 255) / 256, 256, 0, st>>>(T->partials, nblk, P, Q, Wout, bias);
+  k_wgrad<P, Q><<<nblk, 256, 0, st>>>(A, Bm, T->R, T->partials);
+  k_wgrad_final<<<(PQ * 32 + 255) / 256, 256, 0, st>>>(T->partials, nblk, P, Q, Wout, bias);
   return check_launch("wgrad");
 }
 
@@ -918,8 +1060,8 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
   k_dec_bwd<<<grid_rows(R), 256, 0, st>>>(HL, dz, T->tau, R, B, sqrt_n, M->w_dev + dec_off(L), T->r1, T->s32a,
                                           T->s32b, T->g16a);
   float* gd = g + dec_off(L);
-  GNP_TRY(wgrad(T, HL, 16, T->s32b, 32, gd, gd + 512, st));          // dD1, de1
-  GNP_TRY(wgrad(T, T->s32a, 32, T->r1, 1, gd + 544, gd + 576, st));   // dD2, de2
+  GNP_TRY((wgrad<16, 32>(T, HL, T->s32b, gd, gd + 512, st)));          // dD1, de1
+  GNP_TRY((wgrad<32, 1>(T, T->s32a, T->r1, gd + 544, gd + 576, st)));   // dD2, de2
   float* G = T->g16a;
   float* Gn = T->g16b;
   const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
@@ -928,23 +1070,23 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
     const float* AG = T->AGG + (size_t)l * R * 16;
     const float* lw = M->w_dev + layer_off(l);
     if (M->cfg.form == GNP_LAYER_PAPER)
-      k_layer_bwd_rows<GNP_LAYER_PAPER><<<grid_rows(R), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+      k_layer_bwd_rows<GNP_LAYER_PAPER><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
     else
-      k_layer_bwd_rows<GNP_LAYER_RESID><<<grid_rows(R), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+      k_layer_bwd_rows<GNP_LAYER_RESID><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
     // dX = local + A_hat^T Y (gather through the canonical CSC)
     k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->csc.ptr, A->csc.idx, M->valhat_t,
                                         reinterpret_cast<const float4*>(T->y16), n, B * 4, 1.0f,
                                         reinterpret_cast<const float4*>(Gn), 1.0f, reinterpret_cast<float4*>(Gn));
     float* gl = g + layer_off(l);
-    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY(wgrad(T, X, 16, T->gp16, 16, gl, nullptr, st));  // dU
+    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((wgrad<16, 16>(T, X, T->gp16, gl, nullptr, st)));  // dU
     else GNP_TRY_CUDA(cudaMemsetAsync(gl, 0, sizeof(float) * 256, st));
-    GNP_TRY(wgrad(T, AG, 16, T->gp16, 16, gl + 256, nullptr, st));  // dW
+    GNP_TRY((wgrad<16, 16>(T, AG, T->gp16, gl + 256, nullptr, st)));  // dW
     std::swap(G, Gn);
   }
   // encoder: r1 -> s32a, da1 -> s32b
   k_enc_bwd<<<grid_rows(R), 256, 0, st>>>(T->u, G, R, M->w_dev, T->s32a, T->s32b);
-  GNP_TRY(wgrad(T, T->s32a, 32, G, 16, g + ENC_W2, g + ENC_B2, st));  // dW2, db2
-  GNP_TRY(wgrad(T, T->u, 1, T->s32b, 32, g + ENC_W1, g + ENC_B1, st)); // dW1, db1
+  GNP_TRY((wgrad<32, 16>(T, T->s32a, G, g + ENC_W2, g + ENC_B2, st)));  // dW2, db2
+  GNP_TRY((wgrad<1, 32>(T, T->u, T->s32b, g + ENC_W1, g + ENC_B1, st))); // dW1, db1
   return check_launch("backward_batch");
 }
 
@@ -967,7 +1109,8 @@ static int sampler_prepare(gnp_model* M, cudaStream_t st) {
   // H_bar of A_hat = H_bar of A / gamma (same basis V); compact to (k+1) x k
   std::vector<double> Hk((size_t)(k + 1) * k);
   for (int j = 0; j < k; ++j)
-    for (int i = 0; i <= k; ++i) Hk[(size_t)j * (k + 1) + i] = Hh[(size_t)j * (m + 1) + i] / M->gamma;
+    for (int i = 0; i <= k; ++i)  // upper Hessenberg: zero below the subdiagonal
+      Hk[(size_t)j * (k + 1) + i] = i <= j + 1 ? Hh[(size_t)j * (m + 1) + i] / M->gamma : 0.0;
   if (T->Hbar) cudaFree(T->Hbar);
   T->Hbar = nullptr;
   if (T->Q) cudaFree(T->Q);
@@ -983,27 +1126,33 @@ static int sampler_prepare(gnp_model* M, cudaStream_t st) {
   return GNP_OK;
 }
 
+// The batch of step `step`: sample_mode 0 (Sec. 3) fills the first B/2 columns with
+// Eq. 5 samples and the rest with N(0, I); modes 1 and 2 (the Sec. 4 ablations) fill all
+// B columns with N(0, I) (read as x in mode 1, as b in mode 2).
 static int sample_batch(gnp_model* M, int step, float* x, cudaStream_t st) {
   TrainState* T = M->train;
-  GNP_TRY(sampler_prepare(M, st));
-  const int n = M->A->n, B = T->B, Ba = B / 2, mA = T->mA;
-  if (!T->C) GNP_TRY(dev_alloc(&T->C, (size_t)SVD_MAX * GNP_MAX_BATCH));
-  k_sampler_coef<<<1, 256, 0, st>>>(T->Q, mA, Ba, M->cfg.seed, (uint32_t)step, T->C);
+  const int n = M->A->n, B = T->B;
+  const int Ba = M->cfg.sample_mode == 0 ? B / 2 : 0;
+  int mA = 0;
+  if (Ba > 0) {
+    GNP_TRY(sampler_prepare(M, st));
+    mA = T->mA;
+    if (!T->C) GNP_TRY(dev_alloc(&T->C, (size_t)SVD_MAX * GNP_MAX_BATCH));
+    k_sampler_coef<<<1, 256, 0, st>>>(T->Q, mA, Ba, M->cfg.seed, (uint32_t)step, T->C);
+  }
   k_sampler_x<<<grid_rows((long long)n * B), 256, 0, st>>>(T->V, n, mA, T->C, B, Ba, M->cfg.seed,
                                                            (uint32_t)step, x);
   return check_launch("sample_batch");
 }
 
-// b = A_hat x, forward, loss, dz, backward, Adam.  No host synchronisation.
-static int train_pairs(gnp_model* M, const float* x, cudaStream_t st) {
+// Forward on T->bb, loss, dz, backward, Adam.  No host synchronisation.
+static int train_from_b(gnp_model* M, cudaStream_t st) {
   TrainState* T = M->train;
   const gnp_mat* A = M->A;
   const int n = A->n, B = T->B;
   const long long R = T->R;
   const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
   const int W4 = B / 4;
-  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(x), n, W4, 1.0f,
-                                      nullptr, 0.0f, reinterpret_cast<float4*>(T->bb));
   GNP_TRY(forward_batch(M, T->bb, st));
   // r = A_hat z - b; loss = mean |r|; s = sign(r); dz = A_hat^T s / (n B)
   k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(T->z), n, W4,
@@ -1020,6 +1169,29 @@ static int train_pairs(gnp_model* M, const float* x, cudaStream_t st) {
   M->host_stale = true;
   ++M->version;
   return check_launch("train step");
+}
+
+// b = A_hat x, then train_from_b.
+static int train_pairs(gnp_model* M, const float* x, cudaStream_t st) {
+  TrainState* T = M->train;
+  const gnp_mat* A = M->A;
+  const int n = A->n;
+  const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
+  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(x), n, T->B / 4,
+                                      1.0f, nullptr, 0.0f, reinterpret_cast<float4*>(T->bb));
+  return train_from_b(M, st);
+}
+
+// One step on the model's own sampler (sample_mode 2 samples b directly).
+static int train_step_own(gnp_model* M, cudaStream_t st) {
+  TrainState* T = M->train;
+  const int step = T->step++;
+  if (M->cfg.sample_mode == 2) {
+    GNP_TRY(sample_batch(M, step, T->bb, st));
+    return train_from_b(M, st);
+  }
+  GNP_TRY(sample_batch(M, step, T->xb, st));
+  return train_pairs(M, T->xb, st);
 }
 
 static int train_prepare(gnp_model* M, int B, cudaStream_t st) {
@@ -1098,9 +1270,7 @@ int gnp_train_step(gnp_model* M, float* loss_out, void* stream) {
   cudaStream_t st = as_stream(stream);
   GNP_TRY(train_prepare(M, M->cfg.batch, st));
   TrainState* T = M->train;
-  GNP_TRY(sample_batch(M, T->step, T->xb, st));
-  ++T->step;
-  GNP_TRY(train_pairs(M, T->xb, st));
+  GNP_TRY(train_step_own(M, st));
   if (loss_out) {
     GNP_TRY_CUDA(cudaMemcpyAsync(loss_out, T->loss, sizeof(float), cudaMemcpyDeviceToHost, st));
     GNP_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1116,22 +1286,43 @@ int gnp_train_release(gnp_model* M) {
   return GNP_OK;
 }
 
-int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream) {
+int gnp_train_history(gnp_model* M, int steps, float* losses_out, float* best_loss_out, void* stream) {
   GNP_REQUIRE(M && steps >= 0, "gnp_train: bad argument");
   cudaStream_t st = as_stream(stream);
   GNP_TRY(train_prepare(M, M->cfg.batch, st));
   TrainState* T = M->train;
-  GNP_TRY(sampler_prepare(M, st));
-  for (int s = 0; s < steps; ++s) {
-    GNP_TRY(sample_batch(M, T->step, T->xb, st));
-    ++T->step;
-    GNP_TRY(train_pairs(M, T->xb, st));
+  if (M->cfg.sample_mode == 0) GNP_TRY(sampler_prepare(M, st));
+  float* hist = nullptr;
+  if (losses_out && steps > 0) GNP_TRY(dev_alloc(&hist, (size_t)steps));
+  int e = GNP_OK;
+  for (int s = 0; s < steps && e == GNP_OK; ++s) {
+    e = train_step_own(M, st);
+    if (e == GNP_OK && hist && cudaMemcpyAsync(hist + s, T->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) !=
+                                   cudaSuccess) {
+      set_error("gnp_train: loss copy failed");
+      e = GNP_ERR_CUDA;
+    }
   }
-  if (best_loss_out) {
-    GNP_TRY_CUDA(cudaMemcpyAsync(best_loss_out, T->best_loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (e == GNP_OK && hist &&
+      cudaMemcpyAsync(losses_out, hist, sizeof(float) * steps, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    set_error("gnp_train: loss history copy failed");
+    e = GNP_ERR_CUDA;
   }
-  GNP_TRY_CUDA(cudaStreamSynchronize(st));
-  return GNP_OK;
+  if (e == GNP_OK && best_loss_out &&
+      cudaMemcpyAsync(best_loss_out, T->best_loss, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+    set_error("gnp_train: best loss copy failed");
+    e = GNP_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && e == GNP_OK) {
+    set_error("gnp_train: %s", cudaGetErrorString(cudaGetLastError()));
+    e = GNP_ERR_CUDA;
+  }
+  dev_free(hist);
+  return e;
+}
+
+int gnp_train(gnp_model* M, int steps, float* best_loss_out, void* stream) {
+  return gnp_train_history(M, steps, nullptr, best_loss_out, stream);
 }
 
 }  // extern "C"

@@ -1,4 +1,6 @@
 // Error reporting, status names and small allocation helpers.
+#include <cfloat>
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
 
@@ -64,6 +66,27 @@ const char* gnp_status_string(int s) {
 }
 
 const char* gnp_last_error(void) { return gnp::g_err; }
+
+// Sec. 3 "Evaluation metrics": areas under the log10 relative-residual curve above
+// log10 rtol, per iteration (from i = 0) and per unit of time (from i = 1, each term
+// weighted by the time that iteration took).
+static double log_excess(double r, double lrtol) { return std::log10(r > 0.0 ? r : DBL_MIN) - lrtol; }
+
+double gnp_iter_auc(const double* res_history, int len, double rtol) {
+  if (!res_history || len < 1 || !(rtol > 0.0)) return NAN;
+  const double lr = std::log10(rtol);
+  double s = 0.0;
+  for (int i = 0; i < len; ++i) s += log_excess(res_history[i], lr);
+  return s;
+}
+
+double gnp_time_auc(const double* res_history, const double* time_history, int len, double rtol) {
+  if (!res_history || !time_history || len < 1 || !(rtol > 0.0)) return NAN;
+  const double lr = std::log10(rtol);
+  double s = 0.0;
+  for (int i = 1; i < len; ++i) s += log_excess(res_history[i], lr) * (time_history[i] - time_history[i - 1]);
+  return s;
+}
 
 int gnp_weight_count(int L) {
   if (L < 0 || L > GNP_MAX_LAYERS) return -1;

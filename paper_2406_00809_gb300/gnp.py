@@ -34,7 +34,8 @@ class GnpError(RuntimeError):
 class GnpConfig(C.Structure):
     _fields_ = [("L", C.c_int), ("form", C.c_int), ("hprec", C.c_int), ("batch", C.c_int),
                 ("arnoldi_m", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
-                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_ulonglong)]
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_ulonglong),
+                ("sample_mode", C.c_int), ("no_scale", C.c_int)]
 
 
 class _SolveInfo(C.Structure):
@@ -43,7 +44,7 @@ class _SolveInfo(C.Structure):
                 ("seconds", C.c_double), ("res_history", C.POINTER(C.c_double)),
                 ("res_history_len", C.c_int), ("hessenberg", C.POINTER(C.c_double)),
                 ("hessenberg_cols", C.c_int), ("cycles", C.c_int), ("gconv_launches", C.c_int),
-                ("gconv_ms", C.c_double)]
+                ("gconv_ms", C.c_double), ("time_history", C.POINTER(C.c_double))]
 
 
 class _ServerConfig(C.Structure):
@@ -92,10 +93,18 @@ def lib():
         "gnp_train_step_pairs": (i, [vp, vp, i, C.POINTER(f), vp]),
         "gnp_train_step": (i, [vp, C.POINTER(f), vp]),
         "gnp_train": (i, [vp, i, C.POINTER(f), vp]),
+        "gnp_train_history": (i, [vp, i, vp, C.POINTER(f), vp]),
         "gnp_set_weights_device": (i, [vp, vp, i, vp]),
         "gnp_train_release": (i, [vp]),
         "gnp_philox4x32_10": (i, [vp, C.c_uint, C.c_uint, i, vp, vp]),
         "fgmres_solve": (i, [vp, vp, vp, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
+        "fgmres_solve_timeout": (i, [vp, vp, vp, vp, i, d, i, d, C.POINTER(_SolveInfo), vp]),
+        "fgmres_solve_precond": (i, [vp, vp, vp, vp, i, d, i, d, C.POINTER(_SolveInfo), vp]),
+        "gnp_precond_create": (i, [vp, i, vp, i, d, pp]),
+        "gnp_precond_destroy": (None, [vp]),
+        "gnp_precond_apply": (i, [vp, vp, vp, vp]),
+        "gnp_iter_auc": (d, [C.POINTER(C.c_double), i, d]),
+        "gnp_time_auc": (d, [C.POINTER(C.c_double), C.POINTER(C.c_double), i, d]),
         "gnp_profile_gconv": (i, [i]),
         "gnp_gamma_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp, vp]),
         "gnp_server_create": (i, [C.POINTER(_ServerConfig), pp]),
@@ -216,9 +225,14 @@ def gnp_spmv(A: Mat, x, y, stream=None):
 
 # --------------------------------------------------------------------- model
 
+SAMPLE_MIX, SAMPLE_X_NORMAL, SAMPLE_B_NORMAL = 0, 1, 2
+
+
 def make_config(L=8, form=LAYER_PAPER, hprec=H_FP32, batch=16, arnoldi_m=40, lr=1e-3,
-                beta1=0.9, beta2=0.999, eps=1e-8, seed=0) -> GnpConfig:
-    return GnpConfig(L, form, hprec, batch, arnoldi_m, lr, beta1, beta2, eps, seed)
+                beta1=0.9, beta2=0.999, eps=1e-8, seed=0, sample_mode=SAMPLE_MIX,
+                no_scale=False) -> GnpConfig:
+    return GnpConfig(L, form, hprec, batch, arnoldi_m, lr, beta1, beta2, eps, seed, sample_mode,
+                     1 if no_scale else 0)
 
 
 class Model:
@@ -240,6 +254,39 @@ def gnp_create(A: Mat, cfg: GnpConfig, weights) -> Model:
     out = C.c_void_p()
     _check(lib().gnp_create(A.h, C.byref(cfg), w.ctypes.data, C.byref(out)))
     return Model(out, A, cfg)
+
+
+PRECOND_IDENTITY, PRECOND_GNP, PRECOND_JACOBI, PRECOND_GMRES = 0, 1, 2, 3
+
+
+class Precond:
+    """A right preconditioner handle (gnp_precond): identity, GNP, Jacobi or inner GMRES."""
+
+    def __init__(self, handle, A: Mat, kind: int, M: Model | None):
+        self.h = handle
+        self.A = A
+        self.kind = kind
+        self.M = M  # keep the model alive
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.gnp_precond_destroy(self.h)
+            self.h = None
+
+
+def gnp_precond_create(A: Mat, kind: int, M: Model | None = None, inner_iters: int = 10,
+                       inner_rtol: float = 1e-6) -> Precond:
+    out = C.c_void_p()
+    _check(lib().gnp_precond_create(A.h, kind, M.h if M is not None else None, inner_iters, inner_rtol,
+                                    C.byref(out)))
+    return Precond(out, A, kind, M)
+
+
+def gnp_precond_apply(P: Precond, v, z, stream=None):
+    """z = P(v) for float64 CUDA vectors."""
+    import torch
+    _check(lib().gnp_precond_apply(P.h, _dptr(v, torch.float64, "v"), _dptr(z, torch.float64, "z"),
+                                   _stream(stream)))
 
 
 def gnp_model_gamma(M: Model) -> float:
@@ -345,6 +392,15 @@ def gnp_train(M: Model, steps: int, stream=None) -> float:
     return best.value
 
 
+def gnp_train_history(M: Model, steps: int, stream=None):
+    """(per-step losses, best loss) of `steps` training steps."""
+    losses = np.zeros(steps, dtype=np.float32)
+    best = C.c_float(0.0)
+    _check(lib().gnp_train_history(M.h, steps, losses.ctypes.data if steps else None, C.byref(best),
+                                   _stream(stream)))
+    return losses, best.value
+
+
 # --------------------------------------------------------------------- solver
 
 def gnp_profile_gconv(on: bool):
@@ -360,6 +416,7 @@ class SolveInfo:
     rel_res_true: float
     seconds: float
     history: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    times: np.ndarray | None = None
     hessenberg: np.ndarray | None = None
     cycles: int = 0
     gconv_launches: int = 0
@@ -370,20 +427,30 @@ class SolveInfo:
         return STATUS.get(self.status, str(self.status))
 
 
-def fgmres_solve(A: Mat, b, x, M: Model | None = None, restart=30, rtol=1e-8, maxiters=1000,
-                 stream=None, history=True, hessenberg=False, check=False) -> SolveInfo:
-    """Solve A x = b (float64 CUDA tensors; x holds x0 on entry)."""
+def fgmres_solve(A: Mat, b, x, M: Model | Precond | None = None, restart=30, rtol=1e-8, maxiters=1000,
+                 stream=None, history=True, hessenberg=False, check=False, timeout=0.0,
+                 times=False) -> SolveInfo:
+    """Solve A x = b (float64 CUDA tensors; x holds x0 on entry).  timeout > 0 (seconds)
+    calls fgmres_solve_timeout; times=True also returns the per-iteration device times."""
     import torch
     info = _SolveInfo()
     hist = np.zeros(maxiters + 1) if history else None
+    thist = np.zeros(maxiters + 1) if times else None
     hess = np.zeros((restart, restart + 1)) if hessenberg else None
     if hist is not None:
         info.res_history = hist.ctypes.data_as(C.POINTER(C.c_double))
+    if thist is not None:
+        info.time_history = thist.ctypes.data_as(C.POINTER(C.c_double))
     if hess is not None:
         info.hessenberg = hess.ctypes.data_as(C.POINTER(C.c_double))
-    st = lib().fgmres_solve(A.h, _dptr(b, torch.float64, "b"), _dptr(x, torch.float64, "x"),
-                            M.h if M is not None else None, restart, rtol, maxiters, C.byref(info),
-                            _stream(stream))
+    args = (A.h, _dptr(b, torch.float64, "b"), _dptr(x, torch.float64, "x"), M.h if M is not None else None,
+            restart, rtol, maxiters)
+    if isinstance(M, Precond):
+        st = lib().fgmres_solve_precond(*args, timeout, C.byref(info), _stream(stream))
+    elif timeout != 0.0:
+        st = lib().fgmres_solve_timeout(*args, timeout, C.byref(info), _stream(stream))
+    else:
+        st = lib().fgmres_solve(*args, C.byref(info), _stream(stream))
     if check:
         _check(st)
     elif st not in STATUS:
@@ -392,10 +459,28 @@ def fgmres_solve(A: Mat, b, x, M: Model | None = None, restart=30, rtol=1e-8, ma
                     cycles=info.cycles, gconv_launches=info.gconv_launches, gconv_ms=info.gconv_ms)
     if hist is not None:
         out.history = hist[:info.res_history_len].copy()
+    if thist is not None:
+        out.times = thist[:info.iters + 1].copy()
     if hess is not None:
         cols = info.hessenberg_cols
         out.hessenberg = hess.T[:cols + 1, :cols].copy()  # column-major (m+1) x m
     return out
+
+
+def iter_auc(history, rtol: float) -> float:
+    """Iter-AUC of a residual history (Sec. 3 "Evaluation metrics"), computed by the library."""
+    h = np.ascontiguousarray(history, dtype=np.float64)
+    return float(lib().gnp_iter_auc(h.ctypes.data_as(C.POINTER(C.c_double)), len(h), rtol))
+
+
+def time_auc(history, times, rtol: float) -> float:
+    """Time-AUC of a residual history and its per-iteration times (seconds)."""
+    h = np.ascontiguousarray(history, dtype=np.float64)
+    t = np.ascontiguousarray(times, dtype=np.float64)
+    if len(t) != len(h):
+        raise ValueError("history and times differ in length")
+    return float(lib().gnp_time_auc(h.ctypes.data_as(C.POINTER(C.c_double)),
+                                    t.ctypes.data_as(C.POINTER(C.c_double)), len(h), rtol))
 
 
 # --------------------------------------------------------------------- autograd

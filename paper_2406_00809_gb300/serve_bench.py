@@ -1,7 +1,7 @@
 """Serving benchmark: p50/p99 latency and solves/s of the continuous-batching server.
 
-    python -m paper_2406_00809_gb300.serve_bench [--requests 512] [--rates 8,32,128]
-        [--pool 12] [--nmin 1e4] [--nmax 2e6] [--train-steps 40] [--hprec bf16]
+    python -m paper_2406_00809_gb300.serve_bench [--requests 128] [--load 0.25,0.5,1,2]
+        [--pool 12] [--nmin 1e4] [--nmax 2e6] [--train-steps 300] [--hprec bf16]
 
 A pool of `pool` problems is built first (not timed): the three generator families
 (2-D Poisson, 2-D convection-diffusion, power-law general sparse) in turn, n drawn
@@ -13,7 +13,13 @@ picks a pool problem uniformly and has its own right-hand side b = A x, x ~ N(0,
 `maxiters` steps.  Requests arrive as a Poisson process at each swept rate (solves per
 second); latency = submit to finish, measured by the server's steady clock.  A pool
 (not a fresh matrix per request) keeps the set-up time bounded; every request still
-runs with its own workspace, right-hand side and solution.  One JSON line per rate.
+runs with its own workspace, right-hand side and solution.
+
+The arrival rates are multiples (--load) of the sequential capacity: one solve of every
+pool problem is first run alone through the server, and 1 / (mean solo latency) is the
+rate at which requests served one at a time would just keep up.  Load 1 and above
+therefore measure how much concurrent requests gain over serial service.  One JSON line
+per rate (plus one with the solo latencies).
 """
 from __future__ import annotations
 
@@ -114,18 +120,37 @@ def run_rate(g, srv, pool, args, rate, seed):
             "rounds": st["rounds"]}
 
 
+def solo_latencies(g, srv, pool, args):
+    """Each pool problem solved alone through the server (after a warm-up solve that
+    captures its graphs): its latency, iterations and status."""
+    import torch
+    out = []
+    for k, p in enumerate(pool):
+        gen = torch.Generator(device="cuda").manual_seed(10_000 + k)
+        xt = torch.randn(p["n"], dtype=torch.float64, device="cuda", generator=gen)
+        b = torch.empty_like(xt)
+        g.gnp_spmv(p["A"], xt, b)
+        x = torch.zeros_like(xt)
+        srv.wait(srv.submit(p["A"], p["M"], b, x, args.rtol, args.maxiters))
+        x.zero_()
+        res = srv.wait(srv.submit(p["A"], p["M"], b, x, args.rtol, args.maxiters))
+        out.append(dict(n=p["n"], fam=p["fam"], seconds=res.seconds, iters=res.iters, status=res.status_name))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--requests", type=int, default=512)
-    ap.add_argument("--rates", default="8,32,128")
+    ap.add_argument("--requests", type=int, default=128)
+    ap.add_argument("--load", default="0.25,0.5,1,2",
+                    help="arrival rates as multiples of the sequential capacity")
     ap.add_argument("--pool", type=int, default=12)
     ap.add_argument("--nmin", type=float, default=1e4)
     ap.add_argument("--nmax", type=float, default=2e6)
-    ap.add_argument("--train-steps", type=int, default=40)
+    ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--hprec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--maxiters", type=int, default=600)
+    ap.add_argument("--maxiters", type=int, default=1000)
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--max-gb", type=float, default=120.0)
     ap.add_argument("--seed", type=int, default=0)
@@ -141,9 +166,12 @@ def main():
     print(json.dumps({"pool": [{k: p[k] for k in ("fam", "n", "nnz", "train_s")} for p in pool],
                       "setup_s": setup_s}), flush=True)
     srv = g.Server(max_bytes=int(a.max_gb * (1 << 30)), max_active=a.max_active, restart=30)
-    for i, rate in enumerate(float(r) for r in a.rates.split(",")):
-        out = run_rate(g, srv, pool, a, rate, a.seed + 1 + i)
-        out.update({"metric": "serve latency", "hprec": a.hprec, "pool": a.pool,
+    solo = solo_latencies(g, srv, pool, a)
+    capacity = 1.0 / float(np.mean([s_["seconds"] for s_ in solo]))
+    print(json.dumps({"solo": solo, "sequential_capacity_per_s": capacity}), flush=True)
+    for i, load in enumerate(float(r) for r in a.load.split(",")):
+        out = run_rate(g, srv, pool, a, load * capacity, a.seed + 1 + i)
+        out.update({"metric": "serve latency", "load": load, "hprec": a.hprec, "pool": a.pool,
                     "n_range": [a.nmin, a.nmax], "train_steps": a.train_steps})
         print(json.dumps(out), flush=True)
     srv.close()

@@ -1,0 +1,110 @@
+"""The Sec. 4 ablations on the GPU against the float64 oracle: training without the
+scaling s, and training on x ~ N(0, I) or b ~ N(0, I) only.
+
+* no_scale: gnp_apply and the batched forward/backward equal the oracle's forward with
+  scaled=False (1e-5 / 1e-4), and the apply is no longer scale-equivariant.
+* sample_mode 1 / 2: every column of the sampled batch is the Philox N(0, I) draw of
+  stream 1 (element (i, c) at index i*B + c), like the Gaussian half of the paper's mix.
+* sample_mode 2 trains on b directly: one step equals the oracle's step on those b.
+* gnp_train_history returns the per-step losses; its first loss is the loss of the
+  initial weights on the first batch.
+"""
+import numpy as np
+import pytest
+
+from oracle import gnp_ref as G
+from oracle import philox_ref as PH
+from paper_2406_00809_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gnp():
+    import torch
+    from paper_2406_00809_gb300 import build, gnp as g
+    build.build()
+    assert torch.cuda.is_available()
+    return g
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_no_scale_apply_and_batch_match_oracle(gnp, form):
+    import torch
+    A = I.convdiff2d(24, 100.0)
+    n, L, B = A.n, 4, 8
+    blob = I.init_weights(L, seed=4)
+    blob[32:64] = np.random.default_rng(3).standard_normal(32) * 0.3  # biases break homogeneity
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L, form=form, batch=B, no_scale=True), blob)
+    Ahat = G.normalise(A.to_scipy())
+    P = G.unpack(blob, L)
+    v = I.gaussian(n, seed=5) * 3.0
+    z = torch.empty(n, dtype=torch.float32, device="cuda")
+    gnp.gnp_apply(M, torch.from_numpy(v).cuda(), z)
+    zr = G.forward(Ahat, v, P, form, scaled=False)
+    assert rel(z.cpu().numpy(), zr) <= 1e-5
+    z2 = torch.empty_like(z)
+    gnp.gnp_apply(M, torch.from_numpy(2.0 * v).cuda(), z2)
+    assert rel(z2.cpu().numpy(), 2.0 * z.cpu().numpy()) > 1e-4  # not equivariant
+    b = np.random.default_rng(1).standard_normal((n, B)).astype(np.float32)
+    c = np.random.default_rng(2).standard_normal((n, B)).astype(np.float32)
+    zb = torch.empty(n * B, dtype=torch.float32, device="cuda")
+    gnp.gnp_forward_batch(M, torch.from_numpy(b).cuda(), zb)
+    zbr, cache = G.forward(Ahat, b.astype(np.float64), P, form, keep=True, scaled=False)
+    assert rel(zb.cpu().numpy().reshape(n, B), zbr) <= 1e-5
+    g = torch.empty(gnp.weight_count(L), dtype=torch.float32, device="cuda")
+    gnp.gnp_backward_batch(M, torch.from_numpy(c).cuda().reshape(-1), g)
+    gr = G.pack(G.backward(Ahat, P, cache, c.astype(np.float64)))
+    assert rel(g.cpu().numpy(), gr) <= 1e-4
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_gaussian_only_sampling(gnp, mode):
+    import torch
+    A = I.poisson2d(20)
+    n, B, seed, step = A.n, 8, 21, 4
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=2, batch=B, seed=seed, sample_mode=mode), I.init_weights(2, seed=0))
+    x = torch.empty(n * B, dtype=torch.float32, device="cuda")
+    gnp.gnp_sample_batch(M, step, x)
+    gref = PH.normal(n * B, seed, step, PH.STREAM_X).reshape(n, B)
+    np.testing.assert_allclose(x.cpu().numpy().reshape(n, B), gref, rtol=0, atol=2e-5 * np.abs(gref).max())
+
+
+def test_b_sampling_trains_on_b(gnp):
+    import torch
+    A = I.convdiff2d(16, 100.0)
+    n, B, L, seed = A.n, 8, 2, 5
+    blob = I.init_weights(L, seed=2)
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L, batch=B, seed=seed, sample_mode=2), blob)
+    losses, best = gnp.gnp_train_history(M, 3)
+    assert len(losses) == 3 and best == pytest.approx(float(losses.min()))
+    Ahat = G.normalise(A.to_scipy())
+    b0 = PH.normal(n * B, seed, 0, PH.STREAM_X).reshape(n, B).astype(np.float32).astype(np.float64)
+    P = G.unpack(blob, L)
+    z = G.forward(Ahat, b0, P, 0)
+    lref, _ = G.l1_loss(Ahat, z, b0)
+    assert abs(losses[0] - lref) <= 1e-5 * lref
+    # the mix sampler's history starts from the same weights: its first loss is the loss
+    # of those weights on the mixed batch, a different number
+    M2 = gnp.gnp_create(Mt, gnp.make_config(L=L, batch=B, seed=seed, arnoldi_m=10), blob)
+    l2, _ = gnp.gnp_train_history(M2, 2)
+    assert l2[0] != losses[0]
+
+
+def test_ablation_script_runs(gnp, capsys):
+    """The Fig. 6 ablation script end to end on one small problem and few steps."""
+    from paper_2406_00809_gb300 import ablation
+    rows = ablation.main(["--problems", "poisson16", "--train-steps", "20"])
+    assert {r["variant"] for r in rows} == {"mix", "x_normal", "b_normal", "no_scale"}
+    for r in rows:
+        assert np.isfinite(r["best_loss"]) and r["best_loss"] > 0
+        assert r["status"] in ("GNP_OK", "GNP_ERR_NOT_CONVERGED", "GNP_ERR_STAGNATION")
+    out = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(out) == 5

@@ -128,3 +128,34 @@ def test_apply_scale_equivariance_and_zero(gnp):
     assert rel(z2.cpu().numpy(), 1e3 * z1.cpu().numpy()) <= 1e-6
     gnp.gnp_apply(M, dev(np.zeros(A.n), torch.float64), z1)
     assert torch.count_nonzero(z1).item() == 0
+
+
+@pytest.mark.parametrize("rows", ["128", "256"])
+@pytest.mark.parametrize("name", ["convdiff45", "powerlaw12k", "aniso9"])
+@pytest.mark.parametrize("hprec", [0, 1])
+@pytest.mark.parametrize("form", [0, 1])
+def test_apply_both_tile_shapes(gnp, rows, name, hprec, form, monkeypatch):
+    """Both Res-GCONV tile shapes (256 rows with one epilogue thread per row, 128 rows
+    with two) against the oracle, including the decoder-fused last layer and the traced
+    per-layer hidden blocks; the two shapes agree with each other to float32 rounding."""
+    import torch
+    A = MATS[name]()
+    L = 8
+    blob = I.init_weights(L, seed=11)
+    v = I.gaussian(A.n, seed=12)
+    zr = G.forward(G.normalise(A.to_scipy()), v, G.unpack(blob, L), form)
+    monkeypatch.setenv("GNP_GCONV_ROWS", rows)
+    z, M = run_apply(gnp, A, blob, L, form, hprec, v)
+    assert rel(z, zr) <= (F32_TOL if hprec == 0 else BF16_TOL), rel(z, zr)
+    if hprec == 0:
+        hid = torch.empty((L + 1) * A.n * 16, dtype=torch.float32, device="cuda")
+        zt = torch.empty(A.n, dtype=torch.float32, device="cuda")
+        gnp.gnp_apply_trace(M, dev(v, torch.float64), zt, hid)
+        Hs = G.hidden_trace(G.normalise(A.to_scipy()), v, G.unpack(blob, L), form)
+        hg = hid.cpu().numpy().reshape(L + 1, A.n, 16)
+        for l in range(L + 1):
+            assert rel(hg[l], Hs[l]) <= F32_TOL, l
+    other = "256" if rows == "128" else "128"
+    monkeypatch.setenv("GNP_GCONV_ROWS", other)
+    z2, _ = run_apply(gnp, A, blob, L, form, hprec, v)
+    assert rel(z2, z) <= (2e-6 if hprec == 0 else 1e-2)

@@ -49,8 +49,9 @@ def test_gamma_matches_matrix_norms():
 
 # ------------------------------------------------------- forward vs brute force
 
-def brute_force_M(Adense, b, blob, L, form):
-    """Eqs. 6-8 evaluated with explicit scalar loops over a dense matrix."""
+def brute_force_M(Adense, b, blob, L, form, scaled=True):
+    """Eqs. 6-8 evaluated with explicit scalar loops over a dense matrix (scaled=False:
+    the Sec. 4 ablation without s)."""
     n = len(b)
     d, hd = 16, 32
     w = [float(t) for t in blob]
@@ -71,8 +72,8 @@ def brute_force_M(Adense, b, blob, L, form):
     colsum = max(sum(abs(Adense[i][j]) for i in range(n)) for j in range(n))
     gam = min(rowsum, colsum)
     Ah = [[Adense[i][j] / gam for j in range(n)] for i in range(n)]
-    tau = sum(v * v for v in b) ** 0.5
-    u = [v * (n ** 0.5) / tau for v in b]
+    tau = sum(v * v for v in b) ** 0.5 if scaled else n ** 0.5
+    u = [v * (n ** 0.5) / tau for v in b] if scaled else list(b)
     H = []
     for i in range(n):
         hid = [max(0.0, u[i] * eW1[k] + eb1[k]) for k in range(hd)]
@@ -113,6 +114,13 @@ def test_forward_matches_brute_force(form):
     z = G.forward(Ahat, b, G.unpack(blob, L), form)
     zb = brute_force_M(D.tolist(), b.tolist(), blob, L, form)
     np.testing.assert_allclose(z, zb, rtol=1e-12, atol=1e-12)
+    # the ablation without s: the network sees b itself and returns its output unscaled
+    z0 = G.forward(Ahat, 5.0 * b, G.unpack(blob, L), form, scaled=False)
+    zb0 = brute_force_M(D.tolist(), (5.0 * b).tolist(), blob, L, form, scaled=False)
+    np.testing.assert_allclose(z0, zb0, rtol=1e-12, atol=1e-12)
+    # and it is not scale-equivariant (the ReLU MLPs have biases)
+    z1 = G.forward(Ahat, b, G.unpack(blob, L), form, scaled=False)
+    assert np.linalg.norm(z0 - 5.0 * z1) > 1e-3 * np.linalg.norm(z0)
 
 
 def test_linear_regime_kronecker_form():
@@ -186,8 +194,9 @@ def _numeric_grad(f, w, idx, h=1e-6):
     return g
 
 
+@pytest.mark.parametrize("scaled", [True, False])
 @pytest.mark.parametrize("form", [0, 1])
-def test_backward_matches_central_differences(form):
+def test_backward_matches_central_differences(form, scaled):
     rng = np.random.default_rng(7)
     A = I.convdiff2d(4).to_scipy()
     Ahat = G.normalise(A)
@@ -198,10 +207,10 @@ def test_backward_matches_central_differences(form):
     c = rng.standard_normal((n, B))
 
     def f(w):
-        return float((G.forward(Ahat, b, G.unpack(w, L), form) * c).sum())
+        return float((G.forward(Ahat, b, G.unpack(w, L), form, scaled=scaled) * c).sum())
 
     P = G.unpack(blob, L)
-    _, cache = G.forward(Ahat, b, P, form, keep=True)
+    _, cache = G.forward(Ahat, b, P, form, keep=True, scaled=scaled)
     g = G.pack(G.backward(Ahat, P, cache, c))
     idx = rng.choice(blob.size, 120, replace=False)
     gn = _numeric_grad(f, blob, idx)
@@ -230,3 +239,19 @@ def test_adam_first_step_moves_by_lr():
     # second step with the same gradient: m_hat = g, v_hat = g^2 again
     w2 = opt.step(w1, g)
     np.testing.assert_allclose(w1 - w2, 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_train_step_on_b_equals_train_step_on_x():
+    """The b ~ N(0, I) ablation trains on b directly; for an invertible A_hat that is the
+    step on x = A_hat^{-1} b (same loss, same update)."""
+    rng = np.random.default_rng(3)
+    A = I.convdiff2d(4).to_scipy()
+    Ahat = G.normalise(A)
+    L, B = 2, 4
+    blob = I.init_weights(L, seed=1).astype(np.float64)
+    b = rng.standard_normal((A.shape[0], B))
+    x = np.linalg.solve(Ahat.toarray(), b)
+    w1, l1 = G.train_step(Ahat, blob, L, 0, None, G.Adam(blob.size), b=b)
+    w2, l2 = G.train_step(Ahat, blob, L, 0, x, G.Adam(blob.size))
+    assert l1 == pytest.approx(l2, rel=1e-9)
+    np.testing.assert_allclose(w1, w2, rtol=0, atol=1e-9)
