@@ -50,6 +50,8 @@ extern "C" {
 #define GNP_MAX_LAYERS 32
 #define GNP_MAX_RESTART 128
 #define GNP_MAX_BATCH 64
+#define GNP_MAX_RHS 8             /* right-hand sides of one fgmres_solve_multi call */
+#define GNP_MAX_RESTART_MULTI 64  /* restart length of fgmres_solve_multi */
 
 typedef enum {
   GNP_OK = 0,
@@ -254,6 +256,27 @@ int fgmres_solve(gnp_mat* A, const double* b_dev, double* x_dev, gnp_model* M,
 int fgmres_solve_timeout(gnp_mat* A, const double* b_dev, double* x_dev, gnp_model* M,
                          int restart, double rtol, int maxiters, double timeout_s,
                          gnp_solve_info* info, void* stream);
+
+/* Solve k systems A x_r = b_r (1 <= k <= GNP_MAX_RHS) with one matrix and one
+ * preconditioner M (NULL = identity; a GNP with L >= 1 and float32 hidden blocks) by
+ * restarted FGMRES(restart <= GNP_MAX_RESTART_MULTI), advancing all systems in lockstep so
+ * that every sparse gather (the GNP layers, the SpMV, the residual) serves all of them
+ * (Sec. 4: one preconditioner for any number of right-hand sides).  B_dev and X_dev are
+ * float64 [n*k] node-major: element (i, r) at i*k + r; X holds x0 on entry.  Each system
+ * follows the stopping rules of fgmres_solve; one whose cycle ends early waits, inactive,
+ * for the others, so its iterates and iteration count are those of a solve on its own.
+ * infos (may be NULL) is an array of k gnp_solve_info (per-system optional histories as in
+ * fgmres_solve; hessenberg is not filled, seconds is the shared wall time).  Synchronous;
+ * returns GNP_OK when every system converged, else the first failing system's status.
+ * The workspace ((restart+1) n K float64 + restart n K float32 + 32 n K float32, K = k
+ * rounded up to 2, 4 or 8) is cached in A. */
+/* z_r = M(v_r) for k vectors at once (the GNP kernels of fgmres_solve_multi): v_dev
+ * float64 [n*k] and z_dev float32 [n*k], node-major (element (i, r) at i*k + r).  Uses the
+ * multi-system workspace cached in the model's matrix.  Asynchronous. */
+int gnp_apply_multi(gnp_model* M, const double* v_dev, int k, float* z_dev, void* stream);
+int fgmres_solve_multi(gnp_mat* A, const double* B_dev, double* X_dev, int k, gnp_model* M,
+                       int restart, double rtol, int maxiters, gnp_solve_info* infos,
+                       void* stream);
 
 /* A right preconditioner for fgmres_solve_precond (the GNP and the simple baselines
  * the paper compares it with, Sec. 3 "Compared methods"):

@@ -95,7 +95,8 @@ inline int red_blocks(long long n) {
 
 // ------------------------------------------------------------------ objects
 
-struct Solver;  // FGMRES workspace (krylov.cu)
+struct Solver;       // FGMRES workspace (krylov.cu)
+struct MultiSolver;  // multi-right-hand-side FGMRES workspace (multi.cu)
 
 struct CscView {
   int* ptr = nullptr;   // [n+1] column pointers of A (= row pointers of A^T)
@@ -114,6 +115,7 @@ struct gnp_mat {
   double* val = nullptr;
   gnp::CscView csc;          // built lazily for training
   gnp::Solver* solver = nullptr;
+  gnp::MultiSolver* msolver = nullptr;
   gnp::RedScratch red;       // for gnp_gamma / small reductions
   double* scratch_d = nullptr;   // [n] float64 scratch (column sums)
 };

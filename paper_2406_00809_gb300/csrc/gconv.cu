@@ -288,12 +288,19 @@ __device__ __forceinline__ void gconv_part(GconvSmem<HT, ROWS>& sm, int t, int r
   }
 }
 
+// Programmatic dependent launch: each layer is launched while the previous one drains.
+// A layer loads its tile's row pointers (the matrix, never written), then waits for the
+// previous grid to complete and flush (griddepcontrol.wait) before any read of data a
+// previous kernel wrote; it releases its own dependents once its epilogue is done.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// The tile's hidden rows and its gather; the row pointers are already in sm.g.rp.
 template <class HT, int ROWS>
-__device__ __forceinline__ void gconv_load_gather(GconvSmem<HT, ROWS>& sm, const int* __restrict__ rp,
-                                                  const int* __restrict__ col, const float* __restrict__ valhat,
-                                                  const HT* __restrict__ Hin, int r0, int rows) {
+__device__ __forceinline__ void gconv_load_gather(GconvSmem<HT, ROWS>& sm, const int* __restrict__ col,
+                                                  const float* __restrict__ valhat, const HT* __restrict__ Hin,
+                                                  int r0, int rows) {
   using TR = typename HTraits<HT>::TR;
-  tile_load_rp<TR>(sm.g, rp, r0, rows);
   tile_copy<HT, false>(sm.stile, const_cast<HT*>(Hin), r0, rows);
   __syncthreads();
   tile_gather<TR>(sm.g, rows, col, valhat, Hin);
@@ -309,12 +316,14 @@ k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __
         const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
         const __grid_constant__ LayerW lw) {
   static_assert(ROWS == TILE || 2 * ROWS == TILE, "one or two epilogue threads per row");
-  if (ctl && !ctl[1]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   GconvSmem<HT, ROWS>& sm = *reinterpret_cast<GconvSmem<HT, ROWS>*>(smraw);
   const int r0 = blockIdx.x * ROWS;
   const int rows = min(ROWS, n - r0);
-  gconv_load_gather<HT, ROWS>(sm, rp, col, valhat, Hin, r0, rows);
+  tile_load_rp<typename HTraits<HT>::TR>(sm.g, rp, r0, rows);
+  pdl_wait();
+  if (ctl && !ctl[1]) return;
+  gconv_load_gather<HT, ROWS>(sm, col, valhat, Hin, r0, rows);
   const int t = threadIdx.x % ROWS;
   if constexpr (ROWS == TILE) {
     float o[16];
@@ -332,6 +341,7 @@ k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __
       else stage_part<HT, 0, 8>(sm.stile, t, o);
     }
   }
+  pdl_release();
   __syncthreads();
   tile_copy<HT, true>(sm.stile, Hout, r0, rows);
 }
@@ -369,12 +379,14 @@ k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float
             const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n,
             int n, const int* __restrict__ ctl, const __grid_constant__ LayerW lw,
             const __grid_constant__ DecW dw) {
-  if (ctl && !ctl[1]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   GconvSmem<HT, ROWS>& sm = *reinterpret_cast<GconvSmem<HT, ROWS>*>(smraw);
   const int r0 = blockIdx.x * ROWS;
   const int rows = min(ROWS, n - r0);
-  gconv_load_gather<HT, ROWS>(sm, rp, col, valhat, Hin, r0, rows);
+  tile_load_rp<typename HTraits<HT>::TR>(sm.g, rp, r0, rows);
+  pdl_wait();
+  if (ctl && !ctl[1]) return;
+  gconv_load_gather<HT, ROWS>(sm, col, valhat, Hin, r0, rows);
   const int t = threadIdx.x % ROWS;
   const double tv = *tau;
   const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
@@ -444,7 +456,7 @@ __global__ void k_hidden_to_f32(const HT* __restrict__ H, float* __restrict__ ou
 
 // ---------------------------------------------------------------- host side
 
-static void fill_params(const std::vector<float>& w, int L, EncW& ew, DecW& dw) {
+void fill_enc_dec(const std::vector<float>& w, int L, EncW& ew, DecW& dw) {
   memcpy(ew.W1, w.data() + ENC_W1, sizeof(ew.W1));
   memcpy(ew.b1, w.data() + ENC_B1, sizeof(ew.b1));
   memcpy(ew.W2, w.data() + ENC_W2, sizeof(ew.W2));
@@ -456,7 +468,7 @@ static void fill_params(const std::vector<float>& w, int L, EncW& ew, DecW& dw) 
   dw.b2 = d[576];
 }
 
-static void fill_layer(const std::vector<float>& w, int l, LayerW& lw) {
+void fill_layer_w(const std::vector<float>& w, int l, LayerW& lw) {
   const float* p = w.data() + layer_off(l);
   memcpy(lw.U, p, sizeof(lw.U));
   memcpy(lw.W, p + 256, sizeof(lw.W));
@@ -524,6 +536,23 @@ static int set_smem_attrs_all() {
   return GNP_OK;
 }
 
+// Launch with programmatic stream serialization (the kernel calls pdl_wait before it
+// reads anything an earlier kernel wrote).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(TILE);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Layers 0..L-1 (the last one fused with the decoder unless tracing), ROWS-row tiles.
 template <class HT, int FORM, int ROWS>
 static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, const int* ctl,
@@ -536,9 +565,10 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
   const int fused_last = (L > 0 && !trace) ? 1 : 0;
   for (int l = 0; l < L - fused_last; ++l) {
     LayerW lw;
-    fill_layer(M->w_host, l, lw);
+    fill_layer_w(M->w_host, l, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
-    k_gconv<HT, FORM, ROWS><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, H1, n, ctl, lw);
+    GNP_TRY_CUDA(launch_pdl(k_gconv<HT, FORM, ROWS>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
+                            (const HT*)H0, H1, n, ctl, lw));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
     if (trace)
       k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
@@ -546,10 +576,10 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
   }
   if (fused_last) {
     LayerW lw;
-    fill_layer(M->w_host, L - 1, lw);
+    fill_layer_w(M->w_host, L - 1, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
-    k_gconv_dec<HT, FORM, ROWS><<<ntg, TILE, smem, st>>>(A->rp, A->col, M->valhat, H0, z, W.tau, sqrt_n, n,
-                                                         ctl, lw, dw);
+    GNP_TRY_CUDA(launch_pdl(k_gconv_dec<HT, FORM, ROWS>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
+                            (const HT*)H0, z, (const double*)W.tau, sqrt_n, n, ctl, lw, dw));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
     k_decode<HT><<<(n + TILE - 1) / TILE, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
@@ -571,7 +601,7 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
     k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
   EncW ew;
   DecW dw;
-  fill_params(M->w_host, L, ew, dw);
+  fill_enc_dec(M->w_host, L, ew, dw);
   HT* H0 = static_cast<HT*>(W.H[0]);
   HT* H1 = static_cast<HT*>(W.H[1]);
   k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);

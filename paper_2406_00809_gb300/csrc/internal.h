@@ -81,6 +81,10 @@ int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* 
                  const int* ctl, cudaStream_t st, cudaEvent_t* ev = nullptr,
                  const ApplyWs* ws = nullptr);
 
+// Kernel-parameter copies of the encoder/decoder and of layer l's weights.
+void fill_enc_dec(const std::vector<float>& w, int L, EncW& ew, DecW& dw);
+void fill_layer_w(const std::vector<float>& w, int l, LayerW& lw);
+
 // Make the host copy of the weights current (after training).
 int model_sync_host(gnp_model* M);
 // Everything apply_launch needs that is not a stream operation (host weights, kernel
@@ -89,6 +93,7 @@ int apply_prepare(gnp_model* M);
 unsigned long long model_version(const gnp_model* M);
 int gamma_launch(gnp_mat* A, double* gamma_dev, cudaStream_t st);
 void solver_free(Solver* s);
+void multi_solver_free(MultiSolver* s);
 int solver_create(int n, int m, int maxiters, Solver** out);
 size_t solver_bytes(int n, int m, int maxiters);
 void train_reset(TrainState* t);

@@ -174,45 +174,6 @@ k_spmv_tile(const int* __restrict__ rp, const int* __restrict__ col, const doubl
   }
 }
 
-// Grid of the CGS2 kernels: one block per SM while the rows are few enough that L2
-// latency, not bandwidth, bounds the basis reads (each block then reduces once per
-// column chunk, and the float64 pipes of all SMs share the work evenly); up to four per
-// SM on larger systems for memory parallelism.  Never more than red_blocks(n), the
-// capacity of the partial-sum scratch.
-static int dot_blocks(int n) {
-  const int per = (n + NUM_SMS_GB300 * RED_THREADS * 2 - 1) / (NUM_SMS_GB300 * RED_THREADS * 2);
-  return std::min(red_blocks(n), NUM_SMS_GB300 * std::max(1, std::min(4, per)));
-}
-
-constexpr int KC = 8;  // basis columns per register chunk
-constexpr int RSTRIDE = RED_THREADS + 8;  // row stride of the reduction transpose (doubles)
-static_assert(RED_THREADS == TILE && RED_THREADS / 32 == KC, "one warp per chunk column");
-
-// Block-wide sums of KC values per thread (256 threads): the values are transposed
-// through shared memory (sh: KC * RSTRIDE doubles) so that warp w adds column w's 256
-// values with 8 sequential adds per lane and one 5-level shuffle tree, instead of one
-// tree per value per warp.  GB300 executes float64 adds at 2 per SM per cycle, so
-// the number of tree levels, not the memory traffic, decides these kernels' cost.
-// ACC: dst[w] += sum (shared accumulators); else dst[w] = sum.  Fixed order.
-template <bool ACC>
-__device__ __forceinline__ void block_reduce_kc(const double (&a)[KC], double* sh, double* dst, int kvalid) {
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-#pragma unroll
-  for (int kc = 0; kc < KC; ++kc) sh[kc * RSTRIDE + t] = a[kc];
-  __syncthreads();
-  if (w < kvalid) {
-    double s = 0.0;
-#pragma unroll
-    for (int i = 0; i < RED_THREADS / 32; ++i) s += sh[w * RSTRIDE + lane + 32 * i];
-    s = warp_sum(s);
-    if (lane == 0) {
-      if (ACC) dst[w] += s;
-      else dst[w] = s;
-    }
-  }
-  __syncthreads();
-}
-
 // w = A z (tile gather) fused with CGS2 pass 1: h1 = V_j^T w and ||w||^2.  Blocks loop
 // over tiles and keep their dot sums in shared memory, so the partials stay one row
 // per block (at most 4 per SM) however large n is.
@@ -436,73 +397,9 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
     for (int k = 0; k <= j; ++k) h2[k] = shtot[k];
     return;
   }
-  // PASS 3: column j of H_bar, Givens QR update (rotation convention: rho = hypot(a,b),
-  // c = a/rho, s = b/rho; rho = 0 gives c = 1, s = 0), residual estimate |g_{j+1}|.
-  const int m = st->m;
-  const int ldh = m + 1;
+  // PASS 3: column j of H_bar and the Givens update of the least-squares problem
   const double hn = sqrt(shtot[0]);
-  st->hn = hn;
-  double* col = shtot + 1;  // column j, rotated in place in shared memory
-  const double* scs = shh;
-  const double* ssn = &shred[0][0];
-  bool finite = isfinite(hn);
-  for (int i = 0; i <= j; ++i) H[(size_t)j * ldh + i] = col[i];
-  col[j + 1] = hn;
-  H[(size_t)j * ldh + j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
-    col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
-    col[i] = t;
-  }
-  for (int i = 0; i <= j + 1; ++i) finite = finite && isfinite(col[i]);
-  const double a = col[j], b = col[j + 1];
-  const double rho = hypot(a, b);
-  double c = 1.0, s = 0.0;
-  if (rho != 0.0) {
-    c = a / rho;
-    s = b / rho;
-  }
-  const int iters = st->iters + 1;
-  st->iters = iters;
-  const unsigned long long elapsed = global_ns() - st->t0;
-  thist[iters] = elapsed;
-  const double wn0 = st->wnorm0;
-  int flags = 0;
-  int jj;
-  if (!finite || !isfinite(rho)) {
-    flags |= FL_NAN;
-    jj = j;
-  } else if (rho <= BREAKDOWN_REL * wn0) {
-    hist[iters] = fabs(g[j]) / st->bnorm;
-    flags |= FL_DROPPED;
-    jj = j;
-  } else {
-    cs[j] = c;
-    sn[j] = s;
-    col[j] = rho;
-    col[j + 1] = 0.0;
-    for (int i = 0; i <= j + 1; ++i) R[(size_t)j * ldh + i] = col[i];
-    const double gj = g[j];
-    g[j + 1] = -s * gj;
-    g[j] = c * gj;
-    jj = j + 1;
-    const double res = fabs(g[j + 1]);
-    st->res_est = res;
-    hist[iters] = res / st->bnorm;
-    if (hn <= BREAKDOWN_REL * wn0) flags |= FL_BREAKDOWN;
-    else if (res <= st->tol) flags |= FL_EST_CONV;
-    else if (iters >= st->maxiters) flags |= FL_MAXIT;
-    else if (st->timeout_ns != 0ull && elapsed >= st->timeout_ns) flags |= FL_TIMEOUT;
-    else if (j + 1 >= m) flags |= FL_FULL;
-  }
-  st->jj = jj;
-  st->flags = flags;
-  if (flags) {
-    st->active = 0;
-  } else {
-    st->j = j + 1;
-    st->vscale = hn;
-  }
+  arnoldi_step_finish(st, j, shtot + 1, hn, shh, &shred[0][0], H, R, cs, sn, g, hist, thist);
 }
 
 // y = R^{-1} g (back substitution, redundantly in every block), x += Z[:, :jj] y.

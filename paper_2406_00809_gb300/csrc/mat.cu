@@ -268,6 +268,8 @@ void gnp_mat_destroy(gnp_mat* A) {
   if (!A) return;
   solver_free(A->solver);
   A->solver = nullptr;
+  multi_solver_free(A->msolver);
+  A->msolver = nullptr;
   dev_free(A->rp);
   dev_free(A->col);
   dev_free(A->val);

@@ -100,6 +100,8 @@ def lib():
         "fgmres_solve": (i, [vp, vp, vp, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
         "fgmres_solve_timeout": (i, [vp, vp, vp, vp, i, d, i, d, C.POINTER(_SolveInfo), vp]),
         "fgmres_solve_precond": (i, [vp, vp, vp, vp, i, d, i, d, C.POINTER(_SolveInfo), vp]),
+        "fgmres_solve_multi": (i, [vp, vp, vp, i, vp, i, d, i, C.POINTER(_SolveInfo), vp]),
+        "gnp_apply_multi": (i, [vp, vp, i, vp, vp]),
         "gnp_precond_create": (i, [vp, i, vp, i, d, pp]),
         "gnp_precond_destroy": (None, [vp]),
         "gnp_precond_apply": (i, [vp, vp, vp, vp]),
@@ -464,6 +466,46 @@ def fgmres_solve(A: Mat, b, x, M: Model | Precond | None = None, restart=30, rto
     if hess is not None:
         cols = info.hessenberg_cols
         out.hessenberg = hess.T[:cols + 1, :cols].copy()  # column-major (m+1) x m
+    return out
+
+
+def gnp_apply_multi(M: Model, V, Z, stream=None):
+    """Z[:, r] = M(V[:, r]) for [n, k] tensors (V float64, Z float32, row-major)."""
+    import torch
+    _check(lib().gnp_apply_multi(M.h, _dptr(V, torch.float64, "V"), V.shape[1], _dptr(Z, torch.float32, "Z"),
+                                 _stream(stream)))
+
+
+def fgmres_solve_multi(A: Mat, B, X, M: Model | None = None, restart=30, rtol=1e-8, maxiters=1000,
+                       stream=None, history=True, times=False) -> list:
+    """Solve the k systems A X[:, r] = B[:, r] together (float64 CUDA tensors of shape [n, k],
+    row-major, so element (i, r) is at i*k + r; X holds x0 on entry).  Returns k SolveInfo."""
+    import torch
+    if B.dim() != 2 or X.shape != B.shape:
+        raise ValueError("B and X must be [n, k] tensors of the same shape")
+    k = B.shape[1]
+    infos = (_SolveInfo * k)()
+    hists = [np.zeros(maxiters + 1) if history else None for _ in range(k)]
+    thists = [np.zeros(maxiters + 1) if times else None for _ in range(k)]
+    for r in range(k):
+        if hists[r] is not None:
+            infos[r].res_history = hists[r].ctypes.data_as(C.POINTER(C.c_double))
+        if thists[r] is not None:
+            infos[r].time_history = thists[r].ctypes.data_as(C.POINTER(C.c_double))
+    st = lib().fgmres_solve_multi(A.h, _dptr(B, torch.float64, "B"), _dptr(X, torch.float64, "X"), k,
+                                  M.h if M is not None else None, restart, rtol, maxiters, infos, _stream(stream))
+    if st not in STATUS or st in (1, 3, 4):  # invalid argument, out of memory, CUDA error
+        _check(st)
+    out = []
+    for r in range(k):
+        info = infos[r]
+        o = SolveInfo(info.status, info.iters, info.restarts, info.rel_res_est, info.rel_res_true, info.seconds,
+                      cycles=info.cycles)
+        if hists[r] is not None:
+            o.history = hists[r][:info.res_history_len].copy()
+        if thists[r] is not None:
+            o.times = thists[r][:info.iters + 1].copy()
+        out.append(o)
     return out
 
 
