@@ -4,7 +4,7 @@
         [--hprec fp32|bf16|both] [--iters 50]
 
 For each hidden-block precision: the whole apply z = M(v) is timed with CUDA events
-(L2 flushed by a 256 MB write before every rep) and converted to GB/s with the
+(L2 flushed by a 256 MB write before every rep, or warm with --warm) and converted to GB/s with the
 algorithmic bytes of its kernels; then an FGMRES run of a fixed number of iterations
 times every Res-GCONV launch with CUDA events (gnp_profile_gconv).  Prints one JSON
 line per precision.  Inputs are synthetic (paper_2406_00809_gb300.inputs).
@@ -43,6 +43,7 @@ def main():
     ap.add_argument("--hprec", default="both", choices=["fp32", "bf16", "both"])
     ap.add_argument("--iters", type=int, default=50)
     ap.add_argument("--L", type=int, default=8)
+    ap.add_argument("--warm", action="store_true", help="no L2 flush between reps")
     a = ap.parse_args()
     import torch
     from paper_2406_00809_gb300 import build
@@ -71,7 +72,8 @@ def main():
                 gnp.gnp_apply(M, v, z, stream=stream)
             times = []
             for _ in range(a.reps):
-                flush.zero_()
+                if not a.warm:
+                    flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -97,7 +99,8 @@ def main():
                    "gconv_us": g_us, "gconv_GBs": g_gbs,
                    "gconv_frac": g_gbs / peak if g_gbs else None,
                    "gconv_launches": info.gconv_launches, "layer_bytes": layer,
-                   "peak_GBs": peak, "gen_s": gen_s}
+                   "peak_GBs": peak, "gen_s": gen_s, "l2_flushed": not a.warm,
+                   "l2_bytes": torch.cuda.get_device_properties(0).L2_cache_size}
             print(json.dumps(out), flush=True)
         gnp.gnp_set_hprec(M, gnp.H_FP32)
 

@@ -32,6 +32,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="aniso64")
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--maxiters", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=None, help="override the workload's batch")
+    ap.add_argument("--arnoldi-m", type=int, default=None, help="override the workload's Arnoldi steps")
     args = ap.parse_args(argv)
     import torch
     from paper_2406_00809_gb300 import build
@@ -39,7 +41,8 @@ def main(argv=None):
     from paper_2406_00809_gb300 import gnp as g
     A, wl = I.workload(args.workload)
     Mt = g.mat_from_csr(A)
-    cfg = g.make_config(L=wl.get("L", 8), batch=wl.get("batch", 32), arnoldi_m=wl.get("arnoldi_m", 30), lr=1e-3)
+    cfg = g.make_config(L=wl.get("L", 8), batch=args.batch or wl.get("batch", 32),
+                        arnoldi_m=args.arnoldi_m or wl.get("arnoldi_m", 30), lr=1e-3)
     M = g.gnp_create(Mt, cfg, I.init_weights(cfg.L, seed=0))
     g.gnp_train(M, 3)  # sampler set-up and first launches
     torch.cuda.synchronize()

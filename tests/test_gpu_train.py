@@ -124,9 +124,10 @@ def test_forward_backward_batch_match_oracle(gnp, form):
     assert rel(g.cpu().numpy(), gr) <= 1e-4, rel(g.cpu().numpy(), gr)
 
 
-def test_backward_central_differences_on_device(gnp):
+@pytest.mark.parametrize("kind", ["poisson12", "aniso8"])
+def test_backward_central_differences_on_device(gnp, kind):
     import torch
-    A = I.poisson2d(12)
+    A = I.poisson2d(12) if kind == "poisson12" else I.aniso3d(8, 100.0)
     n, B, L = A.n, 8, 2
     Mt, M, blob = _model(gnp, A, L, B=B)
     b = torch.from_numpy(_batch(n, B, 3).astype(np.float32)).cuda()
