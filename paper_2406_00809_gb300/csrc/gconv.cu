@@ -313,13 +313,13 @@ template <> struct GconvBounds<128> { static constexpr int MIN_BLOCKS = 4; };
 template <class HT, int FORM, int ROWS>
 __global__ void __launch_bounds__(TILE, GconvBounds<ROWS>::MIN_BLOCKS)
 k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
-        const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
+        const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, int trows, const int* __restrict__ ctl,
         const __grid_constant__ LayerW lw) {
   static_assert(ROWS == TILE || 2 * ROWS == TILE, "one or two epilogue threads per row");
   extern __shared__ __align__(16) unsigned char smraw[];
   GconvSmem<HT, ROWS>& sm = *reinterpret_cast<GconvSmem<HT, ROWS>*>(smraw);
-  const int r0 = blockIdx.x * ROWS;
-  const int rows = min(ROWS, n - r0);
+  const int r0 = blockIdx.x * trows;  // trows <= ROWS rows per tile
+  const int rows = min(trows, n - r0);
   tile_load_rp<typename HTraits<HT>::TR>(sm.g, rp, r0, rows);
   pdl_wait();
   if (ctl && !ctl[1]) return;
@@ -377,12 +377,12 @@ template <class HT, int FORM, int ROWS>
 __global__ void __launch_bounds__(TILE, GconvBounds<ROWS>::MIN_BLOCKS)
 k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
             const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n,
-            int n, const int* __restrict__ ctl, const __grid_constant__ LayerW lw,
+            int n, int trows, const int* __restrict__ ctl, const __grid_constant__ LayerW lw,
             const __grid_constant__ DecW dw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   GconvSmem<HT, ROWS>& sm = *reinterpret_cast<GconvSmem<HT, ROWS>*>(smraw);
-  const int r0 = blockIdx.x * ROWS;
-  const int rows = min(ROWS, n - r0);
+  const int r0 = blockIdx.x * trows;  // trows <= ROWS rows per tile
+  const int rows = min(trows, n - r0);
   tile_load_rp<typename HTraits<HT>::TR>(sm.g, rp, r0, rows);
   pdl_wait();
   if (ctl && !ctl[1]) return;
@@ -513,6 +513,25 @@ static int gconv_blocks() {
   return ROWS == 256 ? 3 : 4;
 }
 
+// Rows per tile (at most ROWS): for float32 hidden blocks, n spread evenly over every
+// resident block slot (152 SMs x gconv_blocks), so that no SM holds more rows than another
+// and small systems still fill every slot (65,536 rows: 144-row tiles, 456 blocks, instead
+// of 256 tiles of 256 rows on 1-2 blocks per SM); large systems use full ROWS-row tiles.
+// GNP_GCONV_TILE=32..ROWS in the environment forces the tile height (for tuning).
+template <class HT, int ROWS>
+static int gconv_tile_rows(int n) {
+  const int forced = env_int("GNP_GCONV_TILE", 0);
+  if (forced >= 32 && forced <= ROWS) return forced;
+  // bfloat16 rows are 32 bytes: a 256-row tile's nonzeros already give its 128 slots short
+  // chains, and shorter tiles measured slower (65,536 rows: 0.080 ms apply at 256 rows,
+  // 0.088 ms at 144); float32 gains from the even spread (0.097 -> 0.092 ms)
+  if (sizeof(HT) == 2) return ROWS;
+  const long long slots = (long long)NUM_SMS_GB300 * gconv_blocks<HT, ROWS>();
+  int t = (int)((n + slots - 1) / slots);
+  t = (t + 7) & ~7;
+  return std::max(32, std::min(ROWS, t));
+}
+
 template <class HT, int FORM, int ROWS>
 static int set_carveout() {
   static int applied = -1;
@@ -560,7 +579,8 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
   const int smem = (int)sizeof(GconvSmem<HT, ROWS>);
-  const int ntg = (n + ROWS - 1) / ROWS;
+  const int trows = gconv_tile_rows<HT, ROWS>(n);
+  const int ntg = (n + trows - 1) / trows;
   const long long hcount = (long long)n * 16;
   const int fused_last = (L > 0 && !trace) ? 1 : 0;
   for (int l = 0; l < L - fused_last; ++l) {
@@ -568,7 +588,7 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
     fill_layer_w(M->w_host, l, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
     GNP_TRY_CUDA(launch_pdl(k_gconv<HT, FORM, ROWS>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
-                            (const HT*)H0, H1, n, ctl, lw));
+                            (const HT*)H0, H1, n, trows, ctl, lw));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
     if (trace)
       k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
@@ -579,7 +599,7 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
     fill_layer_w(M->w_host, L - 1, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
     GNP_TRY_CUDA(launch_pdl(k_gconv_dec<HT, FORM, ROWS>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
-                            (const HT*)H0, z, (const double*)W.tau, sqrt_n, n, ctl, lw, dw));
+                            (const HT*)H0, z, (const double*)W.tau, sqrt_n, n, trows, ctl, lw, dw));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
     k_decode<HT><<<(n + TILE - 1) / TILE, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);

@@ -338,6 +338,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
     double* vout = V + (size_t)(j + 1) * ld;
     for (int i = gtid; i < n; i += gstride) {
       double x = w[i];
+#pragma unroll 8
       for (int k = 0; k <= j; ++k) x -= V[k * ld + i] * shh[k];
       vout[i] = x;
       acc += x * x;
@@ -348,6 +349,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
     if (PASS == 2) {
       for (int i = gtid; i < n; i += gstride) {
         double x = w[i];
+#pragma unroll 8
         for (int k = 0; k <= j; ++k) x -= V[k * ld + i] * shh[k];
         w[i] = x;
       }

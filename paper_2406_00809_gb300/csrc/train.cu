@@ -215,39 +215,80 @@ constexpr uint32_t STREAM_X = 1, STREAM_EPS = 2, STREAM_V1 = 3;
 // ---------------------------------------------------------------- generic kernels
 
 // Y[i] = alpha * sum_e vals[e] X[idx[e]] + beta * Yadd[i], for node blocks of W4
+// acc += sum_{e in [e0, e1)} vals[e] X[idx[e]] for one node's row of W4 float4: lane
+// `lane` of the node's lane group owns float4s lane, lane+LPN, ... (KM of them, W4 =
+// LPN*KM or less).  Two nonzeros are in flight at a time; the additions keep the order of
+// the nonzeros.
+template <int LPN, int KM>
+__device__ __forceinline__ void gather_rows(const int* __restrict__ idx, const float* __restrict__ vals,
+                                            const float4* __restrict__ X, int W4, int lane, int e0, int e1,
+                                            float4 (&acc)[KM]) {
+  int e = e0;
+  for (; e + 2 <= e1; e += 2) {
+    const int j0 = __ldg(idx + e), j1 = __ldg(idx + e + 1);
+    const float a0 = __ldg(vals + e), a1 = __ldg(vals + e + 1);
+    const float4* x0 = X + (size_t)j0 * W4;
+    const float4* x1 = X + (size_t)j1 * W4;
+    float4 v0[KM], v1[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const int f = lane + LPN * k;
+      if (f < W4) {
+        v0[k] = __ldg(x0 + f);
+        v1[k] = __ldg(x1 + f);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const int f = lane + LPN * k;
+      if (f < W4) {
+        acc[k].x = fmaf(a1, v1[k].x, fmaf(a0, v0[k].x, acc[k].x));
+        acc[k].y = fmaf(a1, v1[k].y, fmaf(a0, v0[k].y, acc[k].y));
+        acc[k].z = fmaf(a1, v1[k].z, fmaf(a0, v0[k].z, acc[k].z));
+        acc[k].w = fmaf(a1, v1[k].w, fmaf(a0, v0[k].w, acc[k].w));
+      }
+    }
+  }
+  if (e < e1) {
+    const int j = __ldg(idx + e);
+    const float a = __ldg(vals + e);
+    const float4* xj = X + (size_t)j * W4;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const int f = lane + LPN * k;
+      if (f < W4) {
+        const float4 v = __ldg(xj + f);
+        acc[k].x = fmaf(a, v.x, acc[k].x);
+        acc[k].y = fmaf(a, v.y, acc[k].y);
+        acc[k].z = fmaf(a, v.z, acc[k].z);
+        acc[k].w = fmaf(a, v.w, acc[k].w);
+      }
+    }
+  }
+}
+
 // float4 values (warp per node).  With (ptr, idx, vals) the CSR of A_hat this is
 // A_hat X; with the canonical CSC and the CSC-ordered values it is A_hat^T X.
+template <int LPN, int KM>
 __global__ void __launch_bounds__(256)
 k_spmm_nodes(const int* __restrict__ ptr, const int* __restrict__ idx, const float* __restrict__ vals,
              const float4* __restrict__ X, int n, int W4, float alpha, const float4* __restrict__ Yadd,
              float beta, float4* __restrict__ Y) {
-  const int lane = threadIdx.x & 31;
+  constexpr int NPW = 32 / LPN;  // nodes per warp
+  const int lane = threadIdx.x & (LPN - 1);
+  const int grp = (threadIdx.x & 31) / LPN;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int i = warp; i < n; i += nwarps) {
-    float4 acc[8];
+  for (int i0 = warp * NPW; i0 < n; i0 += nwarps * NPW) {
+    const int i = i0 + grp;
+    if (i >= n) continue;
+    float4 acc[KM];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int e0 = ptr[i], e1 = ptr[i + 1];
-    for (int e = e0; e < e1; ++e) {
-      const int j = __ldg(idx + e);
-      const float a = __ldg(vals + e);
-      const float4* xj = X + (size_t)j * W4;
+    for (int k = 0; k < KM; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    gather_rows<LPN, KM>(idx, vals, X, W4, lane, ptr[i], ptr[i + 1], acc);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int f = lane + 32 * k;
-        if (f < W4) {
-          const float4 v = __ldg(xj + f);
-          acc[k].x = fmaf(a, v.x, acc[k].x);
-          acc[k].y = fmaf(a, v.y, acc[k].y);
-          acc[k].z = fmaf(a, v.z, acc[k].z);
-          acc[k].w = fmaf(a, v.w, acc[k].w);
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int f = lane + 32 * k;
+    for (int k = 0; k < KM; ++k) {
+      const int f = lane + LPN * k;
       if (f < W4) {
         float4 o = make_float4(alpha * acc[k].x, alpha * acc[k].y, alpha * acc[k].z, alpha * acc[k].w);
         if (Yadd) {
@@ -261,6 +302,27 @@ k_spmm_nodes(const int* __restrict__ ptr, const int* __restrict__ idx, const flo
       }
     }
   }
+}
+
+// Y = alpha A X (+ beta Yadd) for node rows of W4 float4 (W4 = 1..256): a lane group per
+// node, LPN = min(W4, 32) lanes, several nodes per warp when the rows are narrow.
+static int spmm_nodes(const int* ptr, const int* idx, const float* vals, const float4* X, int n, int W4,
+                      float alpha, const float4* Yadd, float beta, float4* Y, cudaStream_t st) {
+  const int lpn = W4 >= 32 ? 32 : W4;
+  const int npw = 32 / lpn;
+  const int grid = std::max(1, std::min((n + 8 * npw - 1) / (8 * npw), 16 * NUM_SMS_GB300));
+#define GNP_SPMM(L, K) k_spmm_nodes<L, K><<<grid, 256, 0, st>>>(ptr, idx, vals, X, n, W4, alpha, Yadd, beta, Y)
+  if (W4 <= 1) GNP_SPMM(1, 1);
+  else if (W4 <= 2) GNP_SPMM(2, 1);
+  else if (W4 <= 4) GNP_SPMM(4, 1);
+  else if (W4 <= 8) GNP_SPMM(8, 1);
+  else if (W4 <= 16) GNP_SPMM(16, 1);
+  else if (W4 <= 32) GNP_SPMM(32, 1);
+  else if (W4 <= 64) GNP_SPMM(32, 2);
+  else if (W4 <= 128) GNP_SPMM(32, 4);
+  else GNP_SPMM(32, 8);
+#undef GNP_SPMM
+  return check_launch("k_spmm_nodes");
 }
 
 // Values of A_hat in the CSC order (perm[k] = CSR position of CSC entry k).
@@ -357,11 +419,16 @@ k_enc_batch(const float* __restrict__ b, const double* __restrict__ tau, long lo
 
 // One Res-GCONV layer on the batch: AGG = A_hat X (saved), Out = layer(X, AGG).
 // Warp per node (gather of the node block), then lane per batch column.
-template <int FORM>
+template <int FORM, int B>
 __global__ void __launch_bounds__(256)
 k_layer_batch(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ vh,
-              const float* __restrict__ X, float* __restrict__ AGG, float* __restrict__ Out, int n, int B,
+              const float* __restrict__ X, float* __restrict__ AGG, float* __restrict__ Out, int n,
               const float* __restrict__ lw) {
+  constexpr int W4 = B * 4;                  // float4 per node block
+  constexpr int KM = (W4 + 31) / 32;         // float4 per lane in the gather
+  constexpr int P = B >= 32 ? 1 : 32 / B;    // lanes per batch column in the epilogue
+  constexpr int OP = 16 / P;                 // outputs per lane
+  constexpr int CPL = B > 32 ? B / 32 : 1;   // batch columns per lane
   extern __shared__ __align__(16) float smf[];
   float* sU = smf;
   float* sW = smf + 256;
@@ -369,34 +436,19 @@ k_layer_batch(const int* __restrict__ rp, const int* __restrict__ col, const flo
   for (int k = threadIdx.x; k < 512; k += blockDim.x) smf[k] = lw[k];
   __syncthreads();
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int W4 = B * 4;
   float* sA = sblk + (size_t)wl * (2 * B * 16);
   float* sX = sA + B * 16;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const float4* X4 = reinterpret_cast<const float4*>(X);
+  const int k0 = (lane % P) * OP;
   for (int i = warp; i < n; i += nwarps) {
-    float4 acc[8];
+    float4 acc[KM];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int e = rp[i]; e < rp[i + 1]; ++e) {
-      const int j = __ldg(col + e);
-      const float a = __ldg(vh + e);
-      const float4* xj = X4 + (size_t)j * W4;
+    for (int k = 0; k < KM; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    gather_rows<32, KM>(col, vh, X4, W4, lane, rp[i], rp[i + 1], acc);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int f = lane + 32 * k;
-        if (f < W4) {
-          const float4 v = __ldg(xj + f);
-          acc[k].x = fmaf(a, v.x, acc[k].x);
-          acc[k].y = fmaf(a, v.y, acc[k].y);
-          acc[k].z = fmaf(a, v.z, acc[k].z);
-          acc[k].w = fmaf(a, v.w, acc[k].w);
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < KM; ++k) {
       const int f = lane + 32 * k;
       if (f < W4) {
         reinterpret_cast<float4*>(AGG)[(size_t)i * W4 + f] = acc[k];
@@ -405,32 +457,41 @@ k_layer_batch(const int* __restrict__ rp, const int* __restrict__ col, const flo
       }
     }
     __syncwarp();
-    for (int bq = lane; bq < B; bq += 32) {
+#pragma unroll
+    for (int cc = 0; cc < CPL; ++cc) {
+      const int bq = lane / P + 32 * cc;
       const float* xa = sX + bq * 16;
       const float* ga = sA + bq * 16;
-      float o[16];
+      float o[OP];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) o[k] = 0.f;
+      for (int k = 0; k < OP; ++k) o[k] = 0.f;
+#pragma unroll 4
       for (int c = 0; c < 16; ++c) {
         const float gc = ga[c];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) o[k] = fmaf(gc, sW[c * 16 + k], o[k]);
+        for (int k = 0; k < OP; ++k) o[k] = fmaf(gc, sW[c * 16 + k0 + k], o[k]);
       }
       if (FORM == GNP_LAYER_PAPER) {
+#pragma unroll 4
         for (int c = 0; c < 16; ++c) {
           const float xc = xa[c];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) o[k] = fmaf(xc, sU[c * 16 + k], o[k]);
+          for (int k = 0; k < OP; ++k) o[k] = fmaf(xc, sU[c * 16 + k0 + k], o[k]);
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) o[k] = fmaxf(o[k], 0.f);
+        for (int k = 0; k < OP; ++k) o[k] = fmaxf(o[k], 0.f);
       } else {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) o[k] = xa[k] + fmaxf(o[k], 0.f);
+        for (int k = 0; k < OP; ++k) o[k] = xa[k0 + k] + fmaxf(o[k], 0.f);
       }
-      float4* out = reinterpret_cast<float4*>(Out + ((size_t)i * B + bq) * 16);
+      float* out = Out + ((size_t)i * B + bq) * 16 + k0;
+      if constexpr (OP >= 4) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) out[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+        for (int q = 0; q < OP / 4; ++q)
+          reinterpret_cast<float4*>(out)[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+      } else {
+        reinterpret_cast<float2*>(out)[0] = make_float2(o[0], o[1]);
+      }
     }
     __syncwarp();
   }
@@ -526,100 +587,101 @@ k_dec_bwd(const float* __restrict__ HL, const float* __restrict__ dz, const doub
 
 // Layer backward, row part: Gp = G * 1[pre > 0] (pre recomputed from X and AGG exactly
 // as the forward did), Y = Gp W^T, local = Gp U^T (paper) or G (residual).  Four threads
-// per row, thread j owning columns 4j..4j+3: it forms those four pre-activations (a
-// 16 x 4 slice of W and of U), its quarter of Gp, and its partial sums of Y and local over
-// its four columns, which a two-step shuffle tree (fixed order) completes; thread j then
-// writes entries 4j..4j+3 of every output row.  (One thread per row needs all 512
-// weights at once and spills.)
+// per row, thread j owning entries 4j..4j+3 of every output: it forms those four
+// pre-activations from a 16 x 4 slice of W and of U, its quarter of Gp, gathers the other
+// three quarters of Gp from its quad with shuffles, and forms entries 4j..4j+3 of Y and
+// local from the same slices of W^T and U^T (kept transposed in shared memory, so every
+// 16-byte weight load of a quad is a broadcast without bank conflicts).
 template <int FORM>
 __global__ void __launch_bounds__(256)
 k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G,
                  long long R, const float* __restrict__ lw, float* __restrict__ Gp_out,
                  float* __restrict__ Y_out, float* __restrict__ local_out) {
-  __shared__ __align__(16) float sU[256];
-  __shared__ __align__(16) float sW[256];
+  __shared__ __align__(16) float sU[256], sW[256], sUt[256], sWt[256];
   for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+    const int c = k >> 4, o = k & 15;
     sU[k] = lw[k];
     sW[k] = lw[256 + k];
+    sUt[o * 16 + c] = lw[k];
+    sWt[o * 16 + c] = lw[256 + k];
   }
   __syncthreads();
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int j = (int)(tid & 3);
+  const int qbase = (threadIdx.x & 31) & ~3;  // first lane of this quad
   // lanes past the last row stay for the shuffles with a clamped row and store nothing
   const bool ok = (tid >> 2) < R;
   const long long r = ok ? (tid >> 2) : R - 1;
   const float4* W4 = reinterpret_cast<const float4*>(sW);
   const float4* U4 = reinterpret_cast<const float4*>(sU);
-  float ag[16];
+  const float4* Wt4 = reinterpret_cast<const float4*>(sWt);
+  const float4* Ut4 = reinterpret_cast<const float4*>(sUt);
+  float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
   {
     const float4* ap = reinterpret_cast<const float4*>(AGG + r * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float4 v = __ldg(ap + q);
-      ag[4 * q] = v.x; ag[4 * q + 1] = v.y; ag[4 * q + 2] = v.z; ag[4 * q + 3] = v.w;
+      const float av[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float4 w = W4[(4 * q + e) * 4 + j];
+        pre.x = fmaf(av[e], w.x, pre.x);
+        pre.y = fmaf(av[e], w.y, pre.y);
+        pre.z = fmaf(av[e], w.z, pre.z);
+        pre.w = fmaf(av[e], w.w, pre.w);
+      }
     }
   }
-  float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const float4 w = W4[c * 4 + j];
-    pre.x = fmaf(ag[c], w.x, pre.x);
-    pre.y = fmaf(ag[c], w.y, pre.y);
-    pre.z = fmaf(ag[c], w.z, pre.z);
-    pre.w = fmaf(ag[c], w.w, pre.w);
-  }
   if (FORM == GNP_LAYER_PAPER) {
-    float x[16];
     const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float4 v = __ldg(xp + q);
-      x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
-    }
+      const float xv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      const float4 u = U4[c * 4 + j];
-      pre.x = fmaf(x[c], u.x, pre.x);
-      pre.y = fmaf(x[c], u.y, pre.y);
-      pre.z = fmaf(x[c], u.z, pre.z);
-      pre.w = fmaf(x[c], u.w, pre.w);
+      for (int e = 0; e < 4; ++e) {
+        const float4 u = U4[(4 * q + e) * 4 + j];
+        pre.x = fmaf(xv[e], u.x, pre.x);
+        pre.y = fmaf(xv[e], u.y, pre.y);
+        pre.z = fmaf(xv[e], u.z, pre.z);
+        pre.w = fmaf(xv[e], u.w, pre.w);
+      }
     }
   }
   const float4 g = __ldg(reinterpret_cast<const float4*>(G + r * 16) + j);
   const float4 gp = make_float4(pre.x > 0.f ? g.x : 0.f, pre.y > 0.f ? g.y : 0.f, pre.z > 0.f ? g.z : 0.f,
                                 pre.w > 0.f ? g.w : 0.f);
   if (ok) reinterpret_cast<float4*>(Gp_out + r * 16)[j] = gp;
-  // partial Y[c] (and local[c]) over this thread's four columns, then the quad sum
-  float y[16], loc[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    const float4 w = W4[c * 4 + j];
-    y[c] = fmaf(gp.x, w.x, fmaf(gp.y, w.y, fmaf(gp.z, w.z, gp.w * w.w)));
-    if (FORM == GNP_LAYER_PAPER) {
-      const float4 u = U4[c * 4 + j];
-      loc[c] = fmaf(gp.x, u.x, fmaf(gp.y, u.y, fmaf(gp.z, u.z, gp.w * u.w)));
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    y[c] += __shfl_xor_sync(0xffffffffu, y[c], 1);
-    y[c] += __shfl_xor_sync(0xffffffffu, y[c], 2);
-    if (FORM == GNP_LAYER_PAPER) {
-      loc[c] += __shfl_xor_sync(0xffffffffu, loc[c], 1);
-      loc[c] += __shfl_xor_sync(0xffffffffu, loc[c], 2);
-    }
-  }
-  float4 yo, lo;
+  // the whole Gp row from the quad
+  float gv[16];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    if (q == j) {
-      yo = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
-      lo = FORM == GNP_LAYER_PAPER ? make_float4(loc[4 * q], loc[4 * q + 1], loc[4 * q + 2], loc[4 * q + 3]) : g;
+    gv[4 * q] = __shfl_sync(0xffffffffu, gp.x, qbase + q);
+    gv[4 * q + 1] = __shfl_sync(0xffffffffu, gp.y, qbase + q);
+    gv[4 * q + 2] = __shfl_sync(0xffffffffu, gp.z, qbase + q);
+    gv[4 * q + 3] = __shfl_sync(0xffffffffu, gp.w, qbase + q);
+  }
+  float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 loc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float4 w = Wt4[k * 4 + j];  // W[4j..4j+3][k]
+    y.x = fmaf(gv[k], w.x, y.x);
+    y.y = fmaf(gv[k], w.y, y.y);
+    y.z = fmaf(gv[k], w.z, y.z);
+    y.w = fmaf(gv[k], w.w, y.w);
+    if (FORM == GNP_LAYER_PAPER) {
+      const float4 u = Ut4[k * 4 + j];
+      loc.x = fmaf(gv[k], u.x, loc.x);
+      loc.y = fmaf(gv[k], u.y, loc.y);
+      loc.z = fmaf(gv[k], u.z, loc.z);
+      loc.w = fmaf(gv[k], u.w, loc.w);
     }
   }
   if (ok) {
-    reinterpret_cast<float4*>(Y_out + r * 16)[j] = yo;
-    reinterpret_cast<float4*>(local_out + r * 16)[j] = lo;
+    reinterpret_cast<float4*>(Y_out + r * 16)[j] = y;
+    reinterpret_cast<float4*>(local_out + r * 16)[j] = FORM == GNP_LAYER_PAPER ? loc : g;
   }
 }
 
@@ -990,13 +1052,35 @@ static int grid_rows(long long R) {
 
 static int layer_smem(int B) { return (512 + 8 * 2 * B * 16) * (int)sizeof(float); }
 
-template <int FORM>
-static int set_layer_attr(int bytes) {
+template <int FORM, int B>
+static int layer_batch_one(int grid, int smem, cudaStream_t st, const int* rp, const int* col, const float* vh,
+                           const float* X, float* AG, float* Out, int n, const float* lw) {
   static int done = 0;
-  if (done >= bytes) return GNP_OK;
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_layer_batch<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  done = bytes;
-  return GNP_OK;
+  if (done < smem) {
+    GNP_TRY_CUDA(cudaFuncSetAttribute(k_layer_batch<FORM, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    done = smem;
+  }
+  k_layer_batch<FORM, B><<<grid, 256, smem, st>>>(rp, col, vh, X, AG, Out, n, lw);
+  return check_launch("k_layer_batch");
+}
+
+template <int FORM>
+static int layer_batch_form(int B, int grid, int smem, cudaStream_t st, const int* rp, const int* col,
+                            const float* vh, const float* X, float* AG, float* Out, int n, const float* lw) {
+  switch (B) {
+    case 4: return layer_batch_one<FORM, 4>(grid, smem, st, rp, col, vh, X, AG, Out, n, lw);
+    case 8: return layer_batch_one<FORM, 8>(grid, smem, st, rp, col, vh, X, AG, Out, n, lw);
+    case 16: return layer_batch_one<FORM, 16>(grid, smem, st, rp, col, vh, X, AG, Out, n, lw);
+    case 32: return layer_batch_one<FORM, 32>(grid, smem, st, rp, col, vh, X, AG, Out, n, lw);
+    case 64: return layer_batch_one<FORM, 64>(grid, smem, st, rp, col, vh, X, AG, Out, n, lw);
+    default: set_error("k_layer_batch: batch %d is not a power of two in [4, 64]", B); return GNP_ERR_INVALID_ARG;
+  }
+}
+
+static int layer_batch_launch(int form, int B, int grid, int smem, cudaStream_t st, const int* rp, const int* col,
+                              const float* vh, const float* X, float* AG, float* Out, int n, const float* lw) {
+  return form == GNP_LAYER_PAPER ? layer_batch_form<GNP_LAYER_PAPER>(B, grid, smem, st, rp, col, vh, X, AG, Out, n, lw)
+                                 : layer_batch_form<GNP_LAYER_RESID>(B, grid, smem, st, rp, col, vh, X, AG, Out, n, lw);
 }
 
 // Forward on the batch b (device, node-major [n*B]); activations saved in T.
@@ -1019,13 +1103,7 @@ static int forward_batch(gnp_model* M, const float* b, cudaStream_t st) {
     float* Out = T->Hs + (size_t)(l + 1) * R * 16;
     float* AG = T->AGG + (size_t)l * R * 16;
     const float* lw = M->w_dev + layer_off(l);
-    if (M->cfg.form == GNP_LAYER_PAPER) {
-      GNP_TRY(set_layer_attr<GNP_LAYER_PAPER>(smem));
-      k_layer_batch<GNP_LAYER_PAPER><<<wgrid, 256, smem, st>>>(A->rp, A->col, M->valhat, X, AG, Out, n, B, lw);
-    } else {
-      GNP_TRY(set_layer_attr<GNP_LAYER_RESID>(smem));
-      k_layer_batch<GNP_LAYER_RESID><<<wgrid, 256, smem, st>>>(A->rp, A->col, M->valhat, X, AG, Out, n, B, lw);
-    }
+    GNP_TRY(layer_batch_launch(M->cfg.form, B, wgrid, smem, st, A->rp, A->col, M->valhat, X, AG, Out, n, lw));
   }
   k_dec_batch<<<grid_rows(R), 256, 0, st>>>(T->Hs + (size_t)L * R * 16, T->tau, R, B, sqrt_n,
                                             M->w_dev + dec_off(L), T->z);
@@ -1074,9 +1152,8 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
     else
       k_layer_bwd_rows<GNP_LAYER_RESID><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
     // dX = local + A_hat^T Y (gather through the canonical CSC)
-    k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->csc.ptr, A->csc.idx, M->valhat_t,
-                                        reinterpret_cast<const float4*>(T->y16), n, B * 4, 1.0f,
-                                        reinterpret_cast<const float4*>(Gn), 1.0f, reinterpret_cast<float4*>(Gn));
+    GNP_TRY(spmm_nodes(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->y16), n, B * 4,
+                       1.0f, reinterpret_cast<const float4*>(Gn), 1.0f, reinterpret_cast<float4*>(Gn), st));
     float* gl = g + layer_off(l);
     if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((wgrad<16, 16>(T, X, T->gp16, gl, nullptr, st)));  // dU
     else GNP_TRY_CUDA(cudaMemsetAsync(gl, 0, sizeof(float) * 256, st));
@@ -1155,13 +1232,11 @@ static int train_from_b(gnp_model* M, cudaStream_t st) {
   const int W4 = B / 4;
   GNP_TRY(forward_batch(M, T->bb, st));
   // r = A_hat z - b; loss = mean |r|; s = sign(r); dz = A_hat^T s / (n B)
-  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(T->z), n, W4,
-                                      1.0f, reinterpret_cast<const float4*>(T->bb), -1.0f,
-                                      reinterpret_cast<float4*>(T->rr));
+  GNP_TRY(spmm_nodes(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(T->z), n, W4, 1.0f,
+                     reinterpret_cast<const float4*>(T->bb), -1.0f, reinterpret_cast<float4*>(T->rr), st));
   k_l1<<<red_blocks(R), 256, 0, st>>>(T->rr, R, T->red.partials, T->red.counter, T->loss);
-  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->rr),
-                                      n, W4, (float)(1.0 / (double)R), nullptr, 0.0f,
-                                      reinterpret_cast<float4*>(T->dz));
+  GNP_TRY(spmm_nodes(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->rr), n, W4,
+                     (float)(1.0 / (double)R), nullptr, 0.0f, reinterpret_cast<float4*>(T->dz), st));
   GNP_TRY(backward_batch(M, T->dz, st));
   const int cnt = weight_count(M->cfg.L);
   k_adam<<<1, 1024, 0, st>>>(M->w_dev, M->w_best, T->grad, T->adam_m, T->adam_v, cnt, T->loss, T->best_loss,
@@ -1177,8 +1252,8 @@ static int train_pairs(gnp_model* M, const float* x, cudaStream_t st) {
   const gnp_mat* A = M->A;
   const int n = A->n;
   const int wgrid = std::min((n + 7) / 8, 16 * NUM_SMS_GB300);
-  k_spmm_nodes<<<wgrid, 256, 0, st>>>(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(x), n, T->B / 4,
-                                      1.0f, nullptr, 0.0f, reinterpret_cast<float4*>(T->bb));
+  GNP_TRY(spmm_nodes(A->rp, A->col, M->valhat, reinterpret_cast<const float4*>(x), n, T->B / 4, 1.0f, nullptr,
+                     0.0f, reinterpret_cast<float4*>(T->bb), st));
   return train_from_b(M, st);
 }
 
