@@ -110,6 +110,7 @@ struct gnp_mat {
   int n = 0;
   long long nnz = 0;
   int device = 0;
+  int max_deg = 0;           // most nonzeros in one row
   int* rp = nullptr;
   int* col = nullptr;
   double* val = nullptr;
@@ -173,14 +174,40 @@ __device__ __forceinline__ bool last_block_arrive(unsigned* counter) {
 
 // In the last block: out[k] = sum_b partials[b*K + k] for k < K, in a fixed order
 // (lane-strided over blocks, then a fixed shuffle tree).  out is shared memory.
+// This runs on one block while the rest of the GPU waits, so it is latency that counts:
+// a warp takes RP_COLS columns at a time and issues the loads of up to RP_UNROLL blocks
+// per lane (for every column) before it adds any, i.e. one L2 round trip per 256 blocks
+// instead of one per 32.  The additions keep the order b = lane, lane + 32, ...
+constexpr int RP_COLS = 4, RP_UNROLL = 8;
 __device__ __forceinline__ void reduce_partials(const double* partials, int nblocks, int K,
                                                 double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int k = w; k < K; k += nw) {
-    double s = 0.0;
-    for (int b = lane; b < nblocks; b += 32) s += __ldcg(partials + (size_t)b * K + k);
-    s = warp_sum(s);
-    if (lane == 0) out[k] = s;
+  for (int k0 = w * RP_COLS; k0 < K; k0 += nw * RP_COLS) {
+    double s[RP_COLS];
+#pragma unroll
+    for (int c = 0; c < RP_COLS; ++c) s[c] = 0.0;
+    for (int b0 = lane; b0 < nblocks; b0 += 32 * RP_UNROLL) {
+      double p[RP_UNROLL][RP_COLS];
+#pragma unroll
+      for (int u = 0; u < RP_UNROLL; ++u) {
+        const int b = b0 + 32 * u;
+#pragma unroll
+        for (int c = 0; c < RP_COLS; ++c)
+          p[u][c] = (b < nblocks && k0 + c < K) ? __ldcg(partials + (size_t)b * K + k0 + c) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < RP_UNROLL; ++u) {
+        if (b0 + 32 * u < nblocks) {
+#pragma unroll
+          for (int c = 0; c < RP_COLS; ++c) s[c] += p[u][c];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < RP_COLS; ++c) {
+      const double t = warp_sum(s[c]);
+      if (lane == 0 && k0 + c < K) out[k0 + c] = t;
+    }
   }
   __syncthreads();
 }

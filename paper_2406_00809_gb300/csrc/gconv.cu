@@ -445,6 +445,263 @@ k_decode(const HT* __restrict__ H, ColPtr zp, const double* __restrict__ tau, do
   }
 }
 
+// ---------------------------------------------------------------- k_gconv_row
+//
+// Res-GCONV for matrices whose rows are all short (at most ROW_DMAX nonzeros: stencils,
+// meshes).  A block of TILE threads owns RB = TILE / LPR consecutive rows.
+//   gather: LPR lanes per row, lane p holding the row-vector quarter/half [p*PW, p*PW+PW)
+//     (PW = 16 / LPR values).  Row pointers, column indices and values are loaded before
+//     the programmatic-launch wait (the matrix is never written), so they overlap the
+//     previous layer's tail; after the wait a lane loads its part of the block's own row
+//     and of every neighbour row, DB neighbours in flight, and sums a_ij h_j in column
+//     order.  No slot bookkeeping, no carries: each row is one lane group's.
+//   epilogue: the parts of h_i and (A_hat H)_i meet in shared memory; thread t computes
+//     outputs [q*PW, q*PW+PW) of row t % RB with q = t / RB, which is the same for a whole
+//     warp, so U and W stay uniform constant-bank operands; it writes them straight out.
+//   decoder (last layer): the output parts meet in shared memory again and part q
+//     evaluates decoder units [q*32/LPR, (q+1)*32/LPR); the parts add in order.
+constexpr int ROW_DMAX = 16;
+
+template <class HT, int LPR>
+struct RowTraits;
+template <>
+struct RowTraits<float, 2> {  // 8 floats: two 16-byte loads
+  static constexpr int PW = 8;
+  __device__ __forceinline__ static void load(const float* X, int c, int p, float (&x)[8]) {
+    const float4* s = reinterpret_cast<const float4*>(X + (size_t)c * 16 + 8 * p);
+    const float4 a = __ldg(s), b = __ldg(s + 1);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+  }
+  __device__ __forceinline__ static void store(float* Y, int r, int p, const float (&o)[8]) {
+    float4* d = reinterpret_cast<float4*>(Y + (size_t)r * 16 + 8 * p);
+    d[0] = make_float4(o[0], o[1], o[2], o[3]);
+    d[1] = make_float4(o[4], o[5], o[6], o[7]);
+  }
+};
+template <>
+struct RowTraits<float, 4> {  // 4 floats: one 16-byte load
+  static constexpr int PW = 4;
+  __device__ __forceinline__ static void load(const float* X, int c, int p, float (&x)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(X + (size_t)c * 16 + 4 * p));
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  }
+  __device__ __forceinline__ static void store(float* Y, int r, int p, const float (&o)[4]) {
+    *reinterpret_cast<float4*>(Y + (size_t)r * 16 + 4 * p) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+template <>
+struct RowTraits<uint16_t, 2> {  // 8 bfloat16: one 16-byte load
+  static constexpr int PW = 8;
+  __device__ __forceinline__ static void load(const uint16_t* X, int c, int p, float (&x)[8]) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(X + (size_t)c * 16 + 8 * p));
+    x[0] = bf16lo(t.x); x[1] = bf16hi(t.x); x[2] = bf16lo(t.y); x[3] = bf16hi(t.y);
+    x[4] = bf16lo(t.z); x[5] = bf16hi(t.z); x[6] = bf16lo(t.w); x[7] = bf16hi(t.w);
+  }
+  __device__ __forceinline__ static void store(uint16_t* Y, int r, int p, const float (&o)[8]) {
+    *reinterpret_cast<uint4*>(Y + (size_t)r * 16 + 8 * p) =
+        make_uint4(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]), pack_bf16x2(o[4], o[5]),
+                   pack_bf16x2(o[6], o[7]));
+  }
+};
+template <>
+struct RowTraits<uint16_t, 4> {  // 4 bfloat16: one 8-byte load
+  static constexpr int PW = 4;
+  __device__ __forceinline__ static void load(const uint16_t* X, int c, int p, float (&x)[4]) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(X + (size_t)c * 16 + 4 * p));
+    x[0] = bf16lo(t.x); x[1] = bf16hi(t.x); x[2] = bf16lo(t.y); x[3] = bf16hi(t.y);
+  }
+  __device__ __forceinline__ static void store(uint16_t* Y, int r, int p, const float (&o)[4]) {
+    *reinterpret_cast<uint2*>(Y + (size_t)r * 16 + 4 * p) =
+        make_uint2(pack_bf16x2(o[0], o[1]), pack_bf16x2(o[2], o[3]));
+  }
+};
+
+constexpr int RSTR = 20;  // shared row stride in floats (conflict-free 16-byte accesses)
+
+template <int LPR>
+struct RowSmem {
+  static constexpr int RB = TILE / LPR;
+  __align__(16) float h[RB * RSTR];
+  __align__(16) float agg[RB * RSTR];
+  float zpart[LPR][RB];
+};
+
+// Gather into shared memory: part p of h_i and of (A_hat H)_i for the block's rows.
+// Before the call the caller has loaded rs / deg / c / v (first DB entries) of its row.
+template <class HT, int LPR, int DB>
+__device__ __forceinline__ void row_gather(RowSmem<LPR>& sm, const int* __restrict__ col,
+                                           const float* __restrict__ valhat, const HT* __restrict__ Hin,
+                                           int r, int gr, int p, int rs, int deg, const int (&c0)[DB],
+                                           const float (&v0)[DB]) {
+  using RT = RowTraits<HT, LPR>;
+  constexpr int PW = RT::PW;
+  float acc[PW], hv[PW];
+#pragma unroll
+  for (int k = 0; k < PW; ++k) acc[k] = 0.0f;
+  if (deg >= 0) {
+    RT::load(Hin, r, p, hv);
+    float x[DB][PW];
+#pragma unroll
+    for (int k = 0; k < DB; ++k)
+      if (k < deg) RT::load(Hin, c0[k], p, x[k]);
+#pragma unroll
+    for (int k = 0; k < DB; ++k)
+      if (k < deg) {
+#pragma unroll
+        for (int i = 0; i < PW; ++i) acc[i] = fmaf(v0[k], x[k][i], acc[i]);
+      }
+    for (int e0 = DB; e0 < deg; e0 += DB) {  // rows longer than DB: further batches
+      int c[DB];
+      float v[DB];
+#pragma unroll
+      for (int k = 0; k < DB; ++k) {
+        c[k] = (e0 + k < deg) ? __ldg(col + rs + e0 + k) : 0;
+        v[k] = (e0 + k < deg) ? __ldg(valhat + rs + e0 + k) : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < DB; ++k)
+        if (e0 + k < deg) RT::load(Hin, c[k], p, x[k]);
+#pragma unroll
+      for (int k = 0; k < DB; ++k)
+        if (e0 + k < deg) {
+#pragma unroll
+          for (int i = 0; i < PW; ++i) acc[i] = fmaf(v[k], x[k][i], acc[i]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PW / 4; ++q) {
+      reinterpret_cast<float4*>(sm.h + gr * RSTR + p * PW)[q] =
+          make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+      reinterpret_cast<float4*>(sm.agg + gr * RSTR + p * PW)[q] =
+          make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+  }
+}
+
+// Row pointers and the first DB column indices / values of this lane's row.
+template <int DB>
+__device__ __forceinline__ void row_prefetch(const int* __restrict__ rp, const int* __restrict__ col,
+                                             const float* __restrict__ valhat, int r, int n, int& rs,
+                                             int& deg, int (&c)[DB], float (&v)[DB]) {
+  rs = 0;
+  deg = -1;  // no row
+  if (r < n) {
+    rs = __ldg(rp + r);
+    deg = __ldg(rp + r + 1) - rs;
+  }
+#pragma unroll
+  for (int k = 0; k < DB; ++k) {
+    c[k] = (k < deg) ? __ldg(col + rs + k) : 0;
+    v[k] = (k < deg) ? __ldg(valhat + rs + k) : 0.0f;
+  }
+}
+
+// Outputs [Q*PW, Q*PW+PW) of epilogue row er (h and agg from shared memory).
+template <int FORM, int LPR, int Q>
+__device__ __forceinline__ void row_layer(const RowSmem<LPR>& sm, int er, const LayerW& lw,
+                                          float (&o)[16 / LPR]) {
+  float h[16], agg[16];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float4 a = reinterpret_cast<const float4*>(sm.h + er * RSTR)[q];
+    const float4 b = reinterpret_cast<const float4*>(sm.agg + er * RSTR)[q];
+    h[4 * q] = a.x; h[4 * q + 1] = a.y; h[4 * q + 2] = a.z; h[4 * q + 3] = a.w;
+    agg[4 * q] = b.x; agg[4 * q + 1] = b.y; agg[4 * q + 2] = b.z; agg[4 * q + 3] = b.w;
+  }
+  layer_part<FORM, Q * (16 / LPR), 16 / LPR>(h, agg, lw, o);
+}
+
+template <int FORM, int LPR>
+__device__ __forceinline__ void row_layer_q(const RowSmem<LPR>& sm, int er, int q, const LayerW& lw,
+                                            float (&o)[16 / LPR]) {
+  if constexpr (LPR == 2) {
+    if (q == 0) row_layer<FORM, 2, 0>(sm, er, lw, o);
+    else row_layer<FORM, 2, 1>(sm, er, lw, o);
+  } else {
+    if (q == 0) row_layer<FORM, 4, 0>(sm, er, lw, o);
+    else if (q == 1) row_layer<FORM, 4, 1>(sm, er, lw, o);
+    else if (q == 2) row_layer<FORM, 4, 2>(sm, er, lw, o);
+    else row_layer<FORM, 4, 3>(sm, er, lw, o);
+  }
+}
+
+template <class HT, int FORM, int LPR, int DB>
+__global__ void __launch_bounds__(TILE)
+k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
+            const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
+            const __grid_constant__ LayerW lw) {
+  constexpr int RB = TILE / LPR;
+  __shared__ RowSmem<LPR> sm;
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * RB;
+  const int gr = t / LPR, p = t % LPR;
+  int rs, deg, c[DB];
+  float v[DB];
+  row_prefetch<DB>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
+  pdl_wait();
+  if (ctl && !ctl[1]) return;
+  row_gather<HT, LPR, DB>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
+  __syncthreads();
+  const int er = t % RB, q = t / RB;
+  float o[16 / LPR];
+  if (r0 + er < n) row_layer_q<FORM, LPR>(sm, er, q, lw, o);
+  pdl_release();
+  if (r0 + er < n) RowTraits<HT, LPR>::store(Hout, r0 + er, q, o);
+}
+
+template <class HT, int FORM, int LPR, int DB>
+__global__ void __launch_bounds__(TILE)
+k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
+                const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
+                const int* __restrict__ ctl, const __grid_constant__ LayerW lw, const __grid_constant__ DecW dw) {
+  constexpr int RB = TILE / LPR;
+  constexpr int PW = 16 / LPR;
+  __shared__ RowSmem<LPR> sm;
+  const int t = threadIdx.x;
+  const int r0 = blockIdx.x * RB;
+  const int gr = t / LPR, p = t % LPR;
+  int rs, deg, c[DB];
+  float v[DB];
+  row_prefetch<DB>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
+  pdl_wait();
+  if (ctl && !ctl[1]) return;
+  row_gather<HT, LPR, DB>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
+  __syncthreads();
+  const int er = t % RB, q = t / RB;
+  const bool valid = r0 + er < n;
+  float o[PW];
+  if (valid) row_layer_q<FORM, LPR>(sm, er, q, lw, o);
+  __syncthreads();  // every thread is done with h and agg
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < PW; ++k) sm.agg[er * RSTR + q * PW + k] = o[k];
+  }
+  __syncthreads();
+  if (valid) {
+    float full[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) full[k] = sm.agg[er * RSTR + k];
+    float part;
+    if constexpr (LPR == 2) {
+      part = q == 0 ? decode_part<0, 16>(full, dw) : decode_part<16, 16>(full, dw);
+    } else {
+      part = q == 0 ? decode_part<0, 8>(full, dw)
+                    : q == 1 ? decode_part<8, 8>(full, dw) : q == 2 ? decode_part<16, 8>(full, dw)
+                                                                     : decode_part<24, 8>(full, dw);
+    }
+    sm.zpart[q][er] = part;
+  }
+  __syncthreads();
+  if (q == 0 && valid) {
+    const double tv = *tau;
+    const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+    float zz = dw.b2;
+#pragma unroll
+    for (int k = 0; k < LPR; ++k) zz += sm.zpart[k][er];
+    static_cast<float*>(colptr(zp))[r0 + er] = zz * back;
+  }
+}
+
 template <class HT>
 __global__ void k_hidden_to_f32(const HT* __restrict__ H, float* __restrict__ out, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
@@ -607,6 +864,52 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
   return GNP_OK;
 }
 
+// Layers 0..L-1 with the short-row kernels (RB = TILE / LPR rows per block).
+template <class HT, int FORM, int LPR, int DB>
+static int launch_layers_row(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, const int* ctl,
+                             cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const DecW& dw, double sqrt_n) {
+  const gnp_mat* A = M->A;
+  const int n = A->n, L = M->cfg.L;
+  constexpr int RB = TILE / LPR;
+  const int nb = (n + RB - 1) / RB;
+  const long long hcount = (long long)n * 16;
+  const int fused_last = (L > 0 && !trace) ? 1 : 0;
+  for (int l = 0; l < L - fused_last; ++l) {
+    LayerW lw;
+    fill_layer_w(M->w_host, l, lw);
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
+    GNP_TRY_CUDA(launch_pdl(k_gconv_row<HT, FORM, LPR, DB>, nb, 0, st, A->rp, A->col, (const float*)M->valhat,
+                            (const HT*)H0, H1, n, ctl, lw));
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
+    if (trace)
+      k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H1, trace + (size_t)(l + 1) * hcount, hcount);
+    std::swap(H0, H1);
+  }
+  if (fused_last) {
+    LayerW lw;
+    fill_layer_w(M->w_host, L - 1, lw);
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
+    GNP_TRY_CUDA(launch_pdl(k_gconv_row_dec<HT, FORM, LPR, DB>, nb, 0, st, A->rp, A->col,
+                            (const float*)M->valhat, (const HT*)H0, z, (const double*)W.tau, sqrt_n, n, ctl, lw,
+                            dw));
+    if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
+  } else {
+    k_decode<HT><<<(n + TILE - 1) / TILE, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
+  }
+  return GNP_OK;
+}
+
+// Short-row kernels when every row has at most ROW_DMAX nonzeros (GNP_GCONV_ROWK=0 in the
+// environment forces the tile kernels; GNP_ROW_LPR=2|4 and GNP_ROW_DB=4|8 set the lanes per
+// row and the neighbour loads in flight, for tuning).
+static int row_kernel_mode(const gnp_mat* A) {
+  static const int on = env_int("GNP_GCONV_ROWK", 1);
+  if (!on || A->max_deg > ROW_DMAX) return 0;
+  static const int lpr = env_int("GNP_ROW_LPR", 4);
+  static const int db = env_int("GNP_ROW_DB", 4);
+  return (lpr == 4 ? 4 : 2) * 10 + (db == 8 ? 8 : 4);
+}
+
 template <class HT, int FORM>
 static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
                       const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W) {
@@ -626,10 +929,17 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   HT* H1 = static_cast<HT*>(W.H[1]);
   k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, (long long)n * 16);
-  if (gconv_rows<HT>() == 128)
-    GNP_TRY((launch_layers<HT, FORM, 128>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));
-  else
-    GNP_TRY((launch_layers<HT, FORM, 256>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));
+  switch (row_kernel_mode(A)) {
+    case 24: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 28: GNP_TRY((launch_layers_row<HT, FORM, 2, 8>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 44: GNP_TRY((launch_layers_row<HT, FORM, 4, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 48: GNP_TRY((launch_layers_row<HT, FORM, 4, 8>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    default:
+      if (gconv_rows<HT>() == 128)
+        GNP_TRY((launch_layers<HT, FORM, 128>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));
+      else
+        GNP_TRY((launch_layers<HT, FORM, 256>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));
+  }
   return check_launch("gnp apply");
 }
 

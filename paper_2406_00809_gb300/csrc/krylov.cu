@@ -2,16 +2,20 @@
 // Algorithm 1), float64 throughout except the preconditioner output z_j (float32).
 //
 // One Arnoldi step j (all on the device, no host round trip):
-//   [M]    z_j = M(v_j): k_vnorm first turns the stored w into v_j = w / h_{j,j-1}
-//          (or r / beta), then the GNP kernels write Z[:, j].  For M = I, k_vscale
-//          only normalises and z_j = v_j.
-//   k_spmv_tile   w = A z_j (nnz-balanced tile gather, float64 values).
-//   k_cgs<1>      h1 = V_j^T w and ||w||^2.
-//   k_cgs<2>      w1 = w - V_j h1 (stored in place), h2 = V_j^T w1.
-//   k_cgs<3>      w2 = w1 - V_j h2 -> V[:, j+1] (not yet normalised), ||w2||; its last
-//                 block forms column j of H_bar (h1 + h2, ||w2||), applies the previous
-//                 Givens rotations and the new one, updates g and the residual estimate
-//                 |g_{j+1}| (Sec. 4), and decides whether the cycle continues.
+//   [M]    z_j = M(v_j): the preconditioner's first kernel turns the stored w into
+//          v_j = w / h_{j,j-1} (or r / beta) in place (the GNP encoder, k_vscale for
+//          M = I, the Jacobi and inner-GMRES kernels), then writes Z[:, j].
+//   k_spmv_dot    w = A z_j (tile gather, float64 values) fused with CGS2 pass 1:
+//                 h1 = V_j^T w and ||w||^2 (the breakdown reference).
+//   k_cgs<4>      w1 = w - V_j h1 (in place), h2 = V_j^T w1 and ||w1||^2.
+//   k_vnext       block 0 forms column j of H_bar (h1 + h2 and h_{j+1,j} =
+//                 sqrt(||w1||^2 - ||h2||^2)), applies the previous Givens rotations and
+//                 the new one, updates g and the residual estimate |g_{j+1}| (Sec. 4),
+//                 and decides whether the cycle continues; meanwhile the other blocks form
+//                 V[:, j+1] = w1 - V_j h2 (normalised by the next step's first kernel).
+// The Arnoldi process of the training sampler (arnoldi_basis) keeps the explicit third
+// pass: k_spmv_tile, k_cgs<1> (h1, ||w||^2), k_cgs<2> (w1, h2), k_cgs<3> (w2 -> V[:, j+1],
+// ||w2||, the same last-block update).
 // Cycle end: k_xupdate (y = R^{-1} g by back substitution, x += Z y) and k_residual
 // (r = b - A x, beta = ||r||, which restarts the cycle).  Every kernel reads the step
 // index j and an `active` flag from device memory, so one captured CUDA graph replays a
@@ -233,6 +237,58 @@ k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double
   }
 }
 
+// k_spmv_dot for matrices whose rows are all short (at most SPMV_ROW_DMAX nonzeros): one
+// thread per row computes w_i = sum_j a_ij x_j in column order (no slot bookkeeping), then
+// the block forms its share of h1 = V_j^T w and ||w||^2 over its rows, KC columns at a
+// time, as k_cgs<1> does.  Same result layout and last-block reduction as k_spmv_dot.
+constexpr int SPMV_ROW_DMAX = 32;
+
+template <class XT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+               ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
+               double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
+  if (!st->active) return;
+  __shared__ double sred[KC * RSTRIDE];
+  __shared__ double shtot[GNP_MAX_RESTART + 2];
+  const int j = st->j;
+  const int K = j + 2;  // h1[0..j] and ||w||^2
+  const size_t ld = (size_t)n;
+  const XT* x = static_cast<const XT*>(colptr_k(xp));
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstride = gridDim.x * blockDim.x;
+  for (int i = gtid; i < n; i += gstride) {
+    const int rs = __ldg(rp + i), re = __ldg(rp + i + 1);
+    double s = 0.0;
+    for (int e = rs; e < re; ++e) s = fma(__ldg(val + e), (double)x[__ldg(col + e)], s);
+    w[i] = s;
+  }
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    double acc[KC];
+#pragma unroll
+    for (int kc = 0; kc < KC; ++kc) acc[kc] = 0.0;
+    for (int i = gtid; i < n; i += gstride) {
+      const double y = w[i];
+#pragma unroll
+      for (int kc = 0; kc < KC; ++kc) {
+        const int k = k0 + kc;
+        if (k < K) {
+          const double vk = (k == j + 1) ? y : V[k * ld + i];
+          acc[kc] += vk * y;
+        }
+      }
+    }
+    block_reduce_kc<false>(acc, sred, partials + (size_t)blockIdx.x * K + k0, min(KC, K - k0));
+  }
+  if (!last_block_arrive(counter)) return;
+  reduce_partials(partials, gridDim.x, K, shtot);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k <= j; ++k) h1[k] = shtot[k];
+    st->wnorm0 = sqrt(shtot[j + 1]);
+    *counter = 0;
+  }
+}
+
 // r = b - A x -> V[:, 0], beta = ||r||; the last block restarts the cycle state.
 __global__ void __launch_bounds__(TILE)
 k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
@@ -319,16 +375,18 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
       double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
       unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
   if (!st->active) return;
+  constexpr bool NORM = PASS == 1 || PASS == 4;  // the dots also give ||w||^2 (entry j+1)
   __shared__ double shh[GNP_MAX_RESTART + 2];
   __shared__ double shred[KC][32];  // KC*32 = 256 >= GNP_MAX_RESTART: reused for sines
   __shared__ double sred[PASS == 3 ? 1 : KC * RSTRIDE];
   __shared__ double shtot[GNP_MAX_RESTART + 4];
+  __shared__ double sx[PASS == 4 ? 2 * (GNP_MAX_RESTART + 4) : 1];
   const int j = st->j;
   const size_t ld = (size_t)n;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gstride = gridDim.x * blockDim.x;
   if (PASS >= 2) {
-    const double* hp = (PASS == 2) ? h1 : h2;
+    const double* hp = (PASS == 3) ? h2 : h1;
     for (int k = threadIdx.x; k <= j; k += blockDim.x) shh[k] = hp[k];
     __syncthreads();
   }
@@ -346,7 +404,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
     double t = block_sum(acc, shred[0]);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
   } else {
-    if (PASS == 2) {
+    if (PASS == 2 || PASS == 4) {
       for (int i = gtid; i < n; i += gstride) {
         double x = w[i];
 #pragma unroll 8
@@ -354,7 +412,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
         w[i] = x;
       }
     }
-    const int K = (PASS == 1) ? j + 2 : j + 1;  // pass 1 also ||w||^2 as entry j+1
+    const int K = NORM ? j + 2 : j + 1;  // passes 1 and 4 also ||w||^2 as entry j+1
     for (int k0 = 0; k0 < K; k0 += KC) {
       double acc[KC];
 #pragma unroll
@@ -365,7 +423,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
         for (int kc = 0; kc < KC; ++kc) {
           const int k = k0 + kc;
           if (k < K) {
-            const double vk = (PASS == 1 && k == j + 1) ? y : V[k * ld + i];
+            const double vk = (NORM && k == j + 1) ? y : V[k * ld + i];
             acc[kc] += vk * y;
           }
         }
@@ -374,8 +432,18 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
     }
   }
   if (!last_block_arrive(counter)) return;
-  const int K = (PASS == 1) ? j + 2 : (PASS == 2 ? j + 1 : 1);
+  const int K = NORM ? j + 2 : (PASS == 2 ? j + 1 : 1);
   reduce_partials(partials, gridDim.x, K, shtot);
+  if (PASS == 4) {
+    // h2 and ||w1||^2 go out; k_vnext finishes the step (Givens update in its block 0)
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = shtot[i];
+    if (threadIdx.x == 0) {
+      st->w1sq = shtot[j + 1];
+      st->jv = j;
+      *counter = 0;
+    }
+    return;
+  }
   if (PASS == 3) {
     // stage the Givens inputs with all threads: column j = h1 + h2, the previous
     // rotations (reuse shh for the cosines, shred for the sines)
@@ -402,6 +470,59 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   // PASS 3: column j of H_bar and the Givens update of the least-squares problem
   const double hn = sqrt(shtot[0]);
   arnoldi_step_finish(st, j, shtot + 1, hn, shh, &shred[0][0], H, R, cs, sn, g, hist, thist);
+}
+
+// After k_cgs<4>, for step j = st->jv.  Block 0 finishes the step while the others form
+// the next basis vector, so the serial Givens update is off the critical path:
+//   block 0: column j of H_bar = h1 + h2, h_{j+1,j} = ||w1 - V h2|| =
+//     sqrt(||w1||^2 - ||h2||^2) (V has orthonormal columns to working precision and
+//     h2 = V^T w1; ||h2|| is O(eps ||w||) after the first pass, so nothing cancels unless
+//     w1 itself is at the breakdown level, where the step ends anyway), then
+//     arnoldi_step_finish (rotations, g, residual estimate, the continue decision).
+//   blocks 1..: V[:, j+1] = w1 - V_j h2 (not yet normalised: the next step's first kernel
+//     divides by st->vscale = h_{j+1,j}).  The column is formed even when block 0 ends the
+//     cycle (V has m+1 columns; an unused column is harmless); these blocks read only jv,
+//     which block 0 does not write.
+__global__ void __launch_bounds__(RED_THREADS)
+k_vnext(double* __restrict__ V, int n, const double* __restrict__ w, DevState* st, const double* __restrict__ h1,
+        const double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
+        double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
+        unsigned long long* __restrict__ thist) {
+  __shared__ double shh[GNP_MAX_RESTART + 4];
+  __shared__ double scs[GNP_MAX_RESTART + 4];
+  __shared__ double ssn[GNP_MAX_RESTART + 4];
+  const int j = st->jv;
+  if (blockIdx.x == 0) {
+    __shared__ double sh2[GNP_MAX_RESTART + 4];
+    if (!st->active) return;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      const double b2 = h2[i];
+      shh[i] = h1[i] + b2;
+      sh2[i] = b2;
+    }
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      scs[i] = cs[i];
+      ssn[i] = sn[i];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double s2 = 0.0;
+    for (int i = 0; i <= j; ++i) s2 += sh2[i] * sh2[i];
+    const double hn = sqrt(fmax(st->w1sq - s2, 0.0));
+    arnoldi_step_finish(st, j, shh, hn, scs, ssn, H, R, cs, sn, g, hist, thist);
+    return;
+  }
+  if (!st->active) return;
+  const size_t ld = (size_t)n;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) shh[k] = h2[k];
+  __syncthreads();
+  double* vout = V + (size_t)(j + 1) * ld;
+  for (int i = (blockIdx.x - 1) * blockDim.x + threadIdx.x; i < n; i += (gridDim.x - 1) * blockDim.x) {
+    double x = w[i];
+#pragma unroll 8
+    for (int k = 0; k <= j; ++k) x -= V[k * ld + i] * shh[k];
+    vout[i] = x;
+  }
 }
 
 // y = R^{-1} g (back substitution, redundantly in every block), x += Z[:, :jj] y.
@@ -464,6 +585,25 @@ int solver_ensure_zd(Solver* S, int m) {
   return GNP_OK;
 }
 
+// Row-per-thread SpMV for matrices without long rows (GNP_SPMV_ROWK=0 in the environment
+// forces the tile kernel, for tuning).
+static bool spmv_short_rows(const gnp_mat* A) {
+  static const char* e = getenv("GNP_SPMV_ROWK");
+  static const bool on = !(e && e[0] == '0');
+  return on && A->max_deg <= SPMV_ROW_DMAX;
+}
+
+// w = A x (x float64) with CGS2 pass 1, on the kernel that suits the row lengths.
+static void spmv_dot_f64(const gnp_mat* A, ColPtr x, Solver* S, int ndot, int ncg, bool short_rows,
+                         cudaStream_t st) {
+  if (short_rows)
+    k_spmv_dot_row<double><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, x, S->w, S->V, A->n, S->st,
+                                                        S->h1, S->red.partials, S->red.counter);
+  else
+    k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, x, S->w, S->V, A->n, S->st, S->h1,
+                                              S->red.partials, S->red.counter);
+}
+
 // Enqueue one restart cycle: m Arnoldi steps, x update, residual.
 int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, double* x,
                  cudaStream_t st, bool prof, const ApplyWs* ws) {
@@ -474,6 +614,7 @@ int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, d
   const int ndot = std::min(nt, 4 * NUM_SMS_GB300);
   const int* ctl = reinterpret_cast<const int*>(S->st);
   const int* jptr = ctl;
+  const bool short_rows = spmv_short_rows(A);
   const bool f64z = P.kind == GNP_PRECOND_JACOBI || P.kind == GNP_PRECOND_GMRES;
   if (f64z) GNP_REQUIRE(S->Zd && S->zd_m >= m, "launch_cycle: float64 directions not allocated");
   for (int j = 0; j < m; ++j) {
@@ -483,25 +624,27 @@ int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, d
       ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
       cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
       GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws));
-      k_spmv_dot<float><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st, S->h1,
-                                               S->red.partials, S->red.counter);
+      if (short_rows)
+        k_spmv_dot_row<float><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st,
+                                                           S->h1, S->red.partials, S->red.counter);
+      else
+        k_spmv_dot<float><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st, S->h1,
+                                                 S->red.partials, S->red.counter);
     } else if (f64z) {
       ColPtr z{S->Zd, sizeof(double) * (size_t)n, jptr, 0};
       if (P.kind == GNP_PRECOND_JACOBI)
         GNP_TRY(jacobi_launch(P.dinv, v, S->st, z, n, st));
       else
         GNP_TRY(inner_gmres_launch(A, P.inner, v, S->st, z, st));
-      k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st, S->h1,
-                                                S->red.partials, S->red.counter);
+      spmv_dot_f64(A, z, S, ndot, ncg, short_rows, st);
     } else {
       k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
-      k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, v, S->w, S->V, n, S->st, S->h1,
-                                                S->red.partials, S->red.counter);
+      spmv_dot_f64(A, v, S, ndot, ncg, short_rows, st);
     }
-    k_cgs<2><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+    k_cgs<4><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
                                          S->g, S->hist, S->thist, S->red.partials, S->red.counter);
-    k_cgs<3><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+    k_vnext<<<1 + nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn, S->g,
+                                            S->hist, S->thist);
   }
   const int xsm = (int)sizeof(double) * m * m;
   if (P.kind == GNP_PRECOND_GNP)
@@ -595,12 +738,11 @@ int inner_gmres_launch(gnp_mat* A, InnerGmres* G, ColPtr v, DevState* outer, Col
   for (int j = 0; j < k; ++j) {
     k_vscale<<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st);
     ColPtr vj{S->V, sizeof(double) * (size_t)n, jptr, 0};
-    k_spmv_dot<double><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, vj, S->w, S->V, n, S->st, S->h1,
-                                              S->red.partials, S->red.counter);
-    k_cgs<2><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
+    spmv_dot_f64(A, vj, S, ndot, ncg, spmv_short_rows(A), st);
+    k_cgs<4><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
                                          S->g, S->hist, S->thist, S->red.partials, S->red.counter);
-    k_cgs<3><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
-                                         S->g, S->hist, S->thist, S->red.partials, S->red.counter);
+    k_vnext<<<1 + nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn, S->g,
+                                            S->hist, S->thist);
   }
   k_xupdate<double><<<nb, RED_THREADS, (int)sizeof(double) * k * k, st>>>(S->V, G->x, n, S->st, S->R, S->g);
   k_inner_end<<<nb, RED_THREADS, 0, st>>>(G->x, outer, z, n);

@@ -240,6 +240,7 @@ int gnp_mat_create(int n, long long nnz, const int* row_ptr, const int* col, con
   gnp_mat* A = new gnp_mat();
   A->n = n;
   A->nnz = nnz;
+  for (int i = 0; i < n; ++i) A->max_deg = std::max(A->max_deg, h_rp[i + 1] - h_rp[i]);
   cudaGetDevice(&A->device);
   int s = GNP_OK;
   if ((s = dev_alloc(&A->rp, (size_t)n + 1)) != GNP_OK ||

@@ -4,6 +4,7 @@
 #include <vector>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -29,8 +30,9 @@ struct DevState {
   int flags;
   int last_flags;  // flags of the cycle that just ended (kept by k_residual)
   int last_jj;     // columns that cycle used
-  int pad;
+  int jv;          // step j whose basis vector k_vnext forms (set by k_cgs<4>)
   double bnorm, tol, rtol, beta, vscale, wnorm0, hn, res_est;
+  double w1sq;     // ||w1||^2 of step jv (k_cgs<4>)
   unsigned long long t0;          // %globaltimer (ns) when the solve began
   unsigned long long timeout_ns;  // 0: no time limit
 };
@@ -49,9 +51,13 @@ constexpr double BREAKDOWN_REL = 1e-14;
 // column chunk, and the float64 pipes of all SMs share the work evenly); up to four per
 // SM on larger systems for memory parallelism.  Never more than red_blocks(n), the
 // capacity of the partial-sum scratch.
+// GNP_DOT_BLOCKS_PER_SM=1..4 in the environment forces the blocks per SM (for tuning).
 inline int dot_blocks(int n) {
+  static const char* e = getenv("GNP_DOT_BLOCKS_PER_SM");
+  static const int forced = e ? atoi(e) : 0;
   const int per = (n + NUM_SMS_GB300 * RED_THREADS * 2 - 1) / (NUM_SMS_GB300 * RED_THREADS * 2);
-  return std::min(red_blocks(n), NUM_SMS_GB300 * std::max(1, std::min(4, per)));
+  const int bps = (forced >= 1 && forced <= 4) ? forced : std::max(1, std::min(4, per));
+  return std::min(red_blocks(n), NUM_SMS_GB300 * bps);
 }
 
 constexpr int KC = 8;  // basis columns per register chunk
@@ -94,9 +100,13 @@ __device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double*
                                                     const double* scs, const double* ssn, double* H,
                                                     double* R, double* cs, double* sn, double* g,
                                                     double* hist, unsigned long long* thist) {
-  const int m = st->m;
+  // one serial thread: the state and g_j come in with one batch of loads and go back at
+  // the end, so that no store to H or R forces a reload of a state field in between
+  DevState s = *st;
+  const double gj = g[j];
+  const int m = s.m;
   const int ldh = m + 1;
-  st->hn = hn;
+  s.hn = hn;
   bool finite = isfinite(hn);
   for (int i = 0; i <= j; ++i) H[(size_t)j * ldh + i] = col[i];
   col[j + 1] = hn;
@@ -109,52 +119,52 @@ __device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double*
   for (int i = 0; i <= j + 1; ++i) finite = finite && isfinite(col[i]);
   const double a = col[j], b = col[j + 1];
   const double rho = hypot(a, b);
-  double c = 1.0, s = 0.0;
+  double c = 1.0, sv = 0.0;
   if (rho != 0.0) {
     c = a / rho;
-    s = b / rho;
+    sv = b / rho;
   }
-  const int iters = st->iters + 1;
-  st->iters = iters;
-  const unsigned long long elapsed = global_ns() - st->t0;
+  const int iters = s.iters + 1;
+  s.iters = iters;
+  const unsigned long long elapsed = global_ns() - s.t0;
   thist[iters] = elapsed;
-  const double wn0 = st->wnorm0;
+  const double wn0 = s.wnorm0;
   int flags = 0;
   int jj;
   if (!finite || !isfinite(rho)) {
     flags |= FL_NAN;
     jj = j;
   } else if (rho <= BREAKDOWN_REL * wn0) {
-    hist[iters] = fabs(g[j]) / st->bnorm;
+    hist[iters] = fabs(gj) / s.bnorm;
     flags |= FL_DROPPED;
     jj = j;
   } else {
     cs[j] = c;
-    sn[j] = s;
+    sn[j] = sv;
     col[j] = rho;
     col[j + 1] = 0.0;
     for (int i = 0; i <= j + 1; ++i) R[(size_t)j * ldh + i] = col[i];
-    const double gj = g[j];
-    g[j + 1] = -s * gj;
+    g[j + 1] = -sv * gj;
     g[j] = c * gj;
     jj = j + 1;
-    const double res = fabs(g[j + 1]);
-    st->res_est = res;
-    hist[iters] = res / st->bnorm;
+    const double res = fabs(-sv * gj);
+    s.res_est = res;
+    hist[iters] = res / s.bnorm;
     if (hn <= BREAKDOWN_REL * wn0) flags |= FL_BREAKDOWN;
-    else if (res <= st->tol) flags |= FL_EST_CONV;
-    else if (iters >= st->maxiters) flags |= FL_MAXIT;
-    else if (st->timeout_ns != 0ull && elapsed >= st->timeout_ns) flags |= FL_TIMEOUT;
+    else if (res <= s.tol) flags |= FL_EST_CONV;
+    else if (iters >= s.maxiters) flags |= FL_MAXIT;
+    else if (s.timeout_ns != 0ull && elapsed >= s.timeout_ns) flags |= FL_TIMEOUT;
     else if (j + 1 >= m) flags |= FL_FULL;
   }
-  st->jj = jj;
-  st->flags = flags;
+  s.jj = jj;
+  s.flags = flags;
   if (flags) {
-    st->active = 0;
+    s.active = 0;
   } else {
-    st->j = j + 1;
-    st->vscale = hn;
+    s.j = j + 1;
+    s.vscale = hn;
   }
+  *st = s;
 }
 
 
