@@ -164,8 +164,8 @@ __device__ __forceinline__ void tile_copy(uint32_t* stile, HT* g, int r0, int ro
 // ---------------------------------------------------------------- k_encode
 
 // Standalone apply: u = (sqrt(n)/tau) v with tau from k_vnorm.  Inside FGMRES
-// (vscale != null): v_j = w / h is unit-norm by construction, so the encoder divides the
-// stored w by the device scalar h, writes v_j back in place and uses tau = 1 (it stores
+// (vscale != null): v_j = w / h is unit-norm by construction, so the encoder scales the
+// stored w by 1/h (h the device scalar), writes v_j back in place and uses tau = 1 (it stores
 // tau = 1 for the decoder's back-scaling).  noscale (the ablation without s): u = v, and
 // tau = sqrt(n) is stored so that the decoder's factor tau/sqrt(n) is 1.
 template <class HT>
@@ -178,21 +178,29 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
   const int r0 = blockIdx.x * TILE;
   const int rows = min(TILE, n - r0);
   const int t = threadIdx.x;
-  double f;
-  if (noscale) {
-    f = 1.0;
-    if (blockIdx.x == 0 && t == 0) *tau = sqrt_n;
-  } else if (vscale) {
-    f = sqrt_n;
-    if (blockIdx.x == 0 && t == 0) *tau = 1.0;
-  } else {
-    const double tv = *tau;
-    f = tv > 0.0 ? sqrt_n / tv : 0.0;
+  // the block's scalars once (a float64 division is slow on GB300): u = f * v, and the
+  // FGMRES step's v_j = w * (1 / h_{j,j-1})
+  __shared__ double s_f, s_inv;
+  if (t == 0) {
+    s_inv = 1.0;
+    if (noscale) {
+      s_f = 1.0;
+      if (blockIdx.x == 0) *tau = sqrt_n;
+    } else if (vscale) {
+      s_f = sqrt_n;
+      s_inv = 1.0 / *vscale;
+      if (blockIdx.x == 0) *tau = 1.0;
+    } else {
+      const double tv = *tau;
+      s_f = tv > 0.0 ? sqrt_n / tv : 0.0;
+    }
   }
+  __syncthreads();
+  const double f = s_f;
   if (t < rows) {
     double x = v[r0 + t];
     if (vscale) {
-      x = x / *vscale;
+      x = x * s_inv;
       v[r0 + t] = x;
     }
     float u = (float)(x * f);
@@ -386,10 +394,14 @@ k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float
   tile_load_rp<typename HTraits<HT>::TR>(sm.g, rp, r0, rows);
   pdl_wait();
   if (ctl && !ctl[1]) return;
-  gconv_load_gather<HT, ROWS>(sm, col, valhat, Hin, r0, rows);
+  __shared__ float s_back;
+  if (threadIdx.x == 0) {  // once per block: a float64 division is slow on GB300
+    const double tv = *tau;
+    s_back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+  }
+  gconv_load_gather<HT, ROWS>(sm, col, valhat, Hin, r0, rows);  // ends with a barrier
   const int t = threadIdx.x % ROWS;
-  const double tv = *tau;
-  const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+  const float back = s_back;
   float* z = static_cast<float*>(colptr(zp));
   if constexpr (ROWS == TILE) {
     float o[16];
@@ -433,15 +445,18 @@ k_decode(const HT* __restrict__ H, ColPtr zp, const double* __restrict__ tau, do
   __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
   const int r0 = blockIdx.x * TILE;
   const int rows = min(TILE, n - r0);
+  __shared__ float s_back;
+  if (threadIdx.x == 0) {  // once per block: a float64 division is slow on GB300
+    const double tv = *tau;
+    s_back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+  }
   tile_copy<HT, false>(stile, const_cast<HT*>(H), r0, rows);
   __syncthreads();
   if (threadIdx.x < rows) {
     float o[16];
     unstage_row<HT>(stile, threadIdx.x, o);
-    const double tv = *tau;
-    const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
     float* z = static_cast<float*>(colptr(zp));
-    z[r0 + threadIdx.x] = decode_row(o, dw) * back;
+    z[r0 + threadIdx.x] = decode_row(o, dw) * s_back;
   }
 }
 
@@ -625,8 +640,13 @@ __device__ __forceinline__ void row_layer_q(const RowSmem<LPR>& sm, int er, int 
   }
 }
 
+// Resident blocks per SM the short-row kernels are compiled for.  Capping the registers
+// for more resident blocks (six per SM at four lanes per row: 40 registers instead of 48)
+// measured slower.
+template <int LPR> struct RowBounds { static constexpr int MIN_BLOCKS = 1; };
+
 template <class HT, int FORM, int LPR, int DB>
-__global__ void __launch_bounds__(TILE)
+__global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
 k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
             const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
             const __grid_constant__ LayerW lw) {
@@ -650,7 +670,7 @@ k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float
 }
 
 template <class HT, int FORM, int LPR, int DB>
-__global__ void __launch_bounds__(TILE)
+__global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
 k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
                 const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
                 const int* __restrict__ ctl, const __grid_constant__ LayerW lw, const __grid_constant__ DecW dw) {
@@ -665,6 +685,11 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
   row_prefetch<DB>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
   pdl_wait();
   if (ctl && !ctl[1]) return;
+  __shared__ float s_back;
+  if (t == 0) {  // once per block: a float64 division is slow on GB300
+    const double tv = *tau;
+    s_back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
+  }
   row_gather<HT, LPR, DB>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
   __syncthreads();
   const int er = t % RB, q = t / RB;
@@ -674,13 +699,18 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
   __syncthreads();  // every thread is done with h and agg
   if (valid) {
 #pragma unroll
-    for (int k = 0; k < PW; ++k) sm.agg[er * RSTR + q * PW + k] = o[k];
+    for (int k = 0; k < PW / 4; ++k)
+      reinterpret_cast<float4*>(sm.agg + er * RSTR + q * PW)[k] =
+          make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
   }
   __syncthreads();
   if (valid) {
     float full[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) full[k] = sm.agg[er * RSTR + k];
+    for (int k = 0; k < 4; ++k) {
+      const float4 f4 = reinterpret_cast<const float4*>(sm.agg + er * RSTR)[k];
+      full[4 * k] = f4.x; full[4 * k + 1] = f4.y; full[4 * k + 2] = f4.z; full[4 * k + 3] = f4.w;
+    }
     float part;
     if constexpr (LPR == 2) {
       part = q == 0 ? decode_part<0, 16>(full, dw) : decode_part<16, 16>(full, dw);
@@ -693,12 +723,10 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
   }
   __syncthreads();
   if (q == 0 && valid) {
-    const double tv = *tau;
-    const float back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
     float zz = dw.b2;
 #pragma unroll
     for (int k = 0; k < LPR; ++k) zz += sm.zpart[k][er];
-    static_cast<float*>(colptr(zp))[r0 + er] = zz * back;
+    static_cast<float*>(colptr(zp))[r0 + er] = zz * s_back;
   }
 }
 
@@ -900,14 +928,14 @@ static int launch_layers_row(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trac
 }
 
 // Short-row kernels when every row has at most ROW_DMAX nonzeros (GNP_GCONV_ROWK=0 in the
-// environment forces the tile kernels; GNP_ROW_LPR=2|4 and GNP_ROW_DB=4|8 set the lanes per
-// row and the neighbour loads in flight, for tuning).
+// environment forces the tile kernels; GNP_ROW_LPR=2|4 sets the lanes per row, for
+// tuning).  Four neighbour loads in flight per lane: eight measured slower at both widths
+// (more registers, fewer resident blocks).
 static int row_kernel_mode(const gnp_mat* A) {
   static const int on = env_int("GNP_GCONV_ROWK", 1);
   if (!on || A->max_deg > ROW_DMAX) return 0;
   static const int lpr = env_int("GNP_ROW_LPR", 4);
-  static const int db = env_int("GNP_ROW_DB", 4);
-  return (lpr == 4 ? 4 : 2) * 10 + (db == 8 ? 8 : 4);
+  return lpr == 2 ? 2 : 4;
 }
 
 template <class HT, int FORM>
@@ -930,10 +958,8 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, (long long)n * 16);
   switch (row_kernel_mode(A)) {
-    case 24: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
-    case 28: GNP_TRY((launch_layers_row<HT, FORM, 2, 8>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
-    case 44: GNP_TRY((launch_layers_row<HT, FORM, 4, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
-    case 48: GNP_TRY((launch_layers_row<HT, FORM, 4, 8>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 2: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 4: GNP_TRY((launch_layers_row<HT, FORM, 4, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
     default:
       if (gconv_rows<HT>() == 128)
         GNP_TRY((launch_layers<HT, FORM, 128>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));

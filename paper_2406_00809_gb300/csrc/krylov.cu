@@ -190,7 +190,7 @@ k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double
   using TR = TrSpmv<XT>;
   __shared__ TileSmem<TR> sm;
   __shared__ double sacc[GNP_MAX_RESTART + 2];
-  __shared__ double sred[KC * RSTRIDE];
+  __shared__ double sred[RED_SH];
   const int j = st->j;
   const int K = j + 2;  // h1[0..j] and ||w||^2
   const size_t ld = (size_t)n;
@@ -249,7 +249,7 @@ k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const do
                ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
                double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
   if (!st->active) return;
-  __shared__ double sred[KC * RSTRIDE];
+  __shared__ double sred[RED_SH];
   __shared__ double shtot[GNP_MAX_RESTART + 2];
   const int j = st->j;
   const int K = j + 2;  // h1[0..j] and ||w||^2
@@ -260,26 +260,25 @@ k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const do
   for (int i = gtid; i < n; i += gstride) {
     const int rs = __ldg(rp + i), re = __ldg(rp + i + 1);
     double s = 0.0;
-    for (int e = rs; e < re; ++e) s = fma(__ldg(val + e), (double)x[__ldg(col + e)], s);
+    for (int e0 = rs; e0 < re; e0 += 8) {  // eight nonzeros' loads in flight, added in order
+      int c[8];
+      double v[8];
+      XT xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = e0 + u < re;
+        c[u] = ok ? __ldg(col + e0 + u) : 0;
+        v[u] = ok ? __ldg(val + e0 + u) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = (e0 + u < re) ? x[c[u]] : XT(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u < re) s = fma(v[u], (double)xv[u], s);
+    }
     w[i] = s;
   }
-  for (int k0 = 0; k0 < K; k0 += KC) {
-    double acc[KC];
-#pragma unroll
-    for (int kc = 0; kc < KC; ++kc) acc[kc] = 0.0;
-    for (int i = gtid; i < n; i += gstride) {
-      const double y = w[i];
-#pragma unroll
-      for (int kc = 0; kc < KC; ++kc) {
-        const int k = k0 + kc;
-        if (k < K) {
-          const double vk = (k == j + 1) ? y : V[k * ld + i];
-          acc[kc] += vk * y;
-        }
-      }
-    }
-    block_reduce_kc<false>(acc, sred, partials + (size_t)blockIdx.x * K + k0, min(KC, K - k0));
-  }
+  block_dots(V, w, n, K, j + 1, sred, partials + (size_t)blockIdx.x * K);
   if (!last_block_arrive(counter)) return;
   reduce_partials(partials, gridDim.x, K, shtot);
   if (threadIdx.x == 0) {
@@ -361,9 +360,12 @@ k_bnorm(const double* __restrict__ b, int n, DevState* st, double* __restrict__ 
 __global__ void __launch_bounds__(RED_THREADS)
 k_vscale(double* __restrict__ V, int n, const DevState* st) {
   if (!st->active) return;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) s_inv = 1.0 / st->vscale;  // once per block: float64 division is slow
+  __syncthreads();
   double* v = V + (size_t)st->j * n;
-  const double s = st->vscale;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = v[i] / s;
+  const double inv = s_inv;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = v[i] * inv;
 }
 
 // ---------------------------------------------------------------- CGS2 passes
@@ -378,7 +380,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   constexpr bool NORM = PASS == 1 || PASS == 4;  // the dots also give ||w||^2 (entry j+1)
   __shared__ double shh[GNP_MAX_RESTART + 2];
   __shared__ double shred[KC][32];  // KC*32 = 256 >= GNP_MAX_RESTART: reused for sines
-  __shared__ double sred[PASS == 3 ? 1 : KC * RSTRIDE];
+  __shared__ double sred[PASS == 3 ? 1 : RED_SH];
   __shared__ double shtot[GNP_MAX_RESTART + 4];
   __shared__ double sx[PASS == 4 ? 2 * (GNP_MAX_RESTART + 4) : 1];
   const int j = st->j;
@@ -413,23 +415,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
       }
     }
     const int K = NORM ? j + 2 : j + 1;  // passes 1 and 4 also ||w||^2 as entry j+1
-    for (int k0 = 0; k0 < K; k0 += KC) {
-      double acc[KC];
-#pragma unroll
-      for (int kc = 0; kc < KC; ++kc) acc[kc] = 0.0;
-      for (int i = gtid; i < n; i += gstride) {
-        const double y = w[i];
-#pragma unroll
-        for (int kc = 0; kc < KC; ++kc) {
-          const int k = k0 + kc;
-          if (k < K) {
-            const double vk = (NORM && k == j + 1) ? y : V[k * ld + i];
-            acc[kc] += vk * y;
-          }
-        }
-      }
-      block_reduce_kc<false>(acc, sred, partials + (size_t)blockIdx.x * K + k0, min(KC, K - k0));
-    }
+    block_dots(V, w, n, K, NORM ? j + 1 : -1, sred, partials + (size_t)blockIdx.x * K);
   }
   if (!last_block_arrive(counter)) return;
   const int K = NORM ? j + 2 : (PASS == 2 ? j + 1 : 1);
@@ -493,23 +479,24 @@ k_vnext(double* __restrict__ V, int n, const double* __restrict__ w, DevState* s
   __shared__ double ssn[GNP_MAX_RESTART + 4];
   const int j = st->jv;
   if (blockIdx.x == 0) {
-    __shared__ double sh2[GNP_MAX_RESTART + 4];
+    __shared__ double sxs[GNP_MAX_RESTART + 4];
+    __shared__ double sbs[GNP_MAX_RESTART + 4];
+    __shared__ double shn;
     if (!st->active) return;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-      const double b2 = h2[i];
-      shh[i] = h1[i] + b2;
-      sh2[i] = b2;
-    }
+    const double w1sq = st->w1sq;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) shh[i] = h1[i] + h2[i];
     for (int i = threadIdx.x; i < j; i += blockDim.x) {
       scs[i] = cs[i];
       ssn[i] = sn[i];
     }
+    if (threadIdx.x < 32) {  // ||h2||^2: warp 0, lane-strided, then a fixed shuffle tree
+      double q = 0.0;
+      for (int i = threadIdx.x; i <= j; i += 32) q = fma(h2[i], h2[i], q);
+      q = warp_sum(q);
+      if (threadIdx.x == 0) shn = sqrt(fmax(w1sq - q, 0.0));
+    }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double s2 = 0.0;
-    for (int i = 0; i <= j; ++i) s2 += sh2[i] * sh2[i];
-    const double hn = sqrt(fmax(st->w1sq - s2, 0.0));
-    arnoldi_step_finish(st, j, shh, hn, scs, ssn, H, R, cs, sn, g, hist, thist);
+    arnoldi_step_finish_block(st, j, shh, shn, scs, ssn, sxs, sbs, H, R, cs, sn, g, hist, thist);
     return;
   }
   if (!st->active) return;

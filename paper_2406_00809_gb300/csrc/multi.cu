@@ -120,7 +120,7 @@ __device__ __forceinline__ int mstep(const int* ctl) { return ctl[0]; }
 template <int K>
 __global__ void __launch_bounds__(RED_THREADS)
 k_mbnorm(const double* __restrict__ b, int n, DevState* st, double* __restrict__ partials, unsigned* counter) {
-  __shared__ double sred[KC * RSTRIDE];
+  __shared__ double sred[RED_SH];
   __shared__ double tot[K];
   if (blockIdx.x == 0 && threadIdx.x < K) st[threadIdx.x].t0 = global_ns();
   double a[KC];
@@ -322,7 +322,7 @@ k_mresidual(const int* __restrict__ rp, const int* __restrict__ col, const doubl
             double* __restrict__ partials, unsigned* counter) {
   using TR = TrSpmvM<K, double>;
   __shared__ TileSmem<TR, MROWS> sm;
-  __shared__ double sred[KC * RSTRIDE];
+  __shared__ double sred[RED_SH];
   __shared__ double tot[K];
   __shared__ int anyact;
   const int r0 = blockIdx.x * MROWS;
@@ -424,7 +424,7 @@ k_mcgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, int*
        unsigned long long* __restrict__ thist, MStrides ms, double* __restrict__ partials, unsigned* counter) {
   constexpr int CC = KC / K;  // columns per reduction
   if (!ctl[1]) return;
-  __shared__ double sred[KC * RSTRIDE];
+  __shared__ double sred[RED_SH];
   __shared__ double shh[(GNP_MAX_RESTART_MULTI + 2) * K];
   __shared__ double shtot[(GNP_MAX_RESTART_MULTI + 2) * K];
   __shared__ int anyact;

@@ -46,83 +46,133 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 constexpr double BREAKDOWN_REL = 1e-14;
 
-// Grid of the CGS2 kernels: one block per SM while the rows are few enough that L2
-// latency, not bandwidth, bounds the basis reads (each block then reduces once per
-// column chunk, and the float64 pipes of all SMs share the work evenly); up to four per
-// SM on larger systems for memory parallelism.  Never more than red_blocks(n), the
-// capacity of the partial-sum scratch.
+// Grid of the CGS2 kernels: about one row per thread, from one block per SM (small
+// systems) up to four per SM on larger ones.  The float64 pipes of all SMs share the
+// work evenly; a second block per SM hides part of the latency of the other's block
+// reduction (65,536 rows: 100.4 against 101.2 us per FGMRES step with one block per SM).
+// Never more than red_blocks(n), the capacity of the partial-sum scratch.
 // GNP_DOT_BLOCKS_PER_SM=1..4 in the environment forces the blocks per SM (for tuning).
 inline int dot_blocks(int n) {
   static const char* e = getenv("GNP_DOT_BLOCKS_PER_SM");
   static const int forced = e ? atoi(e) : 0;
-  const int per = (n + NUM_SMS_GB300 * RED_THREADS * 2 - 1) / (NUM_SMS_GB300 * RED_THREADS * 2);
+  const int per = (n + NUM_SMS_GB300 * RED_THREADS - 1) / (NUM_SMS_GB300 * RED_THREADS);
   const int bps = (forced >= 1 && forced <= 4) ? forced : std::max(1, std::min(4, per));
   return std::min(red_blocks(n), NUM_SMS_GB300 * bps);
 }
 
 constexpr int KC = 8;  // basis columns per register chunk
-constexpr int RSTRIDE = RED_THREADS + 8;  // row stride of the reduction transpose (doubles)
-static_assert(RED_THREADS == TILE && RED_THREADS / 32 == KC, "one warp per chunk column");
+constexpr int RED_SH = 32 * (RED_THREADS / 32);  // shared doubles of block_reduce_w
+static_assert(KC == 8 && RED_THREADS == TILE && RED_THREADS % 32 == 0, "block_reduce_kc: 8 columns, whole warps");
 
-// Block-wide sums of KC values per thread (256 threads): the values are transposed
-// through shared memory (sh: KC * RSTRIDE doubles) so that warp w adds column w's 256
-// values with 8 sequential adds per lane and one 5-level shuffle tree, instead of one
-// tree per value per warp.  GB300 executes float64 adds at 2 per SM per cycle, so
-// the number of tree levels, not the memory traffic, decides these kernels' cost.
-// ACC: dst[w] += sum (shared accumulators); else dst[w] = sum.  Fixed order.
-template <bool ACC>
-__device__ __forceinline__ void block_reduce_kc(const double (&a)[KC], double* sh, double* dst, int kvalid) {
+// Block-wide sums of KW = 8, 16 or 32 values per thread (RED_THREADS threads), in a
+// fixed order.  GB300 executes float64 adds at 2 per SM per cycle, so the number of
+// warp-wide float64 instructions decides the cost.  Each warp first reduces its 32 lanes
+// with a transposing butterfly: at the xor-16 step a lane keeps half of its columns and
+// hands the other half to its partner, at xor 8 a quarter, and so on until one column is
+// left (KW - 1 adds in all), then the remaining xor steps finish the sum: every lane
+// holds the warp total of column (lane >> (5 - log2 KW)) & (KW - 1), for KW + 4 - log2 KW
+// adds where a tree per column would take 5 KW.  The warp totals of each column meet in
+// shared memory (sh: KW * RED_THREADS / 32 doubles) and are added in warp order.
+// ACC: dst[k] += sum (shared accumulators); else dst[k] = sum, for k < kvalid.
+template <int KW, bool ACC>
+__device__ __forceinline__ void block_reduce_w(const double (&a)[KW], double* sh, double* dst, int kvalid) {
+  static_assert(KW == 8 || KW == 16 || KW == 32, "8, 16 or 32 columns");
+  constexpr int LV = KW == 8 ? 3 : (KW == 16 ? 4 : 5);  // transposing steps
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  double v[KW];
 #pragma unroll
-  for (int kc = 0; kc < KC; ++kc) sh[kc * RSTRIDE + t] = a[kc];
+  for (int q = 0; q < KW; ++q) v[q] = a[q];
+#pragma unroll
+  for (int lv = 0; lv < LV; ++lv) {
+    const int m = 16 >> lv;
+    const int h = KW >> (lv + 1);
+    const bool hi = (lane & m) != 0;
+#pragma unroll
+    for (int q = 0; q < h; ++q) {
+      const double keep = hi ? v[h + q] : v[q];
+      const double send = hi ? v[q] : v[h + q];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  double x = v[0];
+#pragma unroll
+  for (int m = 16 >> LV; m >= 1; m >>= 1) x += __shfl_xor_sync(0xffffffffu, x, m);
+  if ((lane & ((1 << (5 - LV)) - 1)) == 0) sh[w * KW + ((lane >> (5 - LV)) & (KW - 1))] = x;
   __syncthreads();
-  if (w < kvalid) {
+  if (t < kvalid) {
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < RED_THREADS / 32; ++i) s += sh[w * RSTRIDE + lane + 32 * i];
-    s = warp_sum(s);
-    if (lane == 0) {
-      if (ACC) dst[w] += s;
-      else dst[w] = s;
-    }
+    for (int i = 0; i < RED_THREADS / 32; ++i) s += sh[i * KW + t];
+    if (ACC) dst[t] += s;
+    else dst[t] = s;
   }
   __syncthreads();
 }
 
+template <bool ACC>
+__device__ __forceinline__ void block_reduce_kc(const double (&a)[KC], double* sh, double* dst, int kvalid) {
+  block_reduce_w<KC, ACC>(a, sh, dst, kvalid);
+}
 
-// One thread finishes Arnoldi step j of its system (Sec. 2.1, Algorithm 1): col[0..j]
-// holds h_{0..j,j} (it is rotated in place, col needs j+2 entries), hn = h_{j+1,j};
-// scs/ssn are the previous rotations.  Stores column j of H_bar, applies the previous
-// Givens rotations and the new one (rho = hypot(a, b), c = a/rho, s = b/rho; rho = 0
-// gives c = 1, s = 0), updates g and the residual estimate |g_{j+1}| (Sec. 4), records
-// the iteration's residual and device time, and decides whether the cycle continues.
-__device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double* col, double hn,
-                                                    const double* scs, const double* ssn, double* H,
+// Per-block partial sums of the dots  sum_i V[k][i] y_i  for k < K over the rows
+// i = blockIdx.x * blockDim.x + threadIdx.x + c * gridDim.x * blockDim.x (y = w; column
+// `normk`, if any, is y itself, giving ||y||^2) -> part[k], KW columns per pass: one
+// pass for up to 32 columns, so that the basis loads of a row are in flight together and
+// the block reduces once.
+template <int KW>
+__device__ __forceinline__ void block_dots_w(const double* __restrict__ V, const double* __restrict__ w, int n,
+                                             int K, int normk, double* sh, double* part) {
+  const size_t ld = (size_t)n;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstride = gridDim.x * blockDim.x;
+  for (int k0 = 0; k0 < K; k0 += KW) {
+    double acc[KW];
+#pragma unroll
+    for (int kc = 0; kc < KW; ++kc) acc[kc] = 0.0;
+    for (int i = gtid; i < n; i += gstride) {
+      const double y = w[i];
+#pragma unroll
+      for (int kc = 0; kc < KW; ++kc) {
+        const int k = k0 + kc;
+        if (k < K) {
+          const double vk = (k == normk) ? y : V[k * ld + i];
+          acc[kc] += vk * y;
+        }
+      }
+    }
+    block_reduce_w<KW, false>(acc, sh, part + k0, min(KW, K - k0));
+  }
+}
+
+__device__ __forceinline__ void block_dots(const double* __restrict__ V, const double* __restrict__ w, int n,
+                                           int K, int normk, double* sh, double* part) {
+  if (K <= 8) block_dots_w<8>(V, w, n, K, normk, sh, part);
+  else if (K <= 16) block_dots_w<16>(V, w, n, K, normk, sh, part);
+  else block_dots_w<32>(V, w, n, K, normk, sh, part);
+}
+
+
+// The new Givens rotation of Arnoldi step j and what follows it (one thread): a = the
+// rotated entry j of column j, b = h_{j+1,j} = hn; `finite` = every other rotated entry
+// of the column is finite.  rho = hypot(a, b), c = a/rho, s = b/rho (rho = 0 gives c = 1,
+// s = 0); R[j, j] = rho (entries above j are already stored), g and the residual
+// estimate |g_{j+1}| (Sec. 4), the iteration's residual and device time, and whether the
+// cycle continues.  The state and g_j come in with one batch of loads and go back at the
+// end, so that no store to R, g or the histories forces a reload of a state field.
+__device__ __forceinline__ void arnoldi_step_decide(DevState* st, int j, double a, double hn, bool finite,
                                                     double* R, double* cs, double* sn, double* g,
                                                     double* hist, unsigned long long* thist) {
-  // one serial thread: the state and g_j come in with one batch of loads and go back at
-  // the end, so that no store to H or R forces a reload of a state field in between
   DevState s = *st;
   const double gj = g[j];
   const int m = s.m;
   const int ldh = m + 1;
   s.hn = hn;
-  bool finite = isfinite(hn);
-  for (int i = 0; i <= j; ++i) H[(size_t)j * ldh + i] = col[i];
-  col[j + 1] = hn;
-  H[(size_t)j * ldh + j + 1] = hn;
-  for (int i = 0; i < j; ++i) {
-    const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
-    col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
-    col[i] = t;
-  }
-  for (int i = 0; i <= j + 1; ++i) finite = finite && isfinite(col[i]);
-  const double a = col[j], b = col[j + 1];
-  const double rho = hypot(a, b);
+  finite = finite && isfinite(hn) && isfinite(a);
+  const double rho = hypot(a, hn);
   double c = 1.0, sv = 0.0;
   if (rho != 0.0) {
     c = a / rho;
-    sv = b / rho;
+    sv = hn / rho;
   }
   const int iters = s.iters + 1;
   s.iters = iters;
@@ -141,9 +191,8 @@ __device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double*
   } else {
     cs[j] = c;
     sn[j] = sv;
-    col[j] = rho;
-    col[j + 1] = 0.0;
-    for (int i = 0; i <= j + 1; ++i) R[(size_t)j * ldh + i] = col[i];
+    R[(size_t)j * ldh + j] = rho;
+    R[(size_t)j * ldh + j + 1] = 0.0;
     g[j + 1] = -sv * gj;
     g[j] = c * gj;
     jj = j + 1;
@@ -165,6 +214,67 @@ __device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double*
     s.vscale = hn;
   }
   *st = s;
+}
+
+// One thread finishes Arnoldi step j of its system (Sec. 2.1, Algorithm 1): col[0..j]
+// holds h_{0..j,j} (it is rotated in place, col needs j+2 entries), hn = h_{j+1,j};
+// scs/ssn are the previous rotations.  Stores column j of H_bar, applies the previous
+// Givens rotations (entries above j go to R at once: column j of R is read only when the
+// step is kept) and then arnoldi_step_decide.
+__device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double* col, double hn,
+                                                    const double* scs, const double* ssn, double* H,
+                                                    double* R, double* cs, double* sn, double* g,
+                                                    double* hist, unsigned long long* thist) {
+  const int ldh = st->m + 1;
+  for (int i = 0; i <= j; ++i) H[(size_t)j * ldh + i] = col[i];
+  H[(size_t)j * ldh + j + 1] = hn;
+  bool finite = true;
+  for (int i = 0; i < j; ++i) {
+    const double t = scs[i] * col[i] + ssn[i] * col[i + 1];
+    col[i + 1] = -ssn[i] * col[i] + scs[i] * col[i + 1];
+    col[i] = t;
+    R[(size_t)j * ldh + i] = t;
+    finite = finite && isfinite(t);
+  }
+  arnoldi_step_decide(st, j, col[j], hn, finite, R, cs, sn, g, hist, thist);
+}
+
+// arnoldi_step_finish with the whole block (every thread calls it; col, scs, ssn, xs and
+// bs in shared memory, xs and bs with room for j+1 entries).  Applying the previous
+// rotations to column j is the recurrence x_{i+1} = -s_i x_i + c_i col_{i+1} (x_0 =
+// col_0; x_i is entry i after rotations 0..i-1), whose products c_i col_{i+1} do not
+// depend on it: the threads form those products, thread 0 runs the recurrence with one
+// fused multiply-add per step, then the threads form the rotated entries
+// c_i x_i + s_i col_{i+1} and store them; thread 0 decides.  On GB300 a dependent
+// float64 operation costs tens of cycles, so the serial chain is what this shortens.
+__device__ __forceinline__ void arnoldi_step_finish_block(DevState* st, int j, const double* col, double hn,
+                                                          const double* scs, const double* ssn, double* xs,
+                                                          double* bs, double* H, double* R, double* cs,
+                                                          double* sn, double* g, double* hist,
+                                                          unsigned long long* thist) {
+  const int t = threadIdx.x;
+  const int ldh = st->m + 1;
+  for (int i = t; i <= j; i += blockDim.x) H[(size_t)j * ldh + i] = col[i];
+  if (t == 0) H[(size_t)j * ldh + j + 1] = hn;
+  for (int i = t; i < j; i += blockDim.x) bs[i] = scs[i] * col[i + 1];
+  __syncthreads();
+  if (t == 0) {
+    double x = col[0];
+    xs[0] = x;
+    for (int i = 0; i < j; ++i) {
+      x = fma(-ssn[i], x, bs[i]);
+      xs[i + 1] = x;
+    }
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int i = t; i < j; i += blockDim.x) {
+    const double ti = fma(scs[i], xs[i], ssn[i] * col[i + 1]);
+    R[(size_t)j * ldh + i] = ti;
+    bad = bad || !isfinite(ti);
+  }
+  bad = __syncthreads_or(bad) != 0;
+  if (t == 0) arnoldi_step_decide(st, j, xs[j], hn, !bad, R, cs, sn, g, hist, thist);
 }
 
 
