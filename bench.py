@@ -317,10 +317,11 @@ def run_ours(args, wl):
             solve()
         btimes, binfos = timed_solves(args.steps)
         gnp.gnp_set_hprec(M, gnp.H_FP32)
-    # kernel launches inside the timed region: per cycle m steps of (encode, L Res-GCONV
-    # with the decoder in the last, SpMV + CGS2 pass 1, pass 2, next basis vector + Givens)
+    # kernel launches inside the timed region: per cycle m steps of (encode, which from
+    # step 1 on also forms the basis vector and finishes the previous step; L Res-GCONV
+    # with the decoder in the last; SpMV + CGS2 pass 1; pass 2) + the last step's finish
     # + x update + residual; per solve + norm and initial residual
-    per_cycle = m * (L + 4) + 2
+    per_cycle = m * (L + 3) + 3
     launches = sum(i.cycles * per_cycle + 2 for i in infos)
     line = {
         "metric": "GNP-FGMRES time-to-rtol 1e-8 (s)", "value": t_max, "unit": "s",

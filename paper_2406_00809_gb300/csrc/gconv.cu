@@ -19,7 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 
-#include "internal.h"
+#include "solver.h"
 
 namespace gnp {
 
@@ -103,6 +103,15 @@ k_vnorm(ColPtr vp, const double* __restrict__ vscale, const int* __restrict__ ct
       *counter = 0;
     }
   }
+}
+
+// d += a * b on two float32 lanes at once (fma.rn.f32x2: each lane an fmaf).
+__device__ __forceinline__ void ffma2(float& dx, float& dy, float ax, float ay, float bx, float by) {
+  asm("{\n\t.reg .b64 ta, tb, td;\n\t"
+      "mov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\tmov.b64 td, {%0, %1};\n\t"
+      "fma.rn.f32x2 td, ta, tb, td;\n\tmov.b64 {%0, %1}, td;\n\t}"
+      : "+f"(dx), "+f"(dy)
+      : "f"(ax), "f"(ay), "f"(bx), "f"(by));
 }
 
 // ---------------------------------------------------------------- tile staging
@@ -209,9 +218,66 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
     for (int c = 0; c < 16; ++c) h[c] = ew.b2[c];
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-      float a = fmaxf(fmaf(u, ew.W1[k], ew.b1[k]), 0.0f);
+      const float a = fmaxf(fmaf(u, ew.W1[k], ew.b1[k]), 0.0f);
 #pragma unroll
-      for (int c = 0; c < 16; ++c) h[c] = fmaf(a, ew.W2[k * 16 + c], h[c]);
+      for (int c = 0; c < 16; c += 2)  // two outputs per paired multiply-add, each an fmaf
+        ffma2(h[c], h[c + 1], a, a, ew.W2[k * 16 + c], ew.W2[k * 16 + c + 1]);
+    }
+    stage_row<HT>(stile, t, h);
+  }
+  __syncthreads();
+  tile_copy<HT, true>(stile, H, r0, rows);
+}
+
+// The encoder inside FGMRES from step 1 on (vn: the pending step j = st->jv): the last
+// block finishes step j (vnext_finish: Givens update, continue decision) while the others
+// form v_{j+1} = (w1 - V_j h2) / h_{j+1,j} for their rows in float64, store it as
+// V[:, j+1] and encode it as k_encode does with u = sqrt(n) v (unit-norm v, tau = 1;
+// noscale: u = v, tau = sqrt(n)).  The rows are formed even if the finish ends the cycle;
+// every later kernel of the step then sees active = 0 and returns.
+template <class HT>
+__global__ void __launch_bounds__(TILE)
+k_encode_vn(const VNext vn, int n, double sqrt_n, int noscale, double* __restrict__ tau, HT* __restrict__ H,
+            const __grid_constant__ EncW ew) {
+  if (blockIdx.x == gridDim.x - 1) {
+    vnext_finish(vn);
+    return;
+  }
+  const DevState* st = vn.st;
+  if (!st->active) return;
+  __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
+  __shared__ double shh[GNP_MAX_RESTART + 4];
+  __shared__ double shn, sinv;
+  const int j = st->jv;
+  const int t = threadIdx.x;
+  for (int k = t; k <= j; k += blockDim.x) shh[k] = vn.h2[k];
+  vnext_hnorm(vn.h2, j, st->w1sq, &shn);
+  if (t == 0) {
+    sinv = 1.0 / shn;  // once per block (thread 0 wrote shn): float64 division is slow
+    if (blockIdx.x == 0) *tau = noscale ? sqrt_n : 1.0;
+  }
+  __syncthreads();
+  const double inv = sinv;
+  const double f = noscale ? 1.0 : sqrt_n;
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  if (t < rows) {
+    const size_t ld = (size_t)n;
+    const int i = r0 + t;
+    double x = vn.w[i];
+#pragma unroll 8
+    for (int k = 0; k <= j; ++k) x -= vn.V[k * ld + i] * shh[k];
+    x = x * inv;
+    vn.V[(size_t)(j + 1) * ld + i] = x;
+    const float u = (float)(x * f);
+    float h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = ew.b2[c];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float a = fmaxf(fmaf(u, ew.W1[k], ew.b1[k]), 0.0f);
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) ffma2(h[c], h[c + 1], a, a, ew.W2[k * 16 + c], ew.W2[k * 16 + c + 1]);
     }
     stage_row<HT>(stile, t, h);
   }
@@ -472,7 +538,10 @@ k_decode(const HT* __restrict__ H, ColPtr zp, const double* __restrict__ tau, do
 //     order.  No slot bookkeeping, no carries: each row is one lane group's.
 //   epilogue: the parts of h_i and (A_hat H)_i meet in shared memory; thread t computes
 //     outputs [q*PW, q*PW+PW) of row t % RB with q = t / RB, which is the same for a whole
-//     warp, so U and W stay uniform constant-bank operands; it writes them straight out.
+//     warp, so the weights are uniform kernel-parameter loads; it writes them straight
+//     out.  Each output's 16- or 32-term sum runs on paired float32 multiply-adds
+//     (fma.rn.f32x2), the even inputs in one lane and the odd ones in the other, over a
+//     transposed copy of U and W (LayerWT): half the multiply-add instructions.
 //   decoder (last layer): the output parts meet in shared memory again and part q
 //     evaluates decoder units [q*32/LPR, (q+1)*32/LPR); the parts add in order.
 constexpr int ROW_DMAX = 16;
@@ -611,23 +680,58 @@ __device__ __forceinline__ void row_prefetch(const int* __restrict__ rp, const i
   }
 }
 
-// Outputs [Q*PW, Q*PW+PW) of epilogue row er (h and agg from shared memory).
-template <int FORM, int LPR, int Q>
-__device__ __forceinline__ void row_layer(const RowSmem<LPR>& sm, int er, const LayerW& lw,
-                                          float (&o)[16 / LPR]) {
-  float h[16], agg[16];
+// sum_c x_c M[c][k] for one output k, x from 16 shared floats, MT the transposed weights
+// (MT[k*16 + c]): the even and the odd inputs accumulate in the two lanes of a paired
+// multiply-add and meet at the end.
+__device__ __forceinline__ void dot16_pairs(const float* __restrict__ xrow, const float* mt, float& se, float& so) {
+  const float4* xp = reinterpret_cast<const float4*>(xrow);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const float4 a = reinterpret_cast<const float4*>(sm.h + er * RSTR)[q];
-    const float4 b = reinterpret_cast<const float4*>(sm.agg + er * RSTR)[q];
-    h[4 * q] = a.x; h[4 * q + 1] = a.y; h[4 * q + 2] = a.z; h[4 * q + 3] = a.w;
-    agg[4 * q] = b.x; agg[4 * q + 1] = b.y; agg[4 * q + 2] = b.z; agg[4 * q + 3] = b.w;
+  for (int c4 = 0; c4 < 4; ++c4) {
+    const float4 x = xp[c4];
+    ffma2(se, so, x.x, x.y, mt[4 * c4], mt[4 * c4 + 1]);
+    ffma2(se, so, x.z, x.w, mt[4 * c4 + 2], mt[4 * c4 + 3]);
   }
-  layer_part<FORM, Q * (16 / LPR), 16 / LPR>(h, agg, lw, o);
+}
+
+// Outputs [Q*PW, Q*PW+PW) of epilogue row er (h and agg from shared memory):
+// ReLU(h U + agg W) or h + ReLU(agg W), each output's sum split over even and odd inputs.
+template <int FORM, int LPR, int Q>
+__device__ __forceinline__ void row_layer(const RowSmem<LPR>& sm, int er, const LayerWT& lw,
+                                          float (&o)[16 / LPR]) {
+  constexpr int PW = 16 / LPR, K0 = Q * PW;
+  const float* ar = sm.agg + er * RSTR;
+  const float* hr = sm.h + er * RSTR;
+#pragma unroll
+  for (int k = 0; k < PW; ++k) {
+    float se = 0.0f, so = 0.0f;
+    dot16_pairs(ar, lw.WT + (K0 + k) * 16, se, so);
+    if (FORM == GNP_LAYER_PAPER) {
+      dot16_pairs(hr, lw.UT + (K0 + k) * 16, se, so);
+      o[k] = fmaxf(se + so, 0.0f);
+    } else {
+      o[k] = hr[K0 + k] + fmaxf(se + so, 0.0f);
+    }
+  }
+}
+
+// Decoder units [K0, K0+KU) of one row (o in shared memory): sum_k w2_k ReLU(b1_k + o D1[:, k]).
+template <int K0, int KU>
+__device__ __forceinline__ float decode_part_pairs(const float* orow, const DecWT& dw) {
+  float ze = 0.0f, zo = 0.0f;
+#pragma unroll
+  for (int k = K0; k < K0 + KU; k += 2) {
+    float ae = 0.0f, ao = 0.0f, be = 0.0f, bo = 0.0f;
+    dot16_pairs(orow, dw.DT1 + k * 16, ae, ao);
+    dot16_pairs(orow, dw.DT1 + (k + 1) * 16, be, bo);
+    const float a0 = fmaxf(dw.b1[k] + (ae + ao), 0.0f);
+    const float a1 = fmaxf(dw.b1[k + 1] + (be + bo), 0.0f);
+    ffma2(ze, zo, a0, a1, dw.W2[k], dw.W2[k + 1]);
+  }
+  return ze + zo;
 }
 
 template <int FORM, int LPR>
-__device__ __forceinline__ void row_layer_q(const RowSmem<LPR>& sm, int er, int q, const LayerW& lw,
+__device__ __forceinline__ void row_layer_q(const RowSmem<LPR>& sm, int er, int q, const LayerWT& lw,
                                             float (&o)[16 / LPR]) {
   if constexpr (LPR == 2) {
     if (q == 0) row_layer<FORM, 2, 0>(sm, er, lw, o);
@@ -649,7 +753,7 @@ template <class HT, int FORM, int LPR, int DB>
 __global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
 k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
             const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
-            const __grid_constant__ LayerW lw) {
+            const __grid_constant__ LayerWT lw) {
   constexpr int RB = TILE / LPR;
   __shared__ RowSmem<LPR> sm;
   const int t = threadIdx.x;
@@ -673,7 +777,7 @@ template <class HT, int FORM, int LPR, int DB>
 __global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
 k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
                 const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
-                const int* __restrict__ ctl, const __grid_constant__ LayerW lw, const __grid_constant__ DecW dw) {
+                const int* __restrict__ ctl, const __grid_constant__ LayerWT lw, const __grid_constant__ DecWT dw) {
   constexpr int RB = TILE / LPR;
   constexpr int PW = 16 / LPR;
   __shared__ RowSmem<LPR> sm;
@@ -705,19 +809,14 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
   }
   __syncthreads();
   if (valid) {
-    float full[16];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float4 f4 = reinterpret_cast<const float4*>(sm.agg + er * RSTR)[k];
-      full[4 * k] = f4.x; full[4 * k + 1] = f4.y; full[4 * k + 2] = f4.z; full[4 * k + 3] = f4.w;
-    }
+    const float* orow = sm.agg + er * RSTR;
     float part;
     if constexpr (LPR == 2) {
-      part = q == 0 ? decode_part<0, 16>(full, dw) : decode_part<16, 16>(full, dw);
+      part = q == 0 ? decode_part_pairs<0, 16>(orow, dw) : decode_part_pairs<16, 16>(orow, dw);
     } else {
-      part = q == 0 ? decode_part<0, 8>(full, dw)
-                    : q == 1 ? decode_part<8, 8>(full, dw) : q == 2 ? decode_part<16, 8>(full, dw)
-                                                                     : decode_part<24, 8>(full, dw);
+      part = q == 0 ? decode_part_pairs<0, 8>(orow, dw)
+                    : q == 1 ? decode_part_pairs<8, 8>(orow, dw)
+                             : q == 2 ? decode_part_pairs<16, 8>(orow, dw) : decode_part_pairs<24, 8>(orow, dw);
     }
     sm.zpart[q][er] = part;
   }
@@ -748,6 +847,24 @@ void fill_enc_dec(const std::vector<float>& w, int L, EncW& ew, DecW& dw) {
   memcpy(ew.b2, w.data() + ENC_B2, sizeof(ew.b2));
   const float* d = w.data() + dec_off(L);
   memcpy(dw.W1, d, sizeof(dw.W1));
+  memcpy(dw.b1, d + 512, sizeof(dw.b1));
+  memcpy(dw.W2, d + 544, sizeof(dw.W2));
+  dw.b2 = d[576];
+}
+
+void fill_layer_wt(const std::vector<float>& w, int l, LayerWT& lw) {
+  const float* p = w.data() + layer_off(l);
+  for (int c = 0; c < 16; ++c)
+    for (int k = 0; k < 16; ++k) {
+      lw.UT[k * 16 + c] = p[c * 16 + k];
+      lw.WT[k * 16 + c] = p[256 + c * 16 + k];
+    }
+}
+
+void fill_dec_wt(const std::vector<float>& w, int L, DecWT& dw) {
+  const float* d = w.data() + dec_off(L);
+  for (int c = 0; c < 16; ++c)
+    for (int k = 0; k < 32; ++k) dw.DT1[k * 16 + c] = d[c * 32 + k];
   memcpy(dw.b1, d + 512, sizeof(dw.b1));
   memcpy(dw.W2, d + 544, sizeof(dw.W2));
   dw.b2 = d[576];
@@ -903,8 +1020,8 @@ static int launch_layers_row(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trac
   const long long hcount = (long long)n * 16;
   const int fused_last = (L > 0 && !trace) ? 1 : 0;
   for (int l = 0; l < L - fused_last; ++l) {
-    LayerW lw;
-    fill_layer_w(M->w_host, l, lw);
+    LayerWT lw;
+    fill_layer_wt(M->w_host, l, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
     GNP_TRY_CUDA(launch_pdl(k_gconv_row<HT, FORM, LPR, DB>, nb, 0, st, A->rp, A->col, (const float*)M->valhat,
                             (const HT*)H0, H1, n, ctl, lw));
@@ -914,12 +1031,14 @@ static int launch_layers_row(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trac
     std::swap(H0, H1);
   }
   if (fused_last) {
-    LayerW lw;
-    fill_layer_w(M->w_host, L - 1, lw);
+    LayerWT lw;
+    fill_layer_wt(M->w_host, L - 1, lw);
+    DecWT dwt;
+    fill_dec_wt(M->w_host, L, dwt);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
     GNP_TRY_CUDA(launch_pdl(k_gconv_row_dec<HT, FORM, LPR, DB>, nb, 0, st, A->rp, A->col,
                             (const float*)M->valhat, (const HT*)H0, z, (const double*)W.tau, sqrt_n, n, ctl, lw,
-                            dw));
+                            dwt));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
     k_decode<HT><<<(n + TILE - 1) / TILE, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
@@ -940,7 +1059,7 @@ static int row_kernel_mode(const gnp_mat* A) {
 
 template <class HT, int FORM>
 static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W) {
+                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const VNext* vn) {
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
   const double sqrt_n = std::sqrt((double)n);
@@ -948,14 +1067,15 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   const int nt = (n + TILE - 1) / TILE;
   const int nb = red_blocks(n);
   const int noscale = M->cfg.no_scale ? 1 : 0;
-  if (!vscale && !noscale)
+  if (!vscale && !noscale && !vn)
     k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
   EncW ew;
   DecW dw;
   fill_enc_dec(M->w_host, L, ew, dw);
   HT* H0 = static_cast<HT*>(W.H[0]);
   HT* H1 = static_cast<HT*>(W.H[1]);
-  k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
+  if (vn) k_encode_vn<HT><<<nt + 1, TILE, 0, st>>>(*vn, n, sqrt_n, noscale, W.tau, H0, ew);
+  else k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, (long long)n * 16);
   switch (row_kernel_mode(A)) {
     case 2: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
@@ -970,17 +1090,17 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
 }
 
 int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                 const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs* ws) {
+                 const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs* ws, const VNext* vn) {
   GNP_TRY(model_sync_host(M));
   const ApplyWs& W = ws ? *ws : M->ws;
   const int form = M->cfg.form;
   if (M->hprec == GNP_H_BF16) {
     return form == GNP_LAYER_PAPER
-               ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W)
-               : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W);
+               ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W, vn)
+               : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W, vn);
   }
-  return form == GNP_LAYER_PAPER ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W)
-                                 : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W);
+  return form == GNP_LAYER_PAPER ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W, vn)
+                                 : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W, vn);
 }
 
 int apply_ws_alloc(ApplyWs& ws, int n) {

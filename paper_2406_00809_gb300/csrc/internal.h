@@ -18,9 +18,14 @@ inline int weight_count(int L) { return ENC_COUNT + L * LAYER_COUNT + DEC_COUNT;
 
 // Kernel-parameter copies of the weights: passed by value (__grid_constant__), so the
 // epilogues read them as uniform constant-bank operands.
-struct EncW { float W1[32]; float b1[32]; float W2[512]; float b2[16]; };
-struct LayerW { float U[256]; float W[256]; };
-struct DecW { float W1[512]; float b1[32]; float W2[32]; float b2; };
+struct __align__(16) EncW { float W1[32]; float b1[32]; float W2[512]; float b2[16]; };
+struct __align__(16) LayerW { float U[256]; float W[256]; };
+struct __align__(16) DecW { float W1[512]; float b1[32]; float W2[32]; float b2; };
+// Transposed copies for the short-row kernels' paired (f32x2) products: WT[k*16 + c] =
+// W[c*16 + k] (and UT from U), DT1[k*16 + c] = decoder W1[c*32 + k], so that the weights of
+// two consecutive inputs c, c+1 of one output k sit side by side.
+struct __align__(16) LayerWT { float WT[256]; float UT[256]; };
+struct __align__(16) DecWT { float DT1[512]; float b1[32]; float W2[32]; float b2; };
 
 // Indexed vector inside a basis: base + (*jptr + off) * stride (jptr may be null).
 struct ColPtr {
@@ -32,6 +37,25 @@ struct ColPtr {
 
 struct TrainState;  // train.cu
 struct Server;      // serve.cu
+struct DevState;    // solver.h
+
+// The FGMRES step whose basis vector the next GNP application forms itself (Algorithm 1):
+// after the CGS2 passes of step j = st->jv, v_{j+1} = (w1 - V_j h2) / h_{j+1,j} with
+// h_{j+1,j} = sqrt(||w1||^2 - ||h2||^2), and the step's Givens update still to do.
+struct VNext {
+  double* V;
+  const double* w;
+  const double* h1;
+  const double* h2;
+  DevState* st;
+  double* H;
+  double* R;
+  double* cs;
+  double* sn;
+  double* g;
+  double* hist;
+  unsigned long long* thist;
+};
 
 // Mutable scratch of one GNP application: hidden ping-pong blocks (n x 16 float32 each,
 // also used as bfloat16), the norm tau and the reduction scratch.  A model owns one;
@@ -77,13 +101,18 @@ namespace gnp {
 // z: float32 output column; trace: optional float32 [(L+1)*n*16].
 // ev (may be null): 2*L events; ev[2l] / ev[2l+1] are recorded on `st` just before /
 // after the launch of layer l's Res-GCONV kernel (the timing of the hot kernel).
+// vn (may be null): the encoder first forms the pending basis vector of that FGMRES step
+// (written to V[:, jv+1], normalised) and encodes it, while one extra block finishes the
+// step (v and vscale are then unused).
 int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
                  const int* ctl, cudaStream_t st, cudaEvent_t* ev = nullptr,
-                 const ApplyWs* ws = nullptr);
+                 const ApplyWs* ws = nullptr, const VNext* vn = nullptr);
 
 // Kernel-parameter copies of the encoder/decoder and of layer l's weights.
 void fill_enc_dec(const std::vector<float>& w, int L, EncW& ew, DecW& dw);
 void fill_layer_w(const std::vector<float>& w, int l, LayerW& lw);
+void fill_layer_wt(const std::vector<float>& w, int l, LayerWT& lw);
+void fill_dec_wt(const std::vector<float>& w, int L, DecWT& dw);
 
 // Make the host copy of the weights current (after training).
 int model_sync_host(gnp_model* M);

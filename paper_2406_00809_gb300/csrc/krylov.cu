@@ -3,8 +3,11 @@
 //
 // One Arnoldi step j (all on the device, no host round trip):
 //   [M]    z_j = M(v_j): the preconditioner's first kernel turns the stored w into
-//          v_j = w / h_{j,j-1} (or r / beta) in place (the GNP encoder, k_vscale for
-//          M = I, the Jacobi and inner-GMRES kernels), then writes Z[:, j].
+//          v_j = w / h_{j,j-1} (or r / beta) in place (k_vscale for M = I, the Jacobi and
+//          inner-GMRES kernels), then writes Z[:, j].  The GNP encoder does more from step
+//          1 on: it forms v_j = (w1 - V h2) / h_{j,j-1} itself from the previous step's
+//          CGS2 output, while one of its blocks finishes that step (k_encode_vn, gconv.cu),
+//          so k_vnext runs only after the cycle's last step.
 //   k_spmv_dot    w = A z_j (tile gather, float64 values) fused with CGS2 pass 1:
 //                 h1 = V_j^T w and ||w||^2 (the breakdown reference).
 //   k_cgs<4>      w1 = w - V_j h1 (in place), h2 = V_j^T w1 and ||w1||^2.
@@ -470,40 +473,21 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
 //     cycle (V has m+1 columns; an unused column is harmless); these blocks read only jv,
 //     which block 0 does not write.
 __global__ void __launch_bounds__(RED_THREADS)
-k_vnext(double* __restrict__ V, int n, const double* __restrict__ w, DevState* st, const double* __restrict__ h1,
-        const double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
-        double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
-        unsigned long long* __restrict__ thist) {
-  __shared__ double shh[GNP_MAX_RESTART + 4];
-  __shared__ double scs[GNP_MAX_RESTART + 4];
-  __shared__ double ssn[GNP_MAX_RESTART + 4];
-  const int j = st->jv;
+k_vnext(const VNext a, int n) {
   if (blockIdx.x == 0) {
-    __shared__ double sxs[GNP_MAX_RESTART + 4];
-    __shared__ double sbs[GNP_MAX_RESTART + 4];
-    __shared__ double shn;
-    if (!st->active) return;
-    const double w1sq = st->w1sq;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) shh[i] = h1[i] + h2[i];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-      scs[i] = cs[i];
-      ssn[i] = sn[i];
-    }
-    if (threadIdx.x < 32) {  // ||h2||^2: warp 0, lane-strided, then a fixed shuffle tree
-      double q = 0.0;
-      for (int i = threadIdx.x; i <= j; i += 32) q = fma(h2[i], h2[i], q);
-      q = warp_sum(q);
-      if (threadIdx.x == 0) shn = sqrt(fmax(w1sq - q, 0.0));
-    }
-    __syncthreads();
-    arnoldi_step_finish_block(st, j, shh, shn, scs, ssn, sxs, sbs, H, R, cs, sn, g, hist, thist);
+    vnext_finish(a);
     return;
   }
+  __shared__ double shh[GNP_MAX_RESTART + 4];
+  const DevState* st = a.st;
   if (!st->active) return;
+  const int j = st->jv;
   const size_t ld = (size_t)n;
-  for (int k = threadIdx.x; k <= j; k += blockDim.x) shh[k] = h2[k];
+  const double* __restrict__ V = a.V;
+  const double* __restrict__ w = a.w;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) shh[k] = a.h2[k];
   __syncthreads();
-  double* vout = V + (size_t)(j + 1) * ld;
+  double* vout = a.V + (size_t)(j + 1) * ld;
   for (int i = (blockIdx.x - 1) * blockDim.x + threadIdx.x; i < n; i += (gridDim.x - 1) * blockDim.x) {
     double x = w[i];
 #pragma unroll 8
@@ -572,6 +556,10 @@ int solver_ensure_zd(Solver* S, int m) {
   return GNP_OK;
 }
 
+static VNext vnext_args(Solver* S) {
+  return VNext{S->V, S->w, S->h1, S->h2, S->st, S->H, S->R, S->cs, S->sn, S->g, S->hist, S->thist};
+}
+
 // Row-per-thread SpMV for matrices without long rows (GNP_SPMV_ROWK=0 in the environment
 // forces the tile kernel, for tuning).
 static bool spmv_short_rows(const gnp_mat* A) {
@@ -610,7 +598,9 @@ int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, d
       gnp_model* M = P.M;
       ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
       cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
-      GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws));
+      // from step 1 on the encoder forms v_j itself (and a block of it finishes step j-1)
+      const VNext vn = vnext_args(S);
+      GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws, j > 0 ? &vn : nullptr));
       if (short_rows)
         k_spmv_dot_row<float><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, z, S->w, S->V, n, S->st,
                                                            S->h1, S->red.partials, S->red.counter);
@@ -630,8 +620,10 @@ int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, d
     }
     k_cgs<4><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
                                          S->g, S->hist, S->thist, S->red.partials, S->red.counter);
-    k_vnext<<<1 + nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn, S->g,
-                                            S->hist, S->thist);
+    if (P.kind != GNP_PRECOND_GNP)
+      k_vnext<<<1 + nb, RED_THREADS, 0, st>>>(vnext_args(S), n);
+    else if (j == m - 1)
+      k_vnext<<<1, RED_THREADS, 0, st>>>(vnext_args(S), n);  // the last step's finish only
   }
   const int xsm = (int)sizeof(double) * m * m;
   if (P.kind == GNP_PRECOND_GNP)
@@ -728,8 +720,7 @@ int inner_gmres_launch(gnp_mat* A, InnerGmres* G, ColPtr v, DevState* outer, Col
     spmv_dot_f64(A, vj, S, ndot, ncg, spmv_short_rows(A), st);
     k_cgs<4><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn,
                                          S->g, S->hist, S->thist, S->red.partials, S->red.counter);
-    k_vnext<<<1 + nb, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->h1, S->h2, S->H, S->R, S->cs, S->sn, S->g,
-                                            S->hist, S->thist);
+    k_vnext<<<1 + nb, RED_THREADS, 0, st>>>(vnext_args(S), n);
   }
   k_xupdate<double><<<nb, RED_THREADS, (int)sizeof(double) * k * k, st>>>(S->V, G->x, n, S->st, S->R, S->g);
   k_inner_end<<<nb, RED_THREADS, 0, st>>>(G->x, outer, z, n);

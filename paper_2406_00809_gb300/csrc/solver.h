@@ -278,6 +278,44 @@ __device__ __forceinline__ void arnoldi_step_finish_block(DevState* st, int j, c
 }
 
 
+// h_{j+1,j} = ||w1 - V h2|| = sqrt(||w1||^2 - ||h2||^2) of step j = st->jv after
+// k_cgs<4>: V has orthonormal columns to working precision and h2 = V^T w1; ||h2|| is
+// O(eps ||w||) after the first pass, so nothing cancels unless w1 itself is at the
+// breakdown level, where the step ends anyway.  Warp 0 of the calling block sums ||h2||^2
+// lane-strided with a fixed shuffle tree (the same bits in every block); the result is in
+// *out (shared) after the caller's next __syncthreads.
+__device__ __forceinline__ void vnext_hnorm(const double* __restrict__ h2, int j, double w1sq, double* out) {
+  if (threadIdx.x < 32) {
+    double q = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 32) q = fma(h2[i], h2[i], q);
+    q = warp_sum(q);
+    if (threadIdx.x == 0) *out = sqrt(fmax(w1sq - q, 0.0));
+  }
+}
+
+// Finish step j = st->jv with the whole block: column j of H_bar = h1 + h2 and h_{j+1,j},
+// the Givens update and the continue decision (arnoldi_step_finish_block).
+__device__ __forceinline__ void vnext_finish(const VNext& a) {
+  __shared__ double shh[GNP_MAX_RESTART + 4];
+  __shared__ double scs[GNP_MAX_RESTART + 4];
+  __shared__ double ssn[GNP_MAX_RESTART + 4];
+  __shared__ double sxs[GNP_MAX_RESTART + 4];
+  __shared__ double sbs[GNP_MAX_RESTART + 4];
+  __shared__ double shn;
+  DevState* st = a.st;
+  if (!st->active) return;
+  const int j = st->jv;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) shh[i] = a.h1[i] + a.h2[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    scs[i] = a.cs[i];
+    ssn[i] = a.sn[i];
+  }
+  vnext_hnorm(a.h2, j, st->w1sq, &shn);
+  __syncthreads();
+  arnoldi_step_finish_block(st, j, shh, shn, scs, ssn, sxs, sbs, a.H, a.R, a.cs, a.sn, a.g, a.hist, a.thist);
+}
+
+
 struct Solver {
   int n = 0, m_cap = 0, maxit_cap = -1;
   double* V = nullptr;   // [n*(m+1)] column-major basis

@@ -7,7 +7,7 @@ Runs `reps` solves of exactly `iters` Arnoldi steps (rtol = 0, so no early exit)
 randomly initialised GNP (Sec. 2.3: the per-step cost depends on the matrix, L, the
 restart length and the hidden-block precision, not on the trained weights) and prints
 one JSON line per solve with the CUDA-event time per step.  The launch sequence is fixed
-(per solve: 2 + cycles * (restart * (L + 4) + 2) kernels), which makes it the command to
+(per solve: 2 + cycles * (restart * (L + 3) + 3) kernels), which makes it the command to
 put under ncu for a per-kernel breakdown of a step.  Inputs are synthetic
 (paper_2406_00809_gb300.inputs).
 """
