@@ -1051,10 +1051,8 @@ static int launch_layers_row(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trac
 // tuning).  Four neighbour loads in flight per lane: eight measured slower at both widths
 // (more registers, fewer resident blocks).
 static int row_kernel_mode(const gnp_mat* A) {
-  static const int on = env_int("GNP_GCONV_ROWK", 1);
-  if (!on || A->max_deg > ROW_DMAX) return 0;
-  static const int lpr = env_int("GNP_ROW_LPR", 4);
-  return lpr == 2 ? 2 : 4;
+  if (!env_int("GNP_GCONV_ROWK", 1) || A->max_deg > ROW_DMAX) return 0;
+  return env_int("GNP_ROW_LPR", 4) == 2 ? 2 : 4;
 }
 
 template <class HT, int FORM>

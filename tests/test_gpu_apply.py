@@ -130,21 +130,32 @@ def test_apply_scale_equivariance_and_zero(gnp):
     assert torch.count_nonzero(z1).item() == 0
 
 
-@pytest.mark.parametrize("rows", ["128", "256"])
+VARIANTS = {  # Res-GCONV kernel variants, chosen through the library's tuning variables
+    "row4": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "4"},      # short-row kernel (the default)
+    "row2": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "2"},
+    "tile256": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_ROWS": "256"},  # nnz-balanced tiles
+    "tile128": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_ROWS": "128"},
+}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("name", ["convdiff45", "powerlaw12k", "aniso9"])
 @pytest.mark.parametrize("hprec", [0, 1])
 @pytest.mark.parametrize("form", [0, 1])
-def test_apply_both_tile_shapes(gnp, rows, name, hprec, form, monkeypatch):
-    """Both Res-GCONV tile shapes (256 rows with one epilogue thread per row, 128 rows
-    with two) against the oracle, including the decoder-fused last layer and the traced
-    per-layer hidden blocks; the two shapes agree with each other to float32 rounding."""
+def test_apply_all_layer_kernels(gnp, variant, name, hprec, form, monkeypatch):
+    """Every Res-GCONV kernel variant (the short-row kernel with four or two lanes per row,
+    the nnz-balanced tile kernel with 256- and 128-row tiles) against the oracle, including
+    the decoder-fused last layer and the traced per-layer hidden blocks; every variant
+    agrees with the default to float32 rounding.  Rows of more than 16 nonzeros
+    (powerlaw12k) always take the tile kernel."""
     import torch
     A = MATS[name]()
     L = 8
     blob = I.init_weights(L, seed=11)
     v = I.gaussian(A.n, seed=12)
     zr = G.forward(G.normalise(A.to_scipy()), v, G.unpack(blob, L), form)
-    monkeypatch.setenv("GNP_GCONV_ROWS", rows)
+    for k, val in VARIANTS[variant].items():
+        monkeypatch.setenv(k, val)
     z, M = run_apply(gnp, A, blob, L, form, hprec, v)
     assert rel(z, zr) <= (F32_TOL if hprec == 0 else BF16_TOL), rel(z, zr)
     if hprec == 0:
@@ -155,7 +166,7 @@ def test_apply_both_tile_shapes(gnp, rows, name, hprec, form, monkeypatch):
         hg = hid.cpu().numpy().reshape(L + 1, A.n, 16)
         for l in range(L + 1):
             assert rel(hg[l], Hs[l]) <= F32_TOL, l
-    other = "256" if rows == "128" else "128"
-    monkeypatch.setenv("GNP_GCONV_ROWS", other)
+    for k in ("GNP_GCONV_ROWK", "GNP_ROW_LPR", "GNP_GCONV_ROWS"):
+        monkeypatch.delenv(k, raising=False)
     z2, _ = run_apply(gnp, A, blob, L, form, hprec, v)
     assert rel(z2, z) <= (2e-6 if hprec == 0 else 1e-2)
