@@ -1047,12 +1047,16 @@ static int launch_layers_row(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trac
 }
 
 // Short-row kernels when every row has at most ROW_DMAX nonzeros (GNP_GCONV_ROWK=0 in the
-// environment forces the tile kernels; GNP_ROW_LPR=2|4 sets the lanes per row, for
-// tuning).  Four neighbour loads in flight per lane: eight measured slower at both widths
-// (more registers, fewer resident blocks).
+// environment forces the tile kernels; GNP_ROW_LPR=2|4 sets the lanes per row and
+// GNP_ROW_DB=4|5 the neighbour loads in flight, for tuning).  Five loads in flight cover a
+// 5-point stencil row in one round trip (56 registers, four blocks per SM): 93.2 -> 89.7 us
+// per FGMRES step at 65,536 rows against four (48 registers, five blocks); eight measured
+// slower (more registers, fewer resident blocks).  Rows of at most four take four.
 static int row_kernel_mode(const gnp_mat* A) {
   if (!env_int("GNP_GCONV_ROWK", 1) || A->max_deg > ROW_DMAX) return 0;
-  return env_int("GNP_ROW_LPR", 4) == 2 ? 2 : 4;
+  const int forced = env_int("GNP_ROW_DB", 0);
+  const int db = forced == 4 || forced == 5 ? forced : (A->max_deg <= 4 ? 4 : 5);
+  return (env_int("GNP_ROW_LPR", 4) == 2 ? 20 : 40) + db;
 }
 
 template <class HT, int FORM>
@@ -1076,8 +1080,10 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   else k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, (long long)n * 16);
   switch (row_kernel_mode(A)) {
-    case 2: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
-    case 4: GNP_TRY((launch_layers_row<HT, FORM, 4, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 24: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 25: GNP_TRY((launch_layers_row<HT, FORM, 2, 5>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 44: GNP_TRY((launch_layers_row<HT, FORM, 4, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
+    case 45: GNP_TRY((launch_layers_row<HT, FORM, 4, 5>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
     default:
       if (gconv_rows<HT>() == 128)
         GNP_TRY((launch_layers<HT, FORM, 128>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n)));

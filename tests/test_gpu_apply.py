@@ -132,7 +132,8 @@ def test_apply_scale_equivariance_and_zero(gnp):
 
 VARIANTS = {  # Res-GCONV kernel variants, chosen through the library's tuning variables
     "row4": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "4"},      # short-row kernel (the default)
-    "row2": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "2"},
+    "row4db4": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "4", "GNP_ROW_DB": "4"},
+    "row2": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "2", "GNP_ROW_DB": "5"},
     "tile256": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_ROWS": "256"},  # nnz-balanced tiles
     "tile128": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_ROWS": "128"},
 }
@@ -143,8 +144,9 @@ VARIANTS = {  # Res-GCONV kernel variants, chosen through the library's tuning v
 @pytest.mark.parametrize("hprec", [0, 1])
 @pytest.mark.parametrize("form", [0, 1])
 def test_apply_all_layer_kernels(gnp, variant, name, hprec, form, monkeypatch):
-    """Every Res-GCONV kernel variant (the short-row kernel with four or two lanes per row,
-    the nnz-balanced tile kernel with 256- and 128-row tiles) against the oracle, including
+    """Every Res-GCONV kernel variant (the short-row kernel with four or two lanes per row and
+    four or five neighbour loads in flight, the nnz-balanced tile kernel with 256- and 128-row
+    tiles) against the oracle, including
     the decoder-fused last layer and the traced per-layer hidden blocks; every variant
     agrees with the default to float32 rounding.  Rows of more than 16 nonzeros
     (powerlaw12k) always take the tile kernel."""
@@ -166,7 +168,7 @@ def test_apply_all_layer_kernels(gnp, variant, name, hprec, form, monkeypatch):
         hg = hid.cpu().numpy().reshape(L + 1, A.n, 16)
         for l in range(L + 1):
             assert rel(hg[l], Hs[l]) <= F32_TOL, l
-    for k in ("GNP_GCONV_ROWK", "GNP_ROW_LPR", "GNP_GCONV_ROWS"):
+    for k in ("GNP_GCONV_ROWK", "GNP_ROW_LPR", "GNP_ROW_DB", "GNP_GCONV_ROWS"):
         monkeypatch.delenv(k, raising=False)
     z2, _ = run_apply(gnp, A, blob, L, form, hprec, v)
     assert rel(z2, z) <= (2e-6 if hprec == 0 else 1e-2)
