@@ -191,13 +191,12 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
   // FGMRES step's v_j = w * (1 / h_{j,j-1})
   __shared__ double s_f, s_inv;
   if (t == 0) {
-    s_inv = 1.0;
+    s_inv = vscale ? 1.0 / *vscale : 1.0;  // v_j = w / h whether or not s is applied
     if (noscale) {
       s_f = 1.0;
       if (blockIdx.x == 0) *tau = sqrt_n;
     } else if (vscale) {
       s_f = sqrt_n;
-      s_inv = 1.0 / *vscale;
       if (blockIdx.x == 0) *tau = 1.0;
     } else {
       const double tv = *tau;
