@@ -175,3 +175,33 @@ def test_cgs2_keeps_orthogonality_under_cancellation():
     assert np.abs(V.T @ wo).max() <= 1e-12 * np.linalg.norm(wo)
     np.testing.assert_allclose(h, c, rtol=1e-12)
     assert abs(np.linalg.norm(wo) - 1e-9) <= 1e-6 * 1e-9
+
+
+def test_pythagorean_subdiagonal_equals_explicit_norm():
+    # The CUDA solver takes h_{j+1,j} = ||w1 - V h2|| as sqrt(||w1||^2 - ||h2||^2) with
+    # ||w1||^2 from its second-pass reduction.  Against the oracle's explicit norm of the
+    # CGS2 output, across cancellation levels down to 1e-10 ||w||, the two agree to a
+    # few units of rounding: V is orthonormal to working precision and ||h2|| is
+    # O(eps ||w||) after the first pass, so the subtraction cancels nothing.  A sign slip
+    # (adding ||h2||^2) or using ||w||^2 instead of ||w1||^2 fails at once.
+    rng = np.random.default_rng(29)
+    V, _ = np.linalg.qr(rng.standard_normal((500, 20)))
+    for delta in (1.0, 1e-3, 1e-6, 1e-8, 1e-10):
+        c = rng.standard_normal(20)
+        u = rng.standard_normal(500)
+        u -= V @ (V.T @ u)
+        u /= np.linalg.norm(u)
+        w = V @ c + delta * u
+        h1 = V.T @ w
+        w1 = w - V @ h1
+        h2 = V.T @ w1
+        explicit = np.linalg.norm(w1 - V @ h2)
+        _, wo = K.orthogonalise(V, w, "cgs2")
+        assert explicit == np.linalg.norm(wo)  # the oracle's CGS2 output, same operations
+        pyth = np.sqrt(max(w1 @ w1 - h2 @ h2, 0.0))
+        assert abs(pyth - explicit) <= 8 * np.finfo(float).eps * explicit, (delta, pyth, explicit)
+        wrong = np.sqrt(w1 @ w1 + h2 @ h2)
+        if delta <= 1e-10:  # ||h2|| is no longer negligible against ||w1|| there
+            assert abs(wrong - explicit) > 8 * np.finfo(float).eps * explicit
+        wrong_w = np.sqrt(max(w @ w - h2 @ h2, 0.0))
+        assert abs(wrong_w - explicit) > 1e-3 * explicit
