@@ -2,16 +2,20 @@
 // L Res-GCONV layers over A_hat = A/gamma (Eqs. 6-7), MLP decoder, back-scaling.
 //
 // Kernels (one launch each):
-//   k_vnorm    tau = ||v||_2 (deterministic two-level reduction); optionally first
-//              divides v in place by a device scalar (the FGMRES step normalises
-//              v_j = w / h_{j,j-1} in the same pass).
-//   k_encode   u_i = (sqrt(n)/tau) v_i; h_i = W2^T ReLU(W1^T u_i + b1) + b2 (1->32->16).
-//   k_gconv    one Res-GCONV layer: nnz-balanced CSR gather (A_hat H)_i over the n x 16
-//              hidden block with 16-byte loads, then per row (thread-per-row epilogue)
-//              ReLU(h_i U + (A_hat H)_i W)  or  h_i + ReLU((A_hat H)_i W), with U and W
-//              read as uniform constant-bank operands from the kernel parameters.
-//   k_gconv_dec the last layer with the decoder (16->32->1) and the back-scaling
-//              tau/sqrt(n) fused into the epilogue: writes z_i, never H^L.
+//   k_vnorm      tau = ||v||_2 (deterministic two-level reduction; standalone apply).
+//   k_encode     u_i = (sqrt(n)/tau) v_i; h_i = W2^T ReLU(W1^T u_i + b1) + b2 (1->32->16);
+//                inside FGMRES it first scales the stored vector to v_j = w / h_{j,j-1}.
+//   k_encode_vn  the encoder of FGMRES steps >= 1: forms v_j = (w1 - V h2) / h_{j,j-1}
+//                itself while one extra block finishes the previous step.
+//   k_gconv_row  one Res-GCONV layer for matrices whose rows have at most 16 nonzeros:
+//                four lanes per row gather every neighbour at once, then per row four
+//                threads compute ReLU(h_i U + (A_hat H)_i W) or h_i + ReLU((A_hat H)_i W)
+//                on paired float32 multiply-adds.
+//   k_gconv      one Res-GCONV layer for any row lengths: nnz-balanced CSR tile gather
+//                over the n x 16 hidden block with 16-byte loads, thread-per-row epilogue
+//                with U and W as uniform kernel-parameter operands.
+//   k_gconv_row_dec, k_gconv_dec  the last layer with the decoder (16->32->1) and the
+//                back-scaling tau/sqrt(n) fused into the epilogue: writes z_i, never H^L.
 // Hidden blocks are node-major (16 contiguous values per node), float32 or bfloat16.
 #include <algorithm>
 #include <cmath>
@@ -76,21 +80,15 @@ __device__ __forceinline__ void* colptr(const ColPtr& p) {
 
 // ---------------------------------------------------------------- k_vnorm
 
-template <bool SCALE>
 __global__ void __launch_bounds__(RED_THREADS)
-k_vnorm(ColPtr vp, const double* __restrict__ vscale, const int* __restrict__ ctl, int n,
-        double* __restrict__ partials, unsigned* __restrict__ counter, double* __restrict__ tau) {
+k_vnorm(ColPtr vp, const int* __restrict__ ctl, int n, double* __restrict__ partials,
+        unsigned* __restrict__ counter, double* __restrict__ tau) {
   if (ctl && !ctl[1]) return;
   __shared__ double sh[32];
-  double* v = static_cast<double*>(colptr(vp));
-  double s = SCALE ? *vscale : 1.0;
+  const double* v = static_cast<const double*>(colptr(vp));
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double x = v[i];
-    if (SCALE) {
-      x = x / s;
-      v[i] = x;
-    }
+    const double x = v[i];
     acc += x * x;
   }
   double t = block_sum(acc, sh);
@@ -1069,7 +1067,7 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   const int nb = red_blocks(n);
   const int noscale = M->cfg.no_scale ? 1 : 0;
   if (!vscale && !noscale && !vn)
-    k_vnorm<false><<<nb, RED_THREADS, 0, st>>>(v, nullptr, ctl, n, W.red.partials, W.red.counter, W.tau);
+    k_vnorm<<<nb, RED_THREADS, 0, st>>>(v, ctl, n, W.red.partials, W.red.counter, W.tau);
   EncW ew;
   DecW dw;
   fill_enc_dec(M->w_host, L, ew, dw);

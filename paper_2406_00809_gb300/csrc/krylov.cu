@@ -359,7 +359,8 @@ k_bnorm(const double* __restrict__ b, int n, DevState* st, double* __restrict__ 
   }
 }
 
-// v_j <- v_j / vscale (M = identity: the normalisation that k_vnorm does for the GNP).
+// v_j <- v_j / vscale (M = identity, Jacobi, inner GMRES: the normalisation that the GNP
+// encoder does in its own first pass).
 __global__ void __launch_bounds__(RED_THREADS)
 k_vscale(double* __restrict__ V, int n, const DevState* st) {
   if (!st->active) return;
