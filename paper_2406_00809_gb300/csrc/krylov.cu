@@ -498,30 +498,38 @@ k_vnext(const VNext a, int n) {
 }
 
 // y = R^{-1} g (back substitution, redundantly in every block), x += Z[:, :jj] y.
+// The substitution runs by columns: y_i = g_i / R_ii, then every lane removes y_i's part
+// from its own entries of g (g_k -= R_ki y_i, k < i).  Per step the serial chain is one
+// multiply and one fused multiply-add (the reciprocals of the diagonal are formed in
+// parallel first) instead of a five-level shuffle tree and a division: float64 operations
+// that depend on one another cost tens of cycles each on GB300.
 template <class ZT>
 __global__ void __launch_bounds__(RED_THREADS)
 k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevState* st,
           const double* __restrict__ R, const double* __restrict__ g) {
   __shared__ double y[GNP_MAX_RESTART];
   __shared__ double sg[GNP_MAX_RESTART];
+  __shared__ double rinv[GNP_MAX_RESTART];
   extern __shared__ double sR[];  // jj x jj upper triangle of R, column-major, ld = jj
   const int jj = st->jj;
   if (jj == 0) return;
   const int ldh = st->m + 1;
-  // stage R and g with all threads, then one warp back-substitutes from shared memory
+  // stage R, g and 1/R_ii with all threads, then one warp back-substitutes
   for (int t = threadIdx.x; t < jj * jj; t += blockDim.x) {
     const int c = t / jj, r = t % jj;
     sR[t] = (r <= c) ? R[(size_t)c * ldh + r] : 0.0;
   }
-  for (int t = threadIdx.x; t < jj; t += blockDim.x) sg[t] = g[t];
+  for (int t = threadIdx.x; t < jj; t += blockDim.x) {
+    sg[t] = g[t];
+    rinv[t] = 1.0 / R[(size_t)t * ldh + t];
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = jj - 1; i >= 0; --i) {
-      double part = 0.0;
-      for (int k = i + 1 + lane; k < jj; k += 32) part += sR[k * jj + i] * y[k];
-      part = warp_sum(part);
-      if (lane == 0) y[i] = (sg[i] - part) / sR[i * jj + i];
+      const double yi = sg[i] * rinv[i];  // sg[i] is final: its last update was in step i+1
+      if (lane == 0) y[i] = yi;
+      for (int k = lane; k < i; k += 32) sg[k] -= sR[i * jj + k] * yi;
       __syncwarp();
     }
   }
