@@ -63,10 +63,11 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def clocks_start():
+def clocks_start(log_path=None):
+    """Start sampling nvidia-smi clocks every 200 ms; the raw samples also go to log_path
+    (CSV) when one is given."""
     try:
-        f = open(os.path.join(ROOT, "gpurun_out", "clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                 else os.devnull, "w")
+        f = open(log_path or os.devnull, "w")
     except OSError:
         f = open(os.devnull, "w")
     cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -269,7 +270,7 @@ def run_ours(args, wl):
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        clk, clkf = clocks_start() if rank == 0 else (None, None)
+        clk, clkf = clocks_start(args.clocks_log) if rank == 0 else (None, None)
         times, infos = timed_solves(args.steps)
         clocks = clocks_stop(clk, clkf, local) if rank == 0 else None
         torch.cuda.synchronize()
@@ -370,6 +371,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=None)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-log", default=None, help="also write the raw clock samples (CSV) here")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
