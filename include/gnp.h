@@ -7,8 +7,9 @@
  *   - the GNP operator z = M(v): scaling s (Eq. 8), MLP encoder, L Res-GCONV layers
  *     over A_hat = A / gamma (Eqs. 6-7), MLP decoder, back-scaling s^{-1};
  *   - restarted flexible GMRES with M as a nonlinear right preconditioner (Sec. 2.1,
- *     Eq. 1, Algorithm 1) in float64: SpMV, CGS2 orthogonalisation, Givens QR of the
- *     Hessenberg matrix;
+ *     Eq. 1, Algorithm 1) in float64: SpMV, CGS2 orthogonalisation (the second pass's
+ *     norm gives h_{j+1,j} = sqrt(||w1||^2 - ||h2||^2), so a step takes two grid-wide
+ *     reductions), Givens QR of the Hessenberg matrix;
  *   - GNP training (Sec. 2.2, Eq. 5, Sec. 3 "Hyperparameters"): the Arnoldi/Gaussian
  *     training-pair sampler, forward, l1 residual loss, hand-written backward, Adam;
  *   - a continuous-batching solve server on top of the solver.
