@@ -4,8 +4,9 @@ Every test here puts one plausible error into the oracle (on the CPU, through a 
 copy of the affected function or argument) and checks that the independent pin that
 guards that part of the oracle rejects it: transposed or swapped layer weights, A_hat^T for
 A_hat, sqrt(n) -> n in the scaling s, max for min in gamma, a flipped Givens sine, a single
-Gram-Schmidt pass, and the transpose product dropped from the backward.  Together with
-the pins themselves this shows that the pins would notice such a mistake in the oracle.
+Gram-Schmidt pass, the transpose product dropped from the backward, swapped Philox key
+words, the natural logarithm in the metrics and D for D^-1 in Jacobi.  Together with the
+pins themselves this shows that the pins would notice such a mistake in the oracle.
 """
 import importlib.util
 import os
@@ -146,3 +147,43 @@ def test_backward_without_the_transpose_fails_the_finite_difference_pin(monkeypa
     _, cache = G.forward(Ahat, b, P, 0, keep=True)
     g = G.pack(G.backward(Ahat, P, cache, c))
     assert np.linalg.norm(g[idx] - gn) / np.linalg.norm(gn) > 1e-6
+
+
+def test_swapped_philox_key_words_fail_the_known_answer_vectors():
+    from oracle import philox_ref as PH
+    kat = os.path.join(HERE, "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(kat):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([int(t, 16) for t in line.split()])
+    hits = 0
+    for r in rows:
+        ctr = np.array([r[0:4]], dtype=np.uint64)
+        good = [int(v) for v in PH.philox4x32_10(ctr, (r[4], r[5]))[0]]
+        bad = [int(v) for v in PH.philox4x32_10(ctr, (r[5], r[4]))[0]]
+        assert good == r[6:10]
+        hits += bad != r[6:10]
+    # the all-zero and all-ones vectors have equal key words and cannot tell the order; the
+    # third (digits of pi) can
+    assert hits >= 1
+
+
+def test_natural_log_in_the_metrics_fails_the_decade_triangle(monkeypatch):
+    import math
+    from oracle import metrics_ref as MR
+    hist = [10.0 ** (-i) for i in range(9)]
+    assert abs(MR.iter_auc(hist, 1e-8) - 36.0) <= 1e-12
+    monkeypatch.setattr(MR, "_excess", lambda r, rtol: math.log(max(r, MR.DBL_MIN)) - math.log(rtol))
+    assert abs(MR.iter_auc(hist, 1e-8) - 36.0) > 1.0
+
+
+def test_jacobi_with_d_instead_of_its_inverse_fails_the_hand_example(monkeypatch):
+    from oracle import precond_ref as PR
+    d = np.array([2.0, -4.0, 0.0, 0.5])
+    A = sp.csr_matrix(np.diag(d) + np.diag([1.0, 1.0, 1.0], 1))
+    v = np.array([1.0, 2.0, 3.0, 4.0])
+    np.testing.assert_array_equal(PR.jacobi(A)(v), [0.5, -0.5, 3.0, 8.0])
+    good = PR.jacobi_diag_inv
+    monkeypatch.setattr(PR, "jacobi_diag_inv", lambda M: np.where(good(M) != 0, 1.0 / good(M), 1.0))
+    assert not np.array_equal(PR.jacobi(A)(v), [0.5, -0.5, 3.0, 8.0])
