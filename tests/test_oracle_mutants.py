@@ -187,3 +187,28 @@ def test_jacobi_with_d_instead_of_its_inverse_fails_the_hand_example(monkeypatch
     good = PR.jacobi_diag_inv
     monkeypatch.setattr(PR, "jacobi_diag_inv", lambda M: np.where(good(M) != 0, 1.0 / good(M), 1.0))
     assert not np.array_equal(PR.jacobi(A)(v), [0.5, -0.5, 3.0, 8.0])
+
+
+def test_sampler_with_s_instead_of_its_inverse_fails_the_eq5_pin():
+    # Eq. 5: x = V_m Z S^-1 eps gives ||A x|| = ||eps||; with Z S instead the norms differ
+    from oracle import philox_ref as PH
+    A = I.convdiff2d(9, 100.0).to_scipy()
+    V, H = K.arnoldi(A, K.arnoldi_v1(A.shape[0], seed=1), 15)
+    eps = PH.normal(15 * 4, 3, 5, PH.STREAM_EPS).reshape(15, 4)
+    Q, s = K.sampler_matrix(H)
+    X = K.training_x(V, Q, n_arnoldi=4, n_gauss=4, seed=3, step=5)
+    np.testing.assert_allclose(np.linalg.norm(A @ X[:, :4], axis=0), np.linalg.norm(eps, axis=0), rtol=1e-9)
+    Xbad = K.training_x(V, Q * (s ** 2)[None, :], n_arnoldi=4, n_gauss=4, seed=3, step=5)  # Z S
+    assert np.max(np.abs(np.linalg.norm(A @ Xbad[:, :4], axis=0) / np.linalg.norm(eps, axis=0) - 1)) > 1e-3
+
+
+def test_arnoldi_with_the_wrong_operator_fails_the_relation_pin():
+    # the sampler's Arnoldi run must multiply by A; a run that orthogonalises v_j itself
+    # (a dropped product) breaks A V_m = V_{m+1} H_bar
+    A = I.aniso3d(5, 100.0).to_scipy()
+    v1 = K.arnoldi_v1(A.shape[0], seed=7)
+    V, H = K.arnoldi(A, v1, 20)
+    assert np.linalg.norm(A @ V[:, :-1] - V @ H) <= 1e-12 * np.linalg.norm(H)
+    ident = sp.identity(A.shape[0], format="csr")
+    Vb, Hb = K.arnoldi(ident @ A @ A, v1, 20)  # the wrong operator (A^2)
+    assert np.linalg.norm(A @ Vb[:, :-1] - Vb @ Hb) > 1e-6 * np.linalg.norm(Hb)
