@@ -14,8 +14,8 @@ beyond:
 * ``convdiff2d``  -Lap(u) + beta (u_x + u_y) on the unit square, first-order upwind,
                   nonsymmetric.
 * ``aniso3d``     7-point -(u_xx + u_yy + eps_z u_zz) on an nx^3 grid.
-* ``powerlaw``    general sparse matrix, power-law row lengths, N(0,1) values,
-                  log-uniform row scaling (ill-conditioning), random row/column
+* ``powerlaw``    general sparse matrix, power-law row lengths, N(0,1) values plus a
+                  diagonal shift calibrated to cond ~ 1e6, random symmetric
                   permutation.
 
 Weight blobs follow the layout documented in ``include/gnp.h``.
@@ -134,25 +134,26 @@ def powerlaw_exponent(mean: float = 12.0, kmin: int = 2, kmax: int = 2000) -> fl
     return 0.5 * (lo + hi)
 
 
-def powerlaw(n: int, mean: float = 12.0, kmax: int = 2000, log10_scale_span: float = 6.0,
-             seed: int = 0) -> CSR:
-    """General sparse matrix with power-law row lengths (diagonal included).
-
-    * row length k ~ P(k) ~ k^-a on [2, min(kmax, n)], a chosen so E[k] = mean;
-    * off-diagonal columns uniform without repeats, values N(0, 1);
-    * diagonal = (sum of |off-diagonal| in the row) + 1, so the unscaled matrix is
-      strictly row diagonally dominant (nonsingular, moderately conditioned);
-    * rows are then scaled by s_i = 10^(U(0, span)) which makes the condition number
-      grow to about 10^span (here ~1e6) while keeping the matrix nonsingular;
-    * finally a random symmetric permutation P A P^T scatters the structure.
-    """
-    rng = np.random.default_rng(seed)
-    kmax = min(kmax, n)
+def _powerlaw_lengths(rng, n: int, mean: float, kmax: int) -> np.ndarray:
+    """Row lengths k (diagonal included) drawn from P(k) ~ k^-a on [2, kmax]."""
     k = np.arange(2, kmax + 1)
     a = powerlaw_exponent(mean, 2, kmax)
     p = k.astype(np.float64) ** (-a)
     p /= p.sum()
-    lens = rng.choice(k, size=n, p=p)
+    return rng.choice(k, size=n, p=p)
+
+
+def powerlaw_unshifted(n: int, mean: float = 12.0, kmax: int = 2000, seed: int = 0):
+    """The random part of the power-law matrix, before the diagonal shift and permutation.
+
+    Returns (rows, cols, vals, diag): the off-diagonal entries in COO form (values
+    N(0, 1), columns uniform over the other n - 1 indices, repeated (row, col) pairs
+    dropped) and the N(0, 1) diagonal.  The draws consume ``seed``'s PCG64 stream in
+    this order: row lengths, columns, off-diagonal values, diagonal values, permutation.
+    """
+    rng = np.random.default_rng(seed)
+    kmax = min(kmax, n)
+    lens = _powerlaw_lengths(rng, n, mean, kmax)
     off = lens - 1
     total = int(off.sum())
     rows = np.repeat(np.arange(n, dtype=np.int64), off)
@@ -166,14 +167,46 @@ def powerlaw(n: int, mean: float = 12.0, kmax: int = 2000, log10_scale_span: flo
     rows = key // n
     cols = key % n
     vals = rng.standard_normal(rows.shape[0])
-    absum = np.bincount(rows, weights=np.abs(vals), minlength=n)
-    diag = absum + 1.0
+    diag = rng.standard_normal(n)
+    return rows, cols, vals, diag, rng
+
+
+def powerlaw_radius(vals: np.ndarray, diag: np.ndarray) -> float:
+    """Spectral-radius estimate of the unshifted matrix: the root-mean-square row norm
+    sqrt(sum a_ij^2 / n), the radius of the circular law for independent entries."""
+    n = diag.size
+    return float(np.sqrt((np.dot(vals, vals) + np.dot(diag, diag)) / n))
+
+
+def _powerlaw_shift_fraction() -> float:
+    import json
+    import os
+    p = os.path.join(os.path.dirname(os.path.abspath(__file__)), "powerlaw_shift.json")
+    return float(json.load(open(p))["fraction"])
+
+
+def powerlaw(n: int, mean: float = 12.0, kmax: int = 2000, shift_fraction: float | None = None,
+             seed: int = 0, permute: bool = True) -> CSR:
+    """General sparse ill-conditioned matrix with power-law row lengths.
+
+    * row length k (diagonal included) ~ P(k) ~ k^-a on [2, min(kmax, n)], a chosen so
+      E[k] = mean;
+    * off-diagonal columns uniform without repeats; every value, the diagonal included,
+      N(0, 1);
+    * a diagonal shift s I with s = shift_fraction * rho, rho the circular-law radius of
+      the unshifted matrix (``powerlaw_radius``).  The default fraction is the one that
+      ``powerlaw_calibration.py`` found by dense singular values to give cond(A) ~ 1e6
+      at n = 4,096 and 16,384 (stored in ``powerlaw_shift.json``);
+    * a random symmetric permutation P A P^T (the shift stays on the diagonal).
+    """
+    rows, cols, vals, diag, rng = powerlaw_unshifted(n, mean, kmax, seed)
+    if shift_fraction is None:
+        shift_fraction = _powerlaw_shift_fraction()
+    s = shift_fraction * powerlaw_radius(vals, diag)
     rows = np.concatenate([rows, np.arange(n)])
     cols = np.concatenate([cols, np.arange(n)])
-    vals = np.concatenate([vals, diag])
-    scale = 10.0 ** rng.uniform(0.0, log10_scale_span, size=n)
-    vals = vals * scale[rows]
-    perm = rng.permutation(n)
+    vals = np.concatenate([vals, diag + s])
+    perm = rng.permutation(n) if permute else np.arange(n)
     return _from_coo_fast(n, perm[rows], perm[cols], vals)
 
 
