@@ -188,6 +188,16 @@ int gnp_apply(gnp_model* M, const double* v_dev, float* z_dev, void* stream);
 int gnp_apply_trace(gnp_model* M, const double* v_dev, float* z_dev, float* hidden_dev,
                     void* stream);
 
+/* One Res-GCONV layer of Eq. 7 (Sec. 2.3 item 2), layer index `layer` in [0, L):
+ * H_out = ReLU(H_in U_l + A_hat H_in W_l) (GNP_LAYER_PAPER) or
+ * H_in + ReLU(A_hat H_in W_l) (GNP_LAYER_RESID), with the kernel gnp_apply runs for its
+ * layers before the last.  h_in_dev / h_out_dev: caller-owned device hidden blocks,
+ * node-major n x 16 (16 consecutive values per node), float32 or bfloat16 as the model's
+ * current hprec says; they must not overlap (GNP_ERR_INVALID_ARG when equal).  Outputs
+ * are rounded to the hidden block's precision (bfloat16: round to nearest even).
+ * Asynchronous on `stream`. */
+int gnp_layer_apply(gnp_model* M, int layer, const void* h_in_dev, void* h_out_dev, void* stream);
+
 /* ---------------------------------------------------------------- training */
 
 /* Batched forward z = M(b) for B right-hand sides stored node-major (b_dev float32
@@ -354,21 +364,26 @@ void gnp_server_destroy(gnp_server* S);
 
 /* ---------------------------------------------------------------- allocation-free gamma */
 
-/* gamma of Eq. 6 for a CSR matrix the caller already holds on the device (row_ptr_dev
- * int32 [n+1], col_dev int32 [nnz], val_dev float64 [nnz], the conventions of
- * gnp_mat_create; only column indices are checked, on the device), written to the
- * device scalar *gamma_dev (NaN if a column index lies outside [0, n)).  The paper has
- * no counterpart of this call: it serves callers that cannot allocate device memory
- * when they call in -- code running while a CUDA graph is being captured, applications
- * whose device memory belongs to their own pool or arena, loops that cannot take the
- * implicit synchronisation of cudaMalloc/cudaFree.  It allocates nothing: its scratch
- * (column sums, block partials, a counter) is a fixed 8 MiB + 10 KiB array inside the
- * library, held by every GPU that loads the library until the process exits, so
- * n <= 1,048,576 (larger n gives GNP_ERR_INVALID_ARG).  The first call on each device
- * looks up that array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call clears the scratch it uses and shares the one
- * array: calls that overlap on the GPU (other streams, other threads) race.
- * Asynchronous on `stream`. */
+/* min(max row abs-sum, max column abs-sum) of a CSR matrix the caller already holds on
+ * the device (row_ptr_dev int32 [n+1], col_dev int32 [nnz], val_dev float64 [nnz], the
+ * conventions of gnp_mat_create), written to the device scalar *gamma_dev.  The CSR is
+ * checked on the device only: every access stays inside [0, nnz) and [0, n), and
+ * *gamma_dev is NaN when row_ptr does not start at 0, decreases or does not end at nnz,
+ * or when a column index lies outside [0, n).  The column sums are added with float64
+ * atomics, so the last bits of the result may differ from call to call (gnp_gamma sums
+ * in a fixed order).  The paper has no counterpart of this call.  It serves callers
+ * that must not allocate device memory when they call in: applications whose device
+ * memory belongs to their own pool or arena, plug-ins that receive only a stream and
+ * their host's buffers, loops that cannot take the implicit synchronisation of
+ * cudaMalloc/cudaFree.  It allocates nothing: its scratch (column sums, block partials,
+ * a counter, an error flag) is one fixed array of 8,398,592 bytes (8 MiB + 9,984 B)
+ * inside the library, held by every GPU that loads the library until the process exits,
+ * so n <= 1,048,576 (larger n gives GNP_ERR_INVALID_ARG).  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress) and caches it for the life
+ * of the process; make that first call before any stream capture, and do not reuse the
+ * library on a device after cudaDeviceReset.  Every call clears the scratch it uses and
+ * shares the one array: calls that overlap on the GPU (other streams, other threads)
+ * race.  Asynchronous on `stream`. */
 int gnp_gamma_noalloc(int n, long long nnz, const int* row_ptr_dev, const int* col_dev,
                       const double* val_dev, double* gamma_dev, void* stream);
 

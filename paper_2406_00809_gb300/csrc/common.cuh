@@ -269,10 +269,14 @@ __device__ __forceinline__ void tile_flush(SM& sm, int s, int q, int fr, int r, 
 
 // Requires sm.rp[0..rows] loaded and a __syncthreads() before the call.  Ends with
 // no barrier; the caller syncs before reading agg/cf/cl.
-template <class TR, class SM>
+//
+// GROUP neighbour rows are loaded at once per lane (4 or 8): the column indices and
+// values of the next group are fetched while the current group's rows are in flight.
+template <class TR, class SM, int GROUP = 4>
 __device__ __forceinline__ void tile_gather(SM& sm, int rows, const int* __restrict__ col,
                                             const typename TR::val_t* __restrict__ val,
                                             const typename TR::x_t* __restrict__ X) {
+  static_assert(GROUP == 4 || GROUP == 8, "4 or 8 rows in flight per lane");
   constexpr int G = TR::G, NV = TR::NV, S = TILE / G;
   using A = typename TR::acc;
   const int s = threadIdx.x / G, q = threadIdx.x % G;
@@ -311,49 +315,56 @@ __device__ __forceinline__ void tile_gather(SM& sm, int rows, const int* __restr
     for (int k = 0; k < NV; ++k) acc[k] = fma(A(v), h[k], acc[k]);
   };
 
-  // groups of 4 nonzeros; the next group's column indices and values are loaded while
-  // the current group's neighbour rows are in flight (one dependent round trip less)
+  // groups of GROUP nonzeros; the next group's column indices and values are loaded
+  // while the current group's neighbour rows are in flight (one dependent round trip less)
   int e = a;
-  int cn[4];
-  typename TR::val_t vn[4];
-  if (e + 4 <= b) {
+  int cn[GROUP];
+  typename TR::val_t vn[GROUP];
+  if (e + GROUP <= b) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < GROUP; ++u) {
       cn[u] = __ldg(col + e + u);
       vn[u] = __ldg(val + e + u);
     }
   }
-  for (; e + 4 <= b; e += 4) {
-    int c[4];
-    typename TR::val_t v[4];
+  for (; e + GROUP <= b; e += GROUP) {
+    int c[GROUP];
+    typename TR::val_t v[GROUP];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < GROUP; ++u) {
       c[u] = cn[u];
       v[u] = vn[u];
     }
-    if (e + 8 <= b) {
+    if (e + 2 * GROUP <= b) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        cn[u] = __ldg(col + e + 4 + u);
-        vn[u] = __ldg(val + e + 4 + u);
+      for (int u = 0; u < GROUP; ++u) {
+        cn[u] = __ldg(col + e + GROUP + u);
+        vn[u] = __ldg(val + e + GROUP + u);
       }
     }
-    A h0[NV], h1[NV], h2[NV], h3[NV];
-    TR::load(X, c[0], q, h0);
-    TR::load(X, c[1], q, h1);
-    TR::load(X, c[2], q, h2);
-    TR::load(X, c[3], q, h3);
-    step(e, v[0], h0);
-    step(e + 1, v[1], h1);
-    step(e + 2, v[2], h2);
-    step(e + 3, v[3], h3);
+    A h[GROUP][NV];
+#pragma unroll
+    for (int u = 0; u < GROUP; ++u) TR::load(X, c[u], q, h[u]);
+#pragma unroll
+    for (int u = 0; u < GROUP; ++u) step(e + u, v[u], h[u]);
   }
-  for (; e < b; ++e) {
-    int c0 = __ldg(col + e);
-    typename TR::val_t v0 = __ldg(val + e);
-    A h0[NV];
-    TR::load(X, c0, q, h0);
-    step(e, v0, h0);
+  if (e < b) {  // the last b - e < GROUP nonzeros: one predicated group, one round trip
+    int c[GROUP];
+    typename TR::val_t v[GROUP];
+    A h[GROUP][NV];
+#pragma unroll
+    for (int u = 0; u < GROUP; ++u) {
+      if (e + u < b) {
+        c[u] = __ldg(col + e + u);
+        v[u] = __ldg(val + e + u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < GROUP; ++u)
+      if (e + u < b) TR::load(X, c[u], q, h[u]);
+#pragma unroll
+    for (int u = 0; u < GROUP; ++u)
+      if (e + u < b) step(e + u, v[u], h[u]);
   }
   tile_flush<TR, SM>(sm, s, q, fr, r, rstart, rnext, a, b, acc);
 }

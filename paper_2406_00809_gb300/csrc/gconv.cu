@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "gconv_common.cuh"
 #include "solver.h"
 
 namespace gnp {
@@ -103,14 +104,6 @@ k_vnorm(ColPtr vp, const int* __restrict__ ctl, int n, double* __restrict__ part
   }
 }
 
-// d += a * b on two float32 lanes at once (fma.rn.f32x2: each lane an fmaf).
-__device__ __forceinline__ void ffma2(float& dx, float& dy, float ax, float ay, float bx, float by) {
-  asm("{\n\t.reg .b64 ta, tb, td;\n\t"
-      "mov.b64 ta, {%2, %3};\n\tmov.b64 tb, {%4, %5};\n\tmov.b64 td, {%0, %1};\n\t"
-      "fma.rn.f32x2 td, ta, tb, td;\n\tmov.b64 {%0, %1}, td;\n\t}"
-      : "+f"(dx), "+f"(dy)
-      : "f"(ax), "f"(ay), "f"(bx), "f"(by));
-}
 
 // ---------------------------------------------------------------- tile staging
 
@@ -303,7 +296,8 @@ struct GconvSmem {
   float zpart[ROWS];  // second half of the decoder sum (two threads per row)
 };
 
-// Outputs [K0, K0+OPT) of one row: ReLU(h U + agg W) (paper) or h + ReLU(agg W).
+// Outputs [K0, K0+OPT) of one row: ReLU(h U + agg W) (paper) or h + ReLU(agg W).  Two
+// outputs per paired multiply-add (each lane an fmaf, inputs in the same order).
 template <int FORM, int K0, int OPT>
 __device__ __forceinline__ void layer_part(const float (&h)[16], const float (&agg)[16],
                                            const LayerW& lw, float (&o)[OPT]) {
@@ -312,13 +306,15 @@ __device__ __forceinline__ void layer_part(const float (&h)[16], const float (&a
 #pragma unroll
   for (int c = 0; c < 16; ++c) {
 #pragma unroll
-    for (int k = 0; k < OPT; ++k) o[k] = fmaf(agg[c], lw.W[c * 16 + K0 + k], o[k]);
+    for (int k = 0; k < OPT; k += 2)
+      ffma2(o[k], o[k + 1], agg[c], agg[c], lw.W[c * 16 + K0 + k], lw.W[c * 16 + K0 + k + 1]);
   }
   if (FORM == GNP_LAYER_PAPER) {
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
 #pragma unroll
-      for (int k = 0; k < OPT; ++k) o[k] = fmaf(h[c], lw.U[c * 16 + K0 + k], o[k]);
+      for (int k = 0; k < OPT; k += 2)
+        ffma2(o[k], o[k + 1], h[c], h[c], lw.U[c * 16 + K0 + k], lw.U[c * 16 + K0 + k + 1]);
     }
 #pragma unroll
     for (int k = 0; k < OPT; ++k) o[k] = fmaxf(o[k], 0.0f);
@@ -359,29 +355,23 @@ __device__ __forceinline__ void gconv_part(GconvSmem<HT, ROWS>& sm, int t, int r
   }
 }
 
-// Programmatic dependent launch: each layer is launched while the previous one drains.
-// A layer loads its tile's row pointers (the matrix, never written), then waits for the
-// previous grid to complete and flush (griddepcontrol.wait) before any read of data a
-// previous kernel wrote; it releases its own dependents once its epilogue is done.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // The tile's hidden rows and its gather; the row pointers are already in sm.g.rp.
-template <class HT, int ROWS>
+template <class HT, int ROWS, int GROUP>
 __device__ __forceinline__ void gconv_load_gather(GconvSmem<HT, ROWS>& sm, const int* __restrict__ col,
                                                   const float* __restrict__ valhat, const HT* __restrict__ Hin,
                                                   int r0, int rows) {
   using TR = typename HTraits<HT>::TR;
   tile_copy<HT, false>(sm.stile, const_cast<HT*>(Hin), r0, rows);
   __syncthreads();
-  tile_gather<TR>(sm.g, rows, col, valhat, Hin);
+  tile_gather<TR, TileSmem<TR, ROWS>, GROUP>(sm.g, rows, col, valhat, Hin);
   __syncthreads();
 }
 
 template <int ROWS> struct GconvBounds { static constexpr int MIN_BLOCKS = 3; };
 template <> struct GconvBounds<128> { static constexpr int MIN_BLOCKS = 4; };
 
-template <class HT, int FORM, int ROWS>
+template <class HT, int FORM, int ROWS, int GROUP>
 __global__ void __launch_bounds__(TILE, GconvBounds<ROWS>::MIN_BLOCKS)
 k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
         const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, int trows, const int* __restrict__ ctl,
@@ -394,7 +384,7 @@ k_gconv(const int* __restrict__ rp, const int* __restrict__ col, const float* __
   tile_load_rp<typename HTraits<HT>::TR>(sm.g, rp, r0, rows);
   pdl_wait();
   if (ctl && !ctl[1]) return;
-  gconv_load_gather<HT, ROWS>(sm, col, valhat, Hin, r0, rows);
+  gconv_load_gather<HT, ROWS, GROUP>(sm, col, valhat, Hin, r0, rows);
   const int t = threadIdx.x % ROWS;
   if constexpr (ROWS == TILE) {
     float o[16];
@@ -444,7 +434,7 @@ __device__ __forceinline__ float decode_row(const float (&o)[16], const DecW& dw
   return z;
 }
 
-template <class HT, int FORM, int ROWS>
+template <class HT, int FORM, int ROWS, int GROUP>
 __global__ void __launch_bounds__(TILE, GconvBounds<ROWS>::MIN_BLOCKS)
 k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
             const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n,
@@ -462,7 +452,7 @@ k_gconv_dec(const int* __restrict__ rp, const int* __restrict__ col, const float
     const double tv = *tau;
     s_back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
   }
-  gconv_load_gather<HT, ROWS>(sm, col, valhat, Hin, r0, rows);  // ends with a barrier
+  gconv_load_gather<HT, ROWS, GROUP>(sm, col, valhat, Hin, r0, rows);  // ends with a barrier
   const int t = threadIdx.x % ROWS;
   const float back = s_back;
   float* z = static_cast<float*>(colptr(zp));
@@ -873,21 +863,37 @@ void fill_layer_w(const std::vector<float>& w, int l, LayerW& lw) {
   memcpy(lw.W, p + 256, sizeof(lw.W));
 }
 
+// Neighbour rows in flight per lane in the tile kernels' gather: 8 for float32 hidden
+// rows, 4 for bfloat16 (8 rows of 8 values would spill); GNP_GCONV_GROUP=4|8 in the
+// environment forces one (for tuning).
+static int env_int(const char* name, int dflt) {
+  const char* e = getenv(name);
+  return e ? atoi(e) : dflt;
+}
+
+template <class HT>
+static int gconv_group() {
+  const int g = env_int("GNP_GCONV_GROUP", sizeof(HT) == 4 ? 8 : 4);
+  return g == 4 ? 4 : 8;
+}
+
+template <class HT, int FORM, int ROWS>
+static int set_attr_all(cudaFuncAttribute attr, int value) {
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM, ROWS, 4>, attr, value));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM, ROWS, 4>, attr, value));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM, ROWS, 8>, attr, value));
+  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM, ROWS, 8>, attr, value));
+  return GNP_OK;
+}
+
 template <class HT, int FORM, int ROWS>
 static int set_smem_attrs() {
   static bool done = false;
   if (done) return GNP_OK;
   const int bytes = (int)sizeof(GconvSmem<HT, ROWS>);
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    bytes));
+  GNP_TRY((set_attr_all<HT, FORM, ROWS>(cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)));
   done = true;
   return GNP_OK;
-}
-
-static int env_int(const char* name, int dflt) {
-  const char* e = getenv(name);
-  return e ? atoi(e) : dflt;
 }
 
 // Rows per Res-GCONV tile: 256-row tiles (one epilogue thread per row) at three
@@ -938,9 +944,7 @@ static int set_carveout() {
   const int per_block = (int)sizeof(GconvSmem<HT, ROWS>) + 1024;  // + the runtime's reserved 1 KB
   const int pct = std::min(100, (blocks * per_block * 100 + 228 * 1024 - 1) / (228 * 1024));
   if (pct == applied) return GNP_OK;
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv<HT, FORM, ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
-  GNP_TRY_CUDA(cudaFuncSetAttribute(k_gconv_dec<HT, FORM, ROWS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                    pct));
+  GNP_TRY((set_attr_all<HT, FORM, ROWS>(cudaFuncAttributePreferredSharedMemoryCarveout, pct)));
   applied = pct;
   return GNP_OK;
 }
@@ -954,26 +958,11 @@ static int set_smem_attrs_all() {
   return GNP_OK;
 }
 
-// Launch with programmatic stream serialization (the kernel calls pdl_wait before it
-// reads anything an earlier kernel wrote).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int smem, cudaStream_t st, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(TILE);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
 
-// Layers 0..L-1 (the last one fused with the decoder unless tracing), ROWS-row tiles.
-template <class HT, int FORM, int ROWS>
-static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, const int* ctl,
+// Layers 0..L-1 (the last one fused with the decoder unless tracing), ROWS-row tiles,
+// GROUP neighbour rows in flight per lane.
+template <class HT, int FORM, int ROWS, int GROUP>
+static int launch_layers_g(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, const int* ctl,
                          cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const DecW& dw, double sqrt_n) {
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
@@ -986,7 +975,7 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
     LayerW lw;
     fill_layer_w(M->w_host, l, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l], st, cudaEventRecordExternal));
-    GNP_TRY_CUDA(launch_pdl(k_gconv<HT, FORM, ROWS>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
+    GNP_TRY_CUDA(launch_pdl(k_gconv<HT, FORM, ROWS, GROUP>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
                             (const HT*)H0, H1, n, trows, ctl, lw));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * l + 1], st, cudaEventRecordExternal));
     if (trace)
@@ -997,13 +986,21 @@ static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, c
     LayerW lw;
     fill_layer_w(M->w_host, L - 1, lw);
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1)], st, cudaEventRecordExternal));
-    GNP_TRY_CUDA(launch_pdl(k_gconv_dec<HT, FORM, ROWS>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
+    GNP_TRY_CUDA(launch_pdl(k_gconv_dec<HT, FORM, ROWS, GROUP>, ntg, smem, st, A->rp, A->col, (const float*)M->valhat,
                             (const HT*)H0, z, (const double*)W.tau, sqrt_n, n, trows, ctl, lw, dw));
     if (ev) GNP_TRY_CUDA(cudaEventRecordWithFlags(ev[2 * (L - 1) + 1], st, cudaEventRecordExternal));
   } else {
     k_decode<HT><<<(n + TILE - 1) / TILE, TILE, 0, st>>>(H0, z, W.tau, sqrt_n, n, ctl, dw);
   }
   return GNP_OK;
+}
+
+template <class HT, int FORM, int ROWS>
+static int launch_layers(gnp_model* M, HT* H0, HT* H1, ColPtr z, float* trace, const int* ctl,
+                         cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const DecW& dw, double sqrt_n) {
+  if (gconv_group<HT>() == 4)
+    return launch_layers_g<HT, FORM, ROWS, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n);
+  return launch_layers_g<HT, FORM, ROWS, 8>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n);
 }
 
 // Layers 0..L-1 with the short-row kernels (RB = TILE / LPR rows per block).
@@ -1054,6 +1051,53 @@ static int row_kernel_mode(const gnp_mat* A) {
   const int forced = env_int("GNP_ROW_DB", 0);
   const int db = forced == 4 || forced == 5 ? forced : (A->max_deg <= 4 ? 4 : 5);
   return (env_int("GNP_ROW_LPR", 4) == 2 ? 20 : 40) + db;
+}
+
+// One Res-GCONV layer l on caller buffers, with the kernel the apply runs for its
+// layers before the last (gnp_layer_apply).
+template <class HT, int FORM, int LPR, int DB>
+static int layer_row_one(gnp_model* M, int l, const HT* Hin, HT* Hout, cudaStream_t st) {
+  constexpr int RB = TILE / LPR;
+  const gnp_mat* A = M->A;
+  LayerWT lw;
+  fill_layer_wt(M->w_host, l, lw);
+  GNP_TRY_CUDA(launch_pdl(k_gconv_row<HT, FORM, LPR, DB>, (A->n + RB - 1) / RB, 0, st, A->rp, A->col,
+                          (const float*)M->valhat, Hin, Hout, A->n, (const int*)nullptr, lw));
+  return GNP_OK;
+}
+
+template <class HT, int FORM, int ROWS, int GROUP>
+static int layer_tile_one(gnp_model* M, int l, const HT* Hin, HT* Hout, cudaStream_t st) {
+  const gnp_mat* A = M->A;
+  const int n = A->n;
+  const int trows = gconv_tile_rows<HT, ROWS>(n);
+  LayerW lw;
+  fill_layer_w(M->w_host, l, lw);
+  GNP_TRY_CUDA(launch_pdl(k_gconv<HT, FORM, ROWS, GROUP>, (n + trows - 1) / trows, (int)sizeof(GconvSmem<HT, ROWS>),
+                          st, A->rp, A->col, (const float*)M->valhat, Hin, Hout, n, trows, (const int*)nullptr, lw));
+  return GNP_OK;
+}
+
+template <class HT, int FORM>
+static int layer_impl(gnp_model* M, int l, const HT* Hin, HT* Hout, cudaStream_t st) {
+  GNP_TRY((set_smem_attrs_all<HT, FORM>()));
+  switch (row_kernel_mode(M->A)) {
+    case 24: GNP_TRY((layer_row_one<HT, FORM, 2, 4>(M, l, Hin, Hout, st))); break;
+    case 25: GNP_TRY((layer_row_one<HT, FORM, 2, 5>(M, l, Hin, Hout, st))); break;
+    case 44: GNP_TRY((layer_row_one<HT, FORM, 4, 4>(M, l, Hin, Hout, st))); break;
+    case 45: GNP_TRY((layer_row_one<HT, FORM, 4, 5>(M, l, Hin, Hout, st))); break;
+    default: {
+      const bool g4 = gconv_group<HT>() == 4;
+      if (gconv_rows<HT>() == 128) {
+        GNP_TRY(g4 ? (layer_tile_one<HT, FORM, 128, 4>(M, l, Hin, Hout, st))
+                   : (layer_tile_one<HT, FORM, 128, 8>(M, l, Hin, Hout, st)));
+      } else {
+        GNP_TRY(g4 ? (layer_tile_one<HT, FORM, 256, 4>(M, l, Hin, Hout, st))
+                   : (layer_tile_one<HT, FORM, 256, 8>(M, l, Hin, Hout, st)));
+      }
+    }
+  }
+  return check_launch("gnp_layer_apply");
 }
 
 template <class HT, int FORM>
@@ -1249,6 +1293,25 @@ int gnp_apply_trace(gnp_model* M, const double* v_dev, float* z_dev, float* hidd
 }
 
 
+
+int gnp_layer_apply(gnp_model* M, int layer, const void* h_in_dev, void* h_out_dev, void* stream) {
+  GNP_REQUIRE(M && h_in_dev && h_out_dev, "gnp_layer_apply: null argument");
+  GNP_REQUIRE(layer >= 0 && layer < M->cfg.L, "gnp_layer_apply: layer %d outside [0, %d)", layer, M->cfg.L);
+  GNP_REQUIRE(h_in_dev != h_out_dev, "gnp_layer_apply: the input and output blocks must differ");
+  GNP_TRY(model_sync_host(M));
+  cudaStream_t st = as_stream(stream);
+  const bool paper = M->cfg.form == GNP_LAYER_PAPER;
+  if (M->hprec == GNP_H_BF16) {
+    auto* hi = static_cast<const uint16_t*>(h_in_dev);
+    auto* ho = static_cast<uint16_t*>(h_out_dev);
+    return paper ? layer_impl<uint16_t, GNP_LAYER_PAPER>(M, layer, hi, ho, st)
+                 : layer_impl<uint16_t, GNP_LAYER_RESID>(M, layer, hi, ho, st);
+  }
+  auto* hi = static_cast<const float*>(h_in_dev);
+  auto* ho = static_cast<float*>(h_out_dev);
+  return paper ? layer_impl<float, GNP_LAYER_PAPER>(M, layer, hi, ho, st)
+               : layer_impl<float, GNP_LAYER_RESID>(M, layer, hi, ho, st);
+}
 
 int gnp_get_weights(gnp_model* M, float* host_blob, int* count) {
   GNP_REQUIRE(M && count, "gnp_get_weights: null argument");

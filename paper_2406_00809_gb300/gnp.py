@@ -87,6 +87,7 @@ def lib():
         "gnp_set_hprec": (i, [vp, i]),
         "gnp_apply": (i, [vp, vp, vp, vp]),
         "gnp_apply_trace": (i, [vp, vp, vp, vp, vp]),
+        "gnp_layer_apply": (i, [vp, i, vp, vp, vp]),
         "gnp_forward_batch": (i, [vp, vp, i, vp, vp]),
         "gnp_backward_batch": (i, [vp, vp, vp, vp]),
         "gnp_sample_batch": (i, [vp, i, vp, vp]),
@@ -242,6 +243,7 @@ class Model:
         self.h = handle
         self.A = A  # keep the matrix alive
         self.cfg = cfg
+        self.hprec = cfg.hprec
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -312,6 +314,7 @@ def gnp_set_weights(M: Model, weights):
 
 def gnp_set_hprec(M: Model, hprec: int):
     _check(lib().gnp_set_hprec(M.h, hprec))
+    M.hprec = hprec
 
 
 def gnp_apply(M: Model, v, z, stream=None):
@@ -330,6 +333,18 @@ def gnp_apply_trace(M: Model, v, z, hidden, stream=None):
 
 
 # --------------------------------------------------------------------- training
+
+def gnp_layer_apply(M: Model, layer: int, Hin, Hout, stream=None):
+    """One Res-GCONV layer (Eq. 7) on caller hidden blocks [n, 16] of the model's precision
+    (torch.float32 for H_FP32, torch.bfloat16 for H_BF16)."""
+    import torch
+    dt = torch.bfloat16 if M.hprec == H_BF16 else torch.float32
+    for t, nm in ((Hin, "Hin"), (Hout, "Hout")):
+        if t.numel() != M.A.n * 16:
+            raise ValueError(f"{nm} must hold n x 16 = {M.A.n * 16} values, got {t.numel()}")
+    _check(lib().gnp_layer_apply(M.h, int(layer), _dptr(Hin, dt, "Hin"), _dptr(Hout, dt, "Hout"),
+                                 _stream(stream)))
+
 
 def gnp_forward_batch(M: Model, b, z, B=None, stream=None):
     """z = M(b) for a node-major batch b (float32 [n, B] or flat [n*B])."""

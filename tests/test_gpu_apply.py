@@ -172,3 +172,50 @@ def test_apply_all_layer_kernels(gnp, variant, name, hprec, form, monkeypatch):
         monkeypatch.delenv(k, raising=False)
     z2, _ = run_apply(gnp, A, blob, L, form, hprec, v)
     assert rel(z2, z) <= (2e-6 if hprec == 0 else 1e-2)
+
+
+@pytest.mark.parametrize("name", ["convdiff45", "powerlaw12k", "aniso9"])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("hprec", [0, 1])
+def test_layer_apply_matches_oracle(gnp, name, form, hprec):
+    """gnp_layer_apply: one Res-GCONV layer (Eq. 7) on the oracle's own H^l (rounded to the
+    hidden block's precision) against the oracle's H^(l+1), per layer; bfloat16 compares
+    with the oracle's layer evaluated on the same rounded input."""
+    import torch
+    A = MATS[name]()
+    L = 3
+    blob = I.init_weights(L, seed=11)
+    v = I.gaussian(A.n, seed=4)
+    Ahat = G.normalise(A.to_scipy())
+    P = G.unpack(blob, L)
+    Hs = G.hidden_trace(Ahat, v, P, form)
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L, form=form, hprec=hprec), blob)
+    dt = torch.bfloat16 if hprec else torch.float32
+    out = torch.empty((A.n, 16), dtype=dt, device="cuda")
+    for l in range(L):
+        hin = dev(Hs[l], torch.float32).to(dt)
+        gnp.gnp_layer_apply(M, l, hin, out)
+        torch.cuda.synchronize()
+        x = hin.float().cpu().numpy().astype(np.float64)    # the input the kernel saw
+        ax = Ahat @ x
+        pre = (x @ P["U"][l] + ax @ P["W"][l]) if form == 0 else ax @ P["W"][l]
+        ref = np.maximum(pre, 0.0) if form == 0 else x + np.maximum(pre, 0.0)
+        got = out.float().cpu().numpy().astype(np.float64)
+        tol = 8e-3 if hprec else F32_TOL   # bfloat16: one rounding of the stored output (2^-8)
+        assert rel(got, ref) <= tol, (name, form, hprec, l, rel(got, ref))
+
+
+def test_layer_apply_rejects_bad_arguments(gnp):
+    import torch
+    A = I.poisson2d(8)
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=2), I.init_weights(2, seed=0))
+    h = torch.zeros((A.n, 16), dtype=torch.float32, device="cuda")
+    o = torch.zeros_like(h)
+    with pytest.raises(gnp.GnpError):
+        gnp.gnp_layer_apply(M, 2, h, o)          # layer outside [0, L)
+    with pytest.raises(gnp.GnpError):
+        gnp.gnp_layer_apply(M, 0, h, h)          # in place
+    with pytest.raises(TypeError):
+        gnp.gnp_layer_apply(M, 0, h.to(torch.bfloat16), o)  # precision of the model is float32
