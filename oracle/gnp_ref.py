@@ -87,6 +87,18 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round to bfloat16 the way a float32 store to a bfloat16 hidden block does: first to
+    float32, then to the upper 16 bits of the float32 pattern, round to nearest, ties to
+    even (add 0x7FFF plus the lowest kept bit, clear the low 16 bits).  Returned as
+    float64.  Inputs are finite."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
 def spmm(Ahat: sp.csr_matrix, X: np.ndarray) -> np.ndarray:
     """A_hat X for X of shape [n, B, d] (the sparse product is the library primitive)."""
     n, B, d = X.shape
@@ -113,14 +125,20 @@ def scale(b: np.ndarray):
 
 
 def forward(Ahat: sp.csr_matrix, b: np.ndarray, P: dict, form: int = FORM_PAPER,
-            keep: bool = False, scaled: bool = True):
+            keep: bool = False, scaled: bool = True, hstore: str = "f64"):
     """z = M(b) for b of shape [n] or [n, B] (Sec. 2.3, Fig. 1, Eqs. 6-8).
 
     s -> encoder (1 -> 32, ReLU, -> 16) -> L x Res-GCONV -> decoder (16 -> 32, ReLU,
     -> 1) -> s^{-1}.  With keep=True also returns the saved activations for backward.
     scaled=False is the ablation of Sec. 4 without s: the network sees b itself and its
-    output is z.
+    output is z.  hstore="bf16" emulates a bfloat16 hidden block (reading c18): every
+    hidden block that is stored between two steps -- the encoder output and the output
+    of each layer but the last, which the decoder consumes directly -- is rounded with
+    round_bf16; all arithmetic stays float64.
     """
+    if hstore not in ("f64", "bf16"):
+        raise ValueError(hstore)
+    store = round_bf16 if hstore == "bf16" else (lambda X: X)
     vec = b.ndim == 1
     bb = b[:, None] if vec else b
     n = bb.shape[0]
@@ -130,10 +148,11 @@ def forward(Ahat: sp.csr_matrix, b: np.ndarray, P: dict, form: int = FORM_PAPER,
         u, tau = bb.copy(), np.full(bb.shape[1], np.sqrt(n))
     a1 = u[:, :, None] * P["enc_W1"][0][None, None, :] + P["enc_b1"]   # [n,B,32]
     r1 = relu(a1)
-    H = r1 @ P["enc_W2"] + P["enc_b2"]                                  # [n,B,16]
+    H = store(r1 @ P["enc_W2"] + P["enc_b2"])                           # [n,B,16]
     Hs = [H]
     Ps, pres = [], []
-    for U, W in zip(P["U"], P["W"]):
+    L = len(P["U"])
+    for l, (U, W) in enumerate(zip(P["U"], P["W"])):
         X = Hs[-1]
         AX = spmm(Ahat, X)
         if form == FORM_PAPER:
@@ -142,6 +161,8 @@ def forward(Ahat: sp.csr_matrix, b: np.ndarray, P: dict, form: int = FORM_PAPER,
         else:
             pre = AX @ W
             Hn = X + relu(pre)
+        if l < L - 1:
+            Hn = store(Hn)
         Ps.append(AX)
         pres.append(pre)
         Hs.append(Hn)

@@ -255,3 +255,53 @@ def test_train_step_on_b_equals_train_step_on_x():
     w2, l2 = G.train_step(Ahat, blob, L, 0, x, G.Adam(blob.size))
     assert l1 == pytest.approx(l2, rel=1e-9)
     np.testing.assert_allclose(w1, w2, rtol=0, atol=1e-9)
+
+
+# ------------------------------------------------------------- bfloat16 hidden block (c18)
+
+def test_round_bf16_matches_torch_and_ties():
+    """round_bf16 against torch's float32 -> bfloat16 conversion (round to nearest even),
+    over many magnitudes, and on exact ties worked by hand."""
+    import torch
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(G.round_bf16(x), ref)
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties to the even pattern (1.0);
+    # 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6: ties to 1 + 2^-6
+    ties = np.array([1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, -(1 + 2.0 ** -8), 1 + 2.0 ** -8 + 2.0 ** -20])
+    np.testing.assert_array_equal(G.round_bf16(ties), [1.0, 1 + 2.0 ** -6, -1.0, 1 + 2.0 ** -7])
+
+
+@pytest.mark.parametrize("form", [G.FORM_PAPER, G.FORM_RESID])
+def test_forward_bf16_store_rounds_exactly_the_stored_blocks(form):
+    """hstore='bf16': H^0 .. H^(L-1) are bfloat16 values (each was rounded when stored),
+    H^L (consumed by the decoder in the same step) is not; z stays within a few bfloat16
+    ulps of the float64 forward; L = 0 rounds only the encoder output."""
+    rng = np.random.default_rng(3)
+    n, L = 40, 3
+    A = I.CSR(n, *_random_csr(rng, n))
+    Ah = G.normalise(A.to_scipy())
+    P = G.unpack(I.init_weights(L, seed=4), L)
+    b = rng.standard_normal(n)
+    z, c = G.forward(Ah, b, P, form, keep=True, hstore="bf16")
+    for l in range(L):
+        np.testing.assert_array_equal(G.round_bf16(c["Hs"][l]), c["Hs"][l])
+    assert np.any(G.round_bf16(c["Hs"][L]) != c["Hs"][L])
+    z64 = G.forward(Ah, b, P, form)
+    err = np.linalg.norm(z - z64) / np.linalg.norm(z64)
+    assert 1e-6 < err < 5e-2
+    with pytest.raises(ValueError):
+        G.forward(Ah, b, P, form, hstore="f16")
+
+
+def _random_csr(rng, n):
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        cs = np.unique(np.concatenate([[i], rng.integers(0, n, 3)]))
+        rows += [i] * cs.size
+        cols += list(cs)
+        vals += list(rng.standard_normal(cs.size) + (cs == i) * 4.0)
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    return row_ptr, np.asarray(cols, dtype=np.int32), np.asarray(vals)

@@ -212,3 +212,34 @@ def test_arnoldi_with_the_wrong_operator_fails_the_relation_pin():
     ident = sp.identity(A.shape[0], format="csr")
     Vb, Hb = K.arnoldi(ident @ A @ A, v1, 20)  # the wrong operator (A^2)
     assert np.linalg.norm(A @ Vb[:, :-1] - Vb @ Hb) > 1e-6 * np.linalg.norm(Hb)
+
+
+def test_truncating_bf16_rounding_fails_the_torch_pin():
+    """Planted: bfloat16 by truncation (clear the low 16 bits) instead of round to nearest
+    even.  The pin compares with torch's conversion."""
+    import torch
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(2000)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+    def trunc(v):
+        u = np.asarray(v, dtype=np.float64).astype(np.float32).view(np.uint32) & np.uint32(0xFFFF0000)
+        return u.view(np.float32).astype(np.float64)
+
+    assert np.any(trunc(x) != ref)
+    np.testing.assert_array_equal(G.round_bf16(x), ref)
+
+
+def test_rounding_the_decoder_input_fails_the_stored_block_pin(monkeypatch):
+    """Planted: the bfloat16 emulation also rounds H^L, which the decoder consumes in the
+    same step without a store.  The pin requires H^L to be left unrounded."""
+    rng = np.random.default_rng(3)
+    n, L = 40, 3
+    A = I.CSR(n, *_pins_gnp()._random_csr(rng, n))
+    Ah = G.normalise(A.to_scipy())
+    P = G.unpack(I.init_weights(L, seed=4), L)
+    b = rng.standard_normal(n)
+    _, c = G.forward(Ah, b, P, 0, keep=True, hstore="bf16")
+    assert np.any(G.round_bf16(c["Hs"][L]) != c["Hs"][L])       # the unmutated oracle passes
+    mutated = [G.round_bf16(H) for H in c["Hs"]]                  # what rounding every block gives
+    assert not np.any(G.round_bf16(mutated[L]) != mutated[L])    # ... and the pin rejects it
