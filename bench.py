@@ -1,20 +1,30 @@
 """Benchmark: GNP-preconditioned FGMRES time-to-rtol on one GB300 (and replicas).
 
-Workload (default): nonsymmetric 2-D convection-diffusion on a 256 x 256 grid
+Headline workload (default): nonsymmetric 2-D convection-diffusion on a 256 x 256 grid
 (n = 65,536, upwind, Peclet 100), GNP with hidden width 16 and 8 Res-GCONV layers in
 float32, weights trained by this library (2,000 Adam steps, batch 16, half Eq. 5
 Arnoldi samples with m = 40 and half N(0, I)), FGMRES(30) to rtol 1e-8 from x0 = 0,
-b = A x with x ~ N(0, 1) (seed 0).  Synthetic inputs (no dataset).
+b = A x with x ~ N(0, 1) (seed 0).  Synthetic inputs (no dataset).  It is the largest
+configured workload on which GNP-FGMRES reaches rtol 1e-8: on the 2^20-row power-law
+matrix (cond ~1e6 by a diagonal shift inside its spectrum) FGMRES(50) stagnates with and
+without the GNP, so that workload measures the apply's bandwidth instead (below).
 
 One step = one complete solve.  Timed with CUDA events on the solve's stream after an
 L2 flush (a 256 MB write); W untimed warm-up solves first.  Also reported:
-* roofline of the dominant kernel (the Res-GCONV layer): CUDA events recorded around
-  every Res-GCONV launch inside the captured restart cycle during a second pass of K
-  solves (the event records slow the solve slightly, so the headline time comes from
-  the first pass without them);
+* bf16 / identity: the bfloat16 hidden-block form of the same GNP and FGMRES without a
+  preconditioner, time-to-rtol and the true relative residual of each;
+* roofline: the step's dominant kernel (the short-row Res-GCONV layer) launched on its
+  own through gnp_layer_apply, R back-to-back launches between two CUDA events on the
+  launching stream; at 65,536 rows its working set (11 MB) stays in the 129 MB L2, so
+  the fraction of the HBM peak is labelled l2_resident;
+* roofline_c3: the nnz-balanced Res-GCONV tile kernel on the 2^20-row power-law matrix
+  (240 MB per float32 layer, larger than L2), each launch event-timed after an L2 flush,
+  float32 and bfloat16, and the whole apply z = M(v) in GB/s;
 * e2e: the same solves with b copied from pinned host memory and x copied back inside
   the timed region;
-* the bf16 hidden-block form of the same trained GNP (time-to-rtol, iterations);
+* c4_train: GNP training on the 64^3 anisotropic problem (batch 32): seconds per step over
+  50 timed steps, extrapolated to the configured 5,000, with its roofline and an oracle
+  sample as its CPU baseline;
 * cpu_baseline: the float64 oracle on the host cores, a bounded sample of FGMRES
   iterations scaled to seconds per solve by this run's iteration count.
 With --impl reference the oracle alone runs as the reference arm.
@@ -39,20 +49,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2406_00809_gb300 import inputs as I  # noqa: E402
+from paper_2406_00809_gb300 import replicas  # noqa: E402
+
+METRIC = "GNP-FGMRES time-to-rtol 1e-8 (s)"
 
 WORKLOADS = {
     "convdiff256": dict(desc="2-D convection-diffusion 256x256 upwind Pe=100 (n=65,536)",
                         make=lambda: I.convdiff2d(256, 100.0), L=8, restart=30, rtol=1e-8,
                         maxiters=3000, train_steps=2000, batch=16, arnoldi_m=40),
-    "powerlaw1m": dict(desc="power-law general sparse n=2^20 (mean 12, max 2000 nnz/row), row scaling 1e6",
-                       make=lambda: I.powerlaw(1 << 20, seed=0), L=8, restart=50, rtol=1e-8,
-                       maxiters=3000, train_steps=200, batch=16, arnoldi_m=40),
 }
-# iterations to rtol 1e-8 that the trained GNP of this library needs on each workload
-# (measured by this bench's own arm: 651-672 on the convection-diffusion workload; the
-# power-law one stops at the 3000-iteration cap); the reference arm scales its
-# per-iteration time by it to report seconds per solve.
-REF_ITERS = {"convdiff256": 660, "powerlaw1m": 3000}
+C3 = dict(desc="power-law general sparse n=2^20 (mean 12, max 2000 nnz/row), N(0,1) values + "
+               "diagonal shift (cond ~1e6 at the calibration sizes), symmetric random permutation",
+          make=lambda: I.powerlaw(1 << 20, seed=0), L=8)
+
+C4 = dict(desc="GNP training: 3-D 7-point anisotropic diffusion 64^3 (n=262,144, coefficient ratio 1:1:100), "
+               "batch 32 (16 Eq. 5 Arnoldi samples with m=30, 16 N(0,I)), L1 loss, Adam lr 1e-3",
+          make=lambda: I.aniso3d(64, 100.0), L=8, batch=32, arnoldi_m=30, total_steps=5000)
+
+# The reference arm times a bounded sample of oracle iterations and scales it to seconds
+# per solve by this many iterations: the iteration count of this library's own float32
+# solve of the workload (643 in its last runs; float32 rounding moves it by a few
+# percent, and the float64 oracle with the same weights takes 622).  The oracle itself
+# cannot train the GNP at this size in bench time (about 11 s per training step).
+SOLVE_ITERS_FOR_SCALING = {"convdiff256": 643}
 
 
 def load_peaks():
@@ -111,15 +130,14 @@ def clocks_stop(p, f, dev_index):
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+def aggregate(t_local: float, units_local: float, device=None):
+    """Whole-job figures over the replicas: the step time is the maximum over ranks, the
+    work the sum over ranks (so value = units / time counts every rank's solves)."""
+    return replicas.max_over_ranks(t_local, device), replicas.sum_over_ranks(units_local, device)
 
 
 def gconv_source_hash():
-    """Hash of the sources that define the Res-GCONV kernel (a stored ncu traffic figure
+    """Hash of the sources that define the Res-GCONV kernels (a stored ncu traffic figure
     is used only while they are unchanged)."""
     import hashlib
     h = hashlib.sha256()
@@ -128,14 +146,14 @@ def gconv_source_hash():
     return h.hexdigest()[:16]
 
 
-def stored_traffic(workload):
+def stored_traffic(workload, hprec="fp32"):
     """DRAM bytes per Res-GCONV launch from the committed ncu summary, or None when the
     kernel sources changed since that capture."""
     p = os.path.join(ROOT, "profiles", "res_gconv_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(workload)
+    e = d.get(workload if hprec == "fp32" else f"{workload}_{hprec}")
     if not e or e.get("source_hash") != gconv_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
@@ -154,6 +172,61 @@ def gconv_bytes(n, nnz, hbytes):
     A_hat values (int32 + float32 per nonzero), the hidden block read once and the
     next one written once."""
     return 4 * (n + 1) + 8 * nnz + 2 * n * 16 * hbytes
+
+
+def apply_bytes(n, nnz, L, hbytes):
+    """Algorithmic bytes of one apply z = M(v): the norm pass and encoder (v read twice,
+    H^0 written), L - 1 layers, the decoder-fused last layer (H read, z written)."""
+    csr = 4 * (n + 1) + 8 * nnz
+    return 8 * n + 8 * n + 16 * n * hbytes + (L - 1) * gconv_bytes(n, nnz, hbytes) + csr + 16 * n * hbytes + 4 * n
+
+
+def train_step_bytes(n, nnz, B, L):
+    """Algorithmic bytes of one training step as the measurement plan states them: per
+    layer the forward reads the batch hidden block (n B 16 float32) and writes the next one
+    and reads the CSR once for all B columns; the backward moves about three times the
+    forward's bytes.  At 262,144 rows, B = 32, L = 8: about 35 GB."""
+    csr = 4 * (n + 1) + 8 * nnz
+    return 4 * L * (csr + 2 * n * B * 16 * 4)
+
+
+def train_kernel_bytes(n, nnz, B, L):
+    """Compulsory DRAM bytes of the kernels one training step of this library launches
+    (float32; S = one batch hidden block of n B 16 floats, R = n B): forward 3S per layer
+    (read H, write A_hat H and the next H, both kept for the backward), encoder and
+    decoder; loss SpMMs; backward per layer 13S (the layer backward reads H, A_hat H and
+    the incoming gradient and writes three blocks, the transposed SpMM, the two weight
+    gradients re-reading their operands), decoder and encoder backward; CSR / CSC once per
+    product."""
+    S = n * B * 16 * 4
+    R4 = n * B * 4
+    csr = 4 * (n + 1) + 8 * nnz
+    fwd = R4 + (2 * R4 + S) + L * (3 * S + csr) + (S + R4)
+    loss = (3 * R4 + csr) + R4 + (2 * R4 + csr + 4 * nnz)
+    bwd = (S + R4 + R4 + 5 * S) + 3 * S + (2 * S + R4) + L * (13 * S + csr + 4 * nnz) + (S + R4 + 4 * S) \
+        + 3 * S + (R4 + 2 * S)
+    return fwd + loss + bwd
+
+
+def oracle_train_sample(A, L, batch, arnoldi_m, seconds=15.0, sample_batch=2):
+    """Seconds per oracle training step at `batch`, from oracle steps at `sample_batch`
+    on the same matrix (the step's cost is linear in the batch) timed for ~`seconds`."""
+    from oracle import gnp_ref as G
+    from oracle import krylov_ref as K
+    Ah = G.normalise(A.to_scipy())
+    V, Hb = K.arnoldi(Ah, K.arnoldi_v1(A.n, 0), arnoldi_m)
+    Q, _ = K.sampler_matrix(Hb)
+    w = I.init_weights(L, seed=0).astype(np.float64)
+    opt = G.Adam(w.size)
+    half = sample_batch // 2
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 1 or (time.perf_counter() - t0 < seconds and steps < 20):
+        x = K.training_x(V, Q, half, sample_batch - half, 0, steps)
+        w, _ = G.train_step(Ah, w, L, G.FORM_PAPER, x, opt)
+        steps += 1
+    per = (time.perf_counter() - t0) / steps
+    return per * batch / sample_batch, steps
 
 
 # ----------------------------------------------------------------------- oracle arm
@@ -179,14 +252,20 @@ def oracle_sample(A, b, L, restart, seconds=15.0, maxit=60):
     return total_t / max(total_it, 1), total_it
 
 
+def base_config(wl, A, hprec="fp32"):
+    return {"workload": wl["desc"], "n": A.n, "nnz": A.nnz, "L": wl["L"], "hidden": 16, "hprec": hprec,
+            "restart": wl["restart"], "rtol": wl["rtol"], "train_steps": wl["train_steps"],
+            "batch": wl["batch"], "arnoldi_m": wl["arnoldi_m"], "x0": "zeros"}
+
+
 def run_reference(args, wl):
-    ws, rank, _ = dist_setup()
+    ws, rank, _ = replicas.env()
     if ws > 1 and rank != 0:
         return
     A = wl["make"]()
     x_true = I.gaussian(A.n, seed=0)
     b = I.spmv(A, x_true)
-    iters = REF_ITERS[args.workload]
+    iters = SOLVE_ITERS_FOR_SCALING[args.workload]
     per_step = []
     for s in range(args.warmup + args.steps):
         spi, nit = oracle_sample(A, b, wl["L"], wl["restart"], seconds=args.ref_seconds)
@@ -194,16 +273,19 @@ def run_reference(args, wl):
             per_step.append(spi * iters)
     value = statistics.mean(per_step)
     cores = os.cpu_count()
+    cfg = base_config(wl, A, hprec="f64")
+    cfg["l2"] = "n/a (host)"
     line = {
-        "impl": "reference", "metric": "GNP-FGMRES time-to-rtol 1e-8 (s)", "value": value, "unit": "s",
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": wl["desc"], "L": wl["L"], "restart": wl["restart"], "rtol": wl["rtol"]},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                          "sample": f"float64 numpy/scipy oracle: FGMRES({wl['restart']}) + GNP iterations "
-                                   f"timed for ~{args.ref_seconds:.0f} s per step, scaled by {iters} "
-                                   "iterations to rtol (the iteration count of this library's trained GNP)"},
+                                   f"timed for ~{args.ref_seconds:.0f} s per step and scaled by {iters} "
+                                   "iterations (an extrapolation: the iteration count of this library's "
+                                   "float32 solve of the same workload)"},
+        "extrapolated_from_iterations": nit, "scaled_by_iterations": iters,
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -211,13 +293,123 @@ def run_reference(args, wl):
 
 # ----------------------------------------------------------------------- our arm
 
+def event_time(stream, fn, reps, flush=None):
+    """Per-call seconds of fn() on `stream`: CUDA events around each call (after an L2
+    flush when given), or with flush=None around reps back-to-back calls (the mean)."""
+    import torch
+    if flush is None:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return [e0.elapsed_time(e1) / 1e3 / reps]
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times
+
+
+def layer_roofline(gnp, M, n, nnz, hbytes, stream, flush, peak, peak_kind, reps, workload, kernel, hprec):
+    """Event-timed stand-alone launches of Res-GCONV layer 0 (gnp_layer_apply)."""
+    import torch
+    dt = torch.bfloat16 if hbytes == 2 else torch.float32
+    H0 = (torch.randn(n, 16, device="cuda") * 0.5).to(dt)
+    H1 = torch.empty_like(H0)
+    for _ in range(3):
+        gnp.gnp_layer_apply(M, 0, H0, H1, stream=stream)
+    times = event_time(stream, lambda: gnp.gnp_layer_apply(M, 0, H0, H1, stream=stream), reps, flush)
+    t = statistics.median(times)
+    by = gconv_bytes(n, nnz, hbytes)
+    ach = by / t / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": stored_traffic(workload, hprec), "kernel": kernel, "peak_kind": peak_kind,
+            "bytes_per_launch": by, "avg_launch_us": t * 1e6, "launches_timed": reps,
+            "l2_resident": flush is None, "hprec": hprec,
+            "timing": ("back-to-back stand-alone launches between two CUDA events (warm L2)" if flush is None
+                       else "CUDA events around each stand-alone launch, L2 flushed (256 MB write) before each")}
+
+
+def c3_block(gnp, stream, flush, peak, peak_kind, reps):
+    """The 2^20-row power-law matrix: HBM roofline of the tile kernel and the apply GB/s."""
+    import torch
+    A = C3["make"]()
+    n, nnz, L = A.n, A.nnz, C3["L"]
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L), I.init_weights(L, seed=0))
+    v = torch.from_numpy(I.gaussian(n, seed=1)).cuda()
+    z = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = {"workload": C3["desc"], "n": n, "nnz": nnz, "L": L,
+           "time_to_rtol": None,
+           "solve": "FGMRES(50) stagnates on this matrix with and without the GNP (the shift that gives "
+                    "cond ~1e6 leaves the spectrum around the origin); no time-to-rtol exists"}
+    for name, hp, hb in (("fp32", gnp.H_FP32, 4), ("bf16", gnp.H_BF16, 2)):
+        gnp.gnp_set_hprec(M, hp)
+        for _ in range(3):
+            gnp.gnp_apply(M, v, z, stream=stream)
+        ta = statistics.median(event_time(stream, lambda: gnp.gnp_apply(M, v, z, stream=stream), reps, flush))
+        ab = apply_bytes(n, nnz, L, hb)
+        out[f"apply_{name}"] = {"ms": ta * 1e3, "GBs": ab / ta / 1e9, "frac": ab / ta / 1e9 / peak,
+                                "bytes": ab}
+        out[f"roofline_{name}"] = layer_roofline(gnp, M, n, nnz, hb, stream, flush, peak, peak_kind, reps,
+                                                 "powerlaw1m", gconv_kernel_name(A), name)
+    gnp.gnp_set_hprec(M, gnp.H_FP32)
+    return out
+
+
+def c4_block(gnp, stream, peak, peak_kind, steps, cpu_seconds):
+    """GNP training on the 64^3 anisotropic problem: a timed run of `steps` training steps
+    (after 5 warm-up steps that include the sampler's Arnoldi process and SVD),
+    extrapolated to the configured 5,000 steps."""
+    import torch
+    A = C4["make"]()
+    n, nnz, L, B = A.n, A.nnz, C4["L"], C4["batch"]
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L, batch=B, arnoldi_m=C4["arnoldi_m"], seed=0),
+                       I.init_weights(L, seed=0))
+    gnp.gnp_train(M, 5, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    best = gnp.gnp_train(M, steps, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    per = e0.elapsed_time(e1) / 1e3 / steps
+    by = train_step_bytes(n, nnz, B, L)
+    out = {"workload": C4["desc"], "n": n, "nnz": nnz, "L": L, "batch": B, "steps_timed": steps,
+           "s_per_step": per, "s_for_5000_steps": per * C4["total_steps"],
+           "extrapolation": f"{steps} timed steps scaled to {C4['total_steps']}", "best_loss": best,
+           "roofline": {"bound": "hbm", "achieved": by / per / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": by / per / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                        "bytes_per_step": by, "kernel_bytes_per_step": train_kernel_bytes(n, nnz, B, L),
+                        "kernel": "whole training step (forward, loss, hand-written backward, Adam)"}}
+    if cpu_seconds:
+        spb, nst = oracle_train_sample(A, L, B, C4["arnoldi_m"], seconds=cpu_seconds)
+        out["cpu_baseline"] = {"value": spb, "unit": "s per training step", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"{nst} float64 oracle training steps at batch 2 on the same matrix "
+                                         f"(after its 30-step Arnoldi run), scaled by 16 to batch 32"}
+    del M, Mt
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, wl):
     import torch
-    import torch.distributed as dist
-    ws, rank, local = dist_setup()
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ws, rank, local = replicas.env()
     torch.cuda.set_device(local)
+    replicas.init("nccl", torch.device("cuda", local))
     from paper_2406_00809_gb300 import build
     build.build()
     from paper_2406_00809_gb300 import gnp
@@ -228,6 +420,8 @@ def run_ours(args, wl):
     x_true = I.gaussian(n, seed=0)
     b_np = I.spmv(A, x_true)
     L, m, rtol, maxit = wl["L"], wl["restart"], wl["rtol"], wl["maxiters"]
+    train_steps = args.train_steps if args.train_steps is not None else wl["train_steps"]
+    peak, peak_kind = load_peaks()
     with torch.cuda.stream(stream):
         Mt = gnp.mat_from_csr(A)
         cfg = gnp.make_config(L=L, batch=wl["batch"], arnoldi_m=wl["arnoldi_m"], seed=0)
@@ -235,20 +429,19 @@ def run_ours(args, wl):
         # construction: GNP training (outside the timed region, reported separately)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        best = gnp.gnp_train(M, args.train_steps if args.train_steps is not None else wl["train_steps"])
+        best = gnp.gnp_train(M, train_steps)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         b = torch.from_numpy(b_np).to(dev)
         x = torch.zeros(n, dtype=torch.float64, device=dev)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-        def solve(prof=False):
+        def solve(prec=M):
             x.zero_()
-            return gnp.fgmres_solve(Mt, b, x, M, restart=m, rtol=rtol, maxiters=maxit, stream=stream,
+            return gnp.fgmres_solve(Mt, b, x, prec, restart=m, rtol=rtol, maxiters=maxit, stream=stream,
                                     history=False)
 
-        def timed_solves(k, prof=False):
-            gnp.gnp_profile_gconv(prof)
+        def timed_solves(k, prec=M):
             times, infos = [], []
             for _ in range(k):
                 flush.zero_()
@@ -256,45 +449,26 @@ def run_ours(args, wl):
                 e1 = torch.cuda.Event(enable_timing=True)
                 stream.synchronize()
                 e0.record(stream)
-                info = solve()
+                info = solve(prec)
                 e1.record(stream)
                 e1.synchronize()
                 times.append(e0.elapsed_time(e1) / 1e3)
                 infos.append(info)
-            gnp.gnp_profile_gconv(False)
             return times, infos
 
         for _ in range(args.warmup):
             solve()
         torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
+        # clocks are sampled over every timed solve below (headline, e2e, bf16, M = I)
         clk, clkf = clocks_start(args.clocks_log) if rank == 0 else (None, None)
         times, infos = timed_solves(args.steps)
-        clocks = clocks_stop(clk, clkf, local) if rank == 0 else None
         torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        t_local = statistics.mean(times)
-        if ws > 1:
-            tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_max = float(tt.item())
-        else:
-            t_max = t_local
+        replicas.barrier()
+        t_max, solves_all = aggregate(statistics.mean(times), 1.0, dev)
         info = infos[-1]
         rel_true = float(np.linalg.norm(b_np - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b_np))
-        # roofline pass: the same solves with the Res-GCONV launches event-timed
-        rtimes, rinfos = timed_solves(max(1, args.steps), prof=True)
-        g_ms = sum(i.gconv_ms for i in rinfos)
-        g_n = sum(i.gconv_launches for i in rinfos)
-        avg_launch_s = (g_ms / max(g_n, 1)) / 1e3
-        # per-launch algorithmic bytes: L-1 plain layers + the decoder-fused last layer
-        # (writes z, 4 bytes per row, instead of the next hidden block)
-        per_solve_bytes = (L - 1) * gconv_bytes(n, nnz, 4) + (4 * (n + 1) + 8 * nnz + n * 16 * 4 + 4 * n)
-        achieved = (per_solve_bytes / L) / avg_launch_s / 1e9 if g_n else None
-        peak, peak_kind = load_peaks()
         # e2e: host buffers, copies inside the timed region
         b_host = torch.from_numpy(b_np).pin_memory()
         x_host = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -312,42 +486,55 @@ def run_ours(args, wl):
             e1.record(stream)
             e1.synchronize()
             e2e_times.append(e0.elapsed_time(e1) / 1e3)
+        e2e_max, _ = aggregate(statistics.mean(e2e_times), 1.0, dev)
         # bf16 hidden block form of the same trained GNP
         gnp.gnp_set_hprec(M, gnp.H_BF16)
         for _ in range(max(1, args.warmup)):
             solve()
         btimes, binfos = timed_solves(args.steps)
         gnp.gnp_set_hprec(M, gnp.H_FP32)
+        # FGMRES without a preconditioner (M = I), for context
+        solve(None)
+        itimes, iinfos = timed_solves(args.steps, None)
+        clocks = clocks_stop(clk, clkf, local) if rank == 0 else None
+        # roofline of the step's dominant kernel, on its own
+        roof = layer_roofline(gnp, M, n, nnz, 4, stream, None, peak, peak_kind, 200, args.workload,
+                              gconv_kernel_name(A), "fp32")
+        c3 = c3_block(gnp, stream, flush, peak, peak_kind, 10) if (rank == 0 and not args.no_c3) else None
+        c4 = (c4_block(gnp, stream, peak, peak_kind, 50,
+                       0.0 if (args.no_cpu_baseline or ws > 1) else args.ref_seconds)
+              if (rank == 0 and not args.no_c4) else None)
     # kernel launches inside the timed region: per cycle m steps of (encode, which from
     # step 1 on also forms the basis vector and finishes the previous step; L Res-GCONV
     # with the decoder in the last; SpMV + CGS2 pass 1; pass 2) + the last step's finish
     # + x update + residual; per solve + norm and initial residual
     per_cycle = m * (L + 3) + 3
     launches = sum(i.cycles * per_cycle + 2 for i in infos)
+    cfg_out = base_config(wl, A)
+    cfg_out.update({"train_steps": train_steps, "l2": "flushed (256 MB write) before every timed solve",
+                    "parallelism": f"replicas{ws}"})
     line = {
-        "metric": "GNP-FGMRES time-to-rtol 1e-8 (s)", "value": t_max, "unit": "s",
+        "metric": METRIC, "value": t_max, "unit": "s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
-        "data": "synthetic",
-        "config": {"workload": wl["desc"], "n": n, "nnz": nnz, "L": L, "hidden": 16, "hprec": "fp32",
-                   "restart": m, "rtol": rtol, "train_steps": args.train_steps or wl["train_steps"],
-                   "batch": wl["batch"], "arnoldi_m": wl["arnoldi_m"], "x0": "zeros",
-                   "l2": "flushed (256 MB write) before every timed solve", "parallelism": f"replicas{ws}"},
+        "data": "synthetic", "config": cfg_out,
         "iters": info.iters, "status": info.status_name, "rel_res_true": rel_true,
-        "solves_per_s": ws / t_max,
-        "train": {"steps": args.train_steps or wl["train_steps"], "seconds": train_s, "best_loss": best},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": stored_traffic(args.workload),
-                     "kernel": gconv_kernel_name(A), "peak_kind": peak_kind,
-                     "bytes_per_launch": per_solve_bytes / L, "launches_timed": g_n,
-                     "avg_launch_us": avg_launch_s * 1e6},
-        "e2e": {"value": statistics.mean(e2e_times), "unit": "s", "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 8 * n},
+        "solves_per_s": solves_all / t_max,
+        "train": {"steps": train_steps, "seconds": train_s, "best_loss": best},
         "bf16": {"value": statistics.mean(btimes), "unit": "s", "iters": binfos[-1].iters,
-                 "status": binfos[-1].status_name},
+                 "status": binfos[-1].status_name, "rel_res_true": binfos[-1].rel_res_true},
+        "identity": {"value": statistics.mean(itimes), "unit": "s", "iters": iinfos[-1].iters,
+                     "status": iinfos[-1].status_name, "rel_res_true": iinfos[-1].rel_res_true},
+        "roofline": roof,
+        "e2e": {"value": e2e_max, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if c3 is not None:
+        line["c3"] = c3
+        line["roofline_c3"] = c3["roofline_fp32"]
+    if c4 is not None:
+        line["c4_train"] = c4
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         spi, nit = oracle_sample(A, b_np, L, m, seconds=args.ref_seconds)
         line["cpu_baseline"] = {"value": spi * info.iters, "unit": "s", "cores": os.cpu_count(),
@@ -357,8 +544,7 @@ def run_ours(args, wl):
                                           f"{info.iters} iterations"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+    replicas.shutdown()
 
 
 def main():
@@ -371,6 +557,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=None)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 2^20-row apply/roofline block")
+    ap.add_argument("--no-c4", action="store_true", help="skip the 64^3 training block")
     ap.add_argument("--clocks-log", default=None, help="also write the raw clock samples (CSV) here")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]

@@ -38,7 +38,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert "workload" in d["config"]
+    for key in ("workload", "n", "nnz", "hprec", "restart", "rtol"):
+        assert key in d["config"], key
+    assert d["scaled_by_iterations"] > 0 and d["extrapolated_from_iterations"] > 0
 
 
 def test_roofline_labels_and_stored_traffic():
@@ -50,7 +52,14 @@ def test_roofline_labels_and_stored_traffic():
     assert b.gconv_bytes(n, nnz, 4) == 4 * (n + 1) + 8 * nnz + 2 * 16 * 4 * n
     stored = json.load(open(os.path.join(ROOT, "profiles", "res_gconv_traffic.json")))
     for wl in ("convdiff256", "powerlaw1m"):
+        if wl not in stored:
+            assert b.stored_traffic(wl) is None
+            continue
         expect = stored[wl]["dram_bytes_per_launch"] if stored[wl]["source_hash"] == b.gconv_source_hash() else None
         assert b.stored_traffic(wl) == expect
     assert b.stored_traffic("no_such_workload") is None
     assert np.isfinite(b.load_peaks()[0])
+    # the apply's bytes: norm + encoder, L - 1 layers, the decoder-fused last layer
+    L, hb = 8, 4
+    expect = 16 * n + 16 * n * hb + (L - 1) * b.gconv_bytes(n, nnz, hb) + 4 * (n + 1) + 8 * nnz + 16 * n * hb + 4 * n
+    assert b.apply_bytes(n, nnz, L, hb) == expect
