@@ -13,6 +13,8 @@ One step = one complete solve.  Timed with CUDA events on the solve's stream aft
 L2 flush (a 256 MB write); W untimed warm-up solves first.  Also reported:
 * bf16 / identity: the bfloat16 hidden-block form of the same GNP and FGMRES without a
   preconditioner, time-to-rtol and the true relative residual of each;
+* transfer: a GNP trained with the same recipe on the 64 x 64 instance of the PDE and
+  applied unchanged to this matrix (context: the headline trains on this matrix);
 * roofline: the step's dominant kernel (the short-row Res-GCONV layer) launched on its
   own through gnp_layer_apply, R back-to-back launches between two CUDA events on the
   launching stream; at 65,536 rows its working set (11 MB) stays in the 129 MB L2, so
@@ -141,7 +143,7 @@ def gconv_source_hash():
     is used only while they are unchanged)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("gconv.cu", "common.cuh", "internal.h"):
+    for f in ("gconv.cu", "gconv_common.cuh", "common.cuh", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2406_00809_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -497,6 +499,28 @@ def run_ours(args, wl):
         solve(None)
         itimes, iinfos = timed_solves(args.steps, None)
         clocks = clocks_stop(clk, clkf, local) if rank == 0 else None
+        # the same recipe trained on the 64 x 64 instance of the PDE and applied unchanged here
+        # (the weights do not depend on n): context, the headline trains on this matrix
+        A64 = I.convdiff2d(64, 100.0)
+        Mt64 = gnp.mat_from_csr(A64)
+        M64 = gnp.gnp_create(Mt64, gnp.make_config(L=L, batch=wl["batch"], arnoldi_m=wl["arnoldi_m"], seed=0),
+                             I.init_weights(L, seed=0))
+        t0 = time.perf_counter()
+        gnp.gnp_train(M64, train_steps, stream=stream)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        Mx = gnp.gnp_create(Mt, gnp.make_config(L=L), gnp.gnp_get_weights(M64))
+        solve(Mx)
+        xtimes, xinfos = timed_solves(args.steps, Mx)
+        gnp.gnp_set_hprec(Mx, gnp.H_BF16)
+        solve(Mx)
+        xbtimes, xbinfos = timed_solves(args.steps, Mx)
+        transfer = {"trained_on": "2-D convection-diffusion 64x64 (n=4,096), same recipe", "train_s": t64,
+                    "value": statistics.mean(xtimes), "unit": "s", "iters": xinfos[-1].iters,
+                    "status": xinfos[-1].status_name, "rel_res_true": xinfos[-1].rel_res_true,
+                    "bf16": {"value": statistics.mean(xbtimes), "iters": xbinfos[-1].iters,
+                             "status": xbinfos[-1].status_name, "rel_res_true": xbinfos[-1].rel_res_true}}
+        del Mx, M64, Mt64
         # roofline of the step's dominant kernel, on its own
         roof = layer_roofline(gnp, M, n, nnz, 4, stream, None, peak, peak_kind, 200, args.workload,
                               gconv_kernel_name(A), "fp32")
@@ -525,6 +549,7 @@ def run_ours(args, wl):
                  "status": binfos[-1].status_name, "rel_res_true": binfos[-1].rel_res_true},
         "identity": {"value": statistics.mean(itimes), "unit": "s", "iters": iinfos[-1].iters,
                      "status": iinfos[-1].status_name, "rel_res_true": iinfos[-1].rel_res_true},
+        "transfer": transfer,
         "roofline": roof,
         "e2e": {"value": e2e_max, "unit": "s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": launches,

@@ -230,6 +230,22 @@ def gaussian(n: int, seed: int, batch: int | None = None) -> np.ndarray:
     return rng.standard_normal((n, batch))
 
 
+def rhs_set(A: CSR, k: int, seed: int) -> np.ndarray:
+    """k right-hand sides b = A x of different character, as columns of an [n, k] array:
+    x = 1 (r % 3 == 0), a smooth sine (r % 3 == 1), x ~ N(0, 1) with seed + r (otherwise)."""
+    n = A.n
+    cols = []
+    for r in range(k):
+        if r % 3 == 0:
+            x = np.ones(n)
+        elif r % 3 == 1:
+            x = np.sin(np.linspace(0, 3 * (r + 1), n))
+        else:
+            x = gaussian(n, seed=seed + r)
+        cols.append(spmv(A, x))
+    return np.stack(cols, axis=1)
+
+
 def spmv(A: CSR, x: np.ndarray) -> np.ndarray:
     """b = A x for building right-hand sides from a chosen solution (problem setup only)."""
     return A.to_scipy() @ x

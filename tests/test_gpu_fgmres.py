@@ -83,7 +83,7 @@ def test_identity_converges_and_status(gnp):
 @pytest.mark.parametrize("kind", ["poisson32", "convdiff32", "powerlaw"])
 def test_gnp_preconditioned_history_matches_oracle(gnp, kind):
     """Untrained (Gaussian-init) GNP: FGMRES runs a fixed budget of steps on GPU and in
-    the oracle.  The first 10 steps agree to 1e-4.  After that the untrained M gives
+    the oracle.  The first 10 steps agree to 1e-5.  After that the untrained M gives
     nearly collinear z_j whose new directions are of the size of float32 rounding, so
     the history is as sensitive as float32-level changes of the oracle's own z make it
     (on the power-law matrix one such change moves it by more than 100%); the GPU's
@@ -109,7 +109,7 @@ def test_gnp_preconditioned_history_matches_oracle(gnp, kind):
     assert info.status == ir["status"]
     assert info.iters == ir["iters"]
     h = np.asarray(ir["history"])
-    np.testing.assert_allclose(info.history[:11], h[:11], rtol=1e-4)
+    np.testing.assert_allclose(info.history[:11], h[:11], rtol=1e-5)
     # sensitivity of this solve to float32-level changes of z: float32 rounding and
     # relative noise of 1e-7 (four seeds) in the oracle's own M
     perturbed = [lambda v: M64(v).astype(np.float32).astype(np.float64)]

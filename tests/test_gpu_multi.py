@@ -3,14 +3,15 @@
 * M = identity: every system's residual history and solution equal the oracle's FGMRES
   on that system alone (1e-10), for k = 1..8 (padded to 2, 4, 8 internally), with systems
   that converge at different iterations, a zero right-hand side and a capped one.
-* M = GNP: each system converges like the single-system GPU solve with the same weights
-  (iteration counts within 20 % + 2: the k-system kernels sum each row's neighbours in
-  another order than the single-system short-row kernel, the float32 preconditioner output
-  rounds differently and the preconditioned iteration amplifies it; 147 against 131 has
-  been seen), the first steps' residuals agree to 1e-4, and the true residual of every
-  converged system meets rtol.
+* M = GNP (weights trained by the oracle, tests/golden/): every system's iteration count
+  lies within the spread that float32-level changes of the oracle's own z cause on that
+  system alone, +-2 (tests/golden/make_iteration_bands.py), and its true residual meets
+  rtol.
 * Bad arguments are rejected.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -29,19 +30,19 @@ def gnp():
     return g
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden_weights():
+    return np.load(os.path.join(GOLDEN, "gnp_convdiff64_weights.npy"))
+
+
+def golden_bands():
+    return json.load(open(os.path.join(GOLDEN, "gnp_iteration_bands.json")))
+
+
 def rhs_set(A, k, seed):
-    """k right-hand sides of different character: x = 1, smooth, random."""
-    n = A.n
-    cols = []
-    for r in range(k):
-        if r % 3 == 0:
-            x = np.ones(n)
-        elif r % 3 == 1:
-            x = np.sin(np.linspace(0, 3 * (r + 1), n))
-        else:
-            x = I.gaussian(n, seed=seed + r)
-        cols.append(I.spmv(A, x))
-    return np.stack(cols, axis=1)
+    return I.rhs_set(A, k, seed)
 
 
 @pytest.mark.parametrize("k", [1, 3, 4, 8])
@@ -107,27 +108,24 @@ def test_identity_zero_rhs_and_cap(gnp):
 
 
 @pytest.mark.parametrize("k", [2, 4, 8])
-def test_gnp_matches_single_system_solves(gnp, k):
+def test_gnp_iterations_within_oracle_band_per_system(gnp, k):
+    """Every system of a k-system GNP solve (oracle-trained weights, 64 x 64 problem,
+    FGMRES(20), rtol 1e-8) against the oracle's FGMRES on that system alone: the count
+    within the spread that float32-level changes of the oracle's z cause, +-2
+    (tests/golden/make_iteration_bands.py), and the true residual meets rtol."""
     import torch
-    A = I.convdiff2d(32, 100.0)
+    A = I.convdiff2d(64, 100.0)
     Mt = gnp.mat_from_csr(A)
-    M = gnp.gnp_create(Mt, gnp.make_config(L=4, batch=8, arnoldi_m=20), I.init_weights(4, seed=2))
-    gnp.gnp_train(M, 200)
-    B = rhs_set(A, k, 20)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=8), golden_weights())
+    B = I.rhs_set(A, 8, 20)[:, :k].copy()
     X = torch.zeros((A.n, k), dtype=torch.float64, device="cuda")
     infos = gnp.fgmres_solve_multi(Mt, torch.from_numpy(B).cuda(), X, M, restart=20, rtol=1e-8, maxiters=1500)
     As = A.to_scipy()
+    bands = golden_bands()
     for r in range(k):
-        x1 = torch.zeros(A.n, dtype=torch.float64, device="cuda")
-        i1 = gnp.fgmres_solve(Mt, torch.from_numpy(B[:, r].copy()).cuda(), x1, M, restart=20, rtol=1e-8,
-                              maxiters=1500)
-        assert i1.status == 0, (r, i1.status_name, i1.iters)
-        assert infos[r].status == i1.status, (r, infos[r].status_name)
-        # the k-system GNP kernels round in a different order (float32 z): the preconditioned
-        # iteration drifts like the single-system one under float32 perturbations
-        assert abs(infos[r].iters - i1.iters) <= 2 + 0.2 * i1.iters, (r, infos[r].iters, i1.iters)
-        h, h1 = infos[r].history, i1.history
-        np.testing.assert_allclose(h[:6], h1[:6], rtol=1e-4)
+        its = [v["iters"] for v in bands[f"convdiff64_rhs{r}"].values()]
+        assert infos[r].status == 0, (r, infos[r].status_name)
+        assert min(its) - 2 <= infos[r].iters <= max(its) + 2, (r, infos[r].iters, its)
         res = B[:, r] - As @ X[:, r].cpu().numpy()
         assert np.linalg.norm(res) <= 1e-8 * np.linalg.norm(B[:, r]) * (1 + 1e-6)
 
