@@ -247,8 +247,20 @@ int gnp_philox4x32_10(const unsigned* ctr_dev, unsigned key0, unsigned key1, int
 
 /* Solve A x = b by restarted FGMRES(restart) with right preconditioner M (NULL =
  * identity, i.e. plain GMRES), x0 = the incoming x_dev, tolerance rtol * ||b||_2,
- * at most maxiters Arnoldi steps (Algorithm 1; stopping rules in the oracle's
- * documentation).  b_dev, x_dev: device float64 [n].  The Krylov basis V
+ * at most maxiters Arnoldi steps (Algorithm 1).  Stopping rules:
+ *   - an iteration is one Arnoldi step (one application of M);
+ *   - within a cycle, the step whose Givens residual estimate |g_{j+1}| <= rtol ||b||
+ *     ends the cycle; so does the cycle's last step (restart) or maxiters;
+ *   - h_{j+1,j} <= 1e-14 ||A z_j|| (breakdown) keeps column j and ends the cycle;
+ *     a rotated diagonal <= 1e-14 ||A z_j|| (z_j in the span) drops column j;
+ *   - at the cycle's end x += Z y (y from the triangular system) and the true residual
+ *     r = b - A x is formed: ||r|| <= rtol ||b|| returns GNP_OK; otherwise the next
+ *     cycle starts from r, except that two consecutive cycles without a decrease of ||r||
+ *     give GNP_ERR_STAGNATION, three consecutive cycles whose estimate met rtol while
+ *     ||r|| did not give GNP_ERR_RESIDUAL_MISMATCH, a non-finite value GNP_ERR_NAN, and
+ *     maxiters reached GNP_ERR_NOT_CONVERGED;
+ *   - b = 0 returns x = 0 at once.
+ * b_dev, x_dev: device float64 [n].  The Krylov basis V
  * ([n*(restart+1)] float64), Z ([n*restart] float32) and the reduction scratch are
  * cached in A and grown on demand (this may allocate).  Synchronous: returns when
  * the solve has ended; `info` (may be NULL) receives the statistics.

@@ -394,7 +394,10 @@ int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, d
 // Float64 direction storage for the Jacobi / inner-GMRES preconditioners.
 int solver_ensure_zd(Solver* S, int m);
 
-// Host bookkeeping between cycles (the stopping rules of the oracle's documentation).
+// Host bookkeeping between cycles: the stopping rules stated with fgmres_solve in gnp.h
+// (true residual at rtol -> OK; two consecutive cycles without decrease -> STAGNATION;
+// three consecutive cycles whose estimate met rtol but not the true residual ->
+// RESIDUAL_MISMATCH; non-finite -> NAN; maxiters -> NOT_CONVERGED).
 struct CycleCtl {
   int stagn = 0, mism = 0, restarts = 0, cycles = 0;
 };

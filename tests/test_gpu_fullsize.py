@@ -91,3 +91,25 @@ def test_apply_and_sampled_layer_powerlaw1m(gnp):
         agg = Ahat.data[s:e] @ H0[Ahat.indices[s:e]]
         ref = np.maximum(H0[i] @ U + agg @ W, 0.0)
         assert np.linalg.norm(H1[i] - ref) <= 1e-5 * max(np.linalg.norm(ref), 1e-3), i
+
+
+def test_apply_bf16_powerlaw1m(gnp):
+    """The bfloat16 hidden block on the 2^20-row power-law matrix: within 2e-2 of the
+    float64 oracle, and much closer to the oracle's bfloat16-store emulation (reading c18),
+    which rounds the same stored blocks."""
+    import torch
+    A, _ = I.workload("powerlaw1m")
+    L = 8
+    blob = I.init_weights(L, seed=4)
+    Mt = gnp.mat_from_csr(A)
+    M = gnp.gnp_create(Mt, gnp.make_config(L=L, hprec=1), blob)
+    v = I.gaussian(A.n, seed=11)
+    z = torch.empty(A.n, dtype=torch.float32, device="cuda")
+    gnp.gnp_apply(M, torch.from_numpy(v).cuda(), z)
+    zg = z.cpu().numpy().astype(np.float64)
+    Ahat = G.normalise(A.to_scipy())
+    P = G.unpack(blob, L)
+    z64 = G.forward(Ahat, v, P, 0)
+    zb = G.forward(Ahat, v, P, 0, hstore="bf16")
+    assert rel(zg, z64) <= 2e-2, rel(zg, z64)
+    assert rel(zg, zb) <= 0.25 * rel(zg, z64), (rel(zg, zb), rel(zg, z64))
