@@ -572,13 +572,66 @@ def run_ours(args, wl):
     replicas.shutdown()
 
 
+def run_serve(args):
+    """--workload serve: the continuous-batching server under a Poisson stream of solve
+    requests (paper_2406_00809_gb300.serve_bench): a pool of 12 problems (2-D Poisson,
+    2-D convection-diffusion, power-law general sparse in turn; n log-uniform in [1e4, 2e6]),
+    each with its own GNP trained on its own matrix for a stated budget of Adam steps and
+    applied with a bfloat16 hidden block; `serve_requests` requests per rate, FGMRES(30) to
+    rtol 1e-8, at most 1000 iterations; rates at the given multiples of the sequential
+    capacity (1 / mean latency of each pool problem solved alone).  One JSON line: value =
+    p99 latency at the first rate; every rate's p50/p99, solves/s and status counts."""
+    import torch
+    from paper_2406_00809_gb300 import build
+    from paper_2406_00809_gb300 import serve_bench as SB
+    ws, rank, local = replicas.env()
+    torch.cuda.set_device(local)
+    build.build()
+    from paper_2406_00809_gb300 import gnp as g
+    sa = argparse.Namespace(requests=args.serve_requests, pool=12, nmin=1e4, nmax=2e6,
+                            train_steps=args.serve_train_steps, batch=8, hprec="bf16", rtol=1e-8,
+                            maxiters=1000, max_active=64, max_gb=120.0, seed=0)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    pool = SB.build_pool(g, sa, rng)
+    setup_s = time.perf_counter() - t0
+    srv = g.Server(max_bytes=int(sa.max_gb * (1 << 30)), max_active=sa.max_active, restart=30)
+    solo = SB.solo_latencies(g, srv, pool, sa)
+    capacity = 1.0 / float(np.mean([s_["seconds"] for s_ in solo]))
+    clk, clkf = clocks_start(args.clocks_log) if rank == 0 else (None, None)
+    rates = []
+    for i, load in enumerate(float(r) for r in args.serve_loads.split(",")):
+        out = SB.run_rate(g, srv, pool, sa, load * capacity, 1 + i)
+        out["load"] = load
+        rates.append(out)
+    clocks = clocks_stop(clk, clkf, local) if rank == 0 else None
+    srv.close()
+    first = rates[0]
+    line = {"metric": "serve p99 latency (s)", "value": first["p99_s"], "unit": "s", "n_gpus": ws,
+            "steps": len(rates), "warmup": 1, "ms_per_step": first["p99_s"] * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic",
+            "config": {"workload": "serving: Poisson stream of solve requests, 12-problem pool over 2-D Poisson, "
+                                   "2-D convection-diffusion and power-law general sparse, n log-uniform in "
+                                   "[1e4, 2e6], own GNP per problem (bfloat16 hidden), FGMRES(30) to 1e-8",
+                       "requests_per_rate": sa.requests, "loads": args.serve_loads,
+                       "train_steps_per_problem": sa.train_steps, "maxiters": sa.maxiters,
+                       "parallelism": f"replicas{ws}"},
+            "pool": [{k: p[k] for k in ("fam", "n", "nnz", "train_s")} for p in pool], "setup_s": setup_s,
+            "solo": solo, "sequential_capacity_per_s": capacity, "rates": rates, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="convdiff256")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["serve"], default="convdiff256")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-loads", default="1,2,4", help="arrival rates as multiples of the sequential capacity")
+    ap.add_argument("--serve-train-steps", type=int, default=500)
     ap.add_argument("--train-steps", type=int, default=None)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -586,6 +639,13 @@ def main():
     ap.add_argument("--no-c4", action="store_true", help="skip the 64^3 training block")
     ap.add_argument("--clocks-log", default=None, help="also write the raw clock samples (CSV) here")
     args = ap.parse_args()
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving stream has no oracle counterpart: "
+                                                                  "the oracle is a single-solve CPU program"}))
+            return
+        run_serve(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

@@ -110,14 +110,20 @@ def run_rate(g, srv, pool, args, rate, seed):
     lat = np.array([res.seconds for res in results])
     its = np.array([res.iters for res in results])
     status = {}
-    for res in results:
+    by_family = {}
+    for k, res in zip(picks, results):
         status[res.status_name] = status.get(res.status_name, 0) + 1
+        fam = by_family.setdefault(pool[k]["fam"], {})
+        fam[res.status_name] = fam.get(res.status_name, 0) + 1
+    ok = np.array([res.status_name == "GNP_OK" for res in results])
     st = srv.stats()
     return {"rate_per_s": rate, "requests": args.requests, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
             "solves_per_s": args.requests / (t_end - t_start), "iters_mean": float(its.mean()),
-            "iters_max": int(its.max()), "status": status, "max_active_seen": st["max_active_seen"],
-            "rounds": st["rounds"]}
+            "iters_max": int(its.max()), "status": status, "status_by_family": by_family,
+            "p50_s_converged": float(np.percentile(lat[ok], 50)) if ok.any() else None,
+            "p99_s_converged": float(np.percentile(lat[ok], 99)) if ok.any() else None,
+            "max_active_seen": st["max_active_seen"], "rounds": st["rounds"]}
 
 
 def solo_latencies(g, srv, pool, args):
