@@ -599,11 +599,15 @@ struct RowSmem {
 
 // Gather into shared memory: part p of h_i and of (A_hat H)_i for the block's rows.
 // Before the call the caller has loaded rs / deg / c / v (first DB entries) of its row.
-template <class HT, int LPR, int DB>
+//
+// K systems at once (K > 1): r is the pair (node r / K, system r % K) of an [n K, 16]
+// hidden block, the CSR row is the node's and neighbour c of the pair is row c K + s.
+template <class HT, int LPR, int DB, int K = 1>
 __device__ __forceinline__ void row_gather(RowSmem<LPR>& sm, const int* __restrict__ col,
                                            const float* __restrict__ valhat, const HT* __restrict__ Hin,
                                            int r, int gr, int p, int rs, int deg, const int (&c0)[DB],
                                            const float (&v0)[DB]) {
+  const int sys = K > 1 ? r % K : 0;
   using RT = RowTraits<HT, LPR>;
   constexpr int PW = RT::PW;
   float acc[PW], hv[PW];
@@ -614,7 +618,7 @@ __device__ __forceinline__ void row_gather(RowSmem<LPR>& sm, const int* __restri
     float x[DB][PW];
 #pragma unroll
     for (int k = 0; k < DB; ++k)
-      if (k < deg) RT::load(Hin, c0[k], p, x[k]);
+      if (k < deg) RT::load(Hin, c0[k] * K + sys, p, x[k]);
 #pragma unroll
     for (int k = 0; k < DB; ++k)
       if (k < deg) {
@@ -631,7 +635,7 @@ __device__ __forceinline__ void row_gather(RowSmem<LPR>& sm, const int* __restri
       }
 #pragma unroll
       for (int k = 0; k < DB; ++k)
-        if (e0 + k < deg) RT::load(Hin, c[k], p, x[k]);
+        if (e0 + k < deg) RT::load(Hin, c[k] * K + sys, p, x[k]);
 #pragma unroll
       for (int k = 0; k < DB; ++k)
         if (e0 + k < deg) {
@@ -650,15 +654,17 @@ __device__ __forceinline__ void row_gather(RowSmem<LPR>& sm, const int* __restri
 }
 
 // Row pointers and the first DB column indices / values of this lane's row.
-template <int DB>
+// (K > 1: r is a pair of the K-system block and n the number of pairs; the row is node r / K.)
+template <int DB, int K = 1>
 __device__ __forceinline__ void row_prefetch(const int* __restrict__ rp, const int* __restrict__ col,
                                              const float* __restrict__ valhat, int r, int n, int& rs,
                                              int& deg, int (&c)[DB], float (&v)[DB]) {
   rs = 0;
   deg = -1;  // no row
   if (r < n) {
-    rs = __ldg(rp + r);
-    deg = __ldg(rp + r + 1) - rs;
+    const int node = K > 1 ? r / K : r;
+    rs = __ldg(rp + node);
+    deg = __ldg(rp + node + 1) - rs;
   }
 #pragma unroll
   for (int k = 0; k < DB; ++k) {
@@ -736,7 +742,7 @@ __device__ __forceinline__ void row_layer_q(const RowSmem<LPR>& sm, int er, int 
 // measured slower.
 template <int LPR> struct RowBounds { static constexpr int MIN_BLOCKS = 1; };
 
-template <class HT, int FORM, int LPR, int DB>
+template <class HT, int FORM, int LPR, int DB, int K = 1>
 __global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
 k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
             const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
@@ -748,10 +754,10 @@ k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float
   const int gr = t / LPR, p = t % LPR;
   int rs, deg, c[DB];
   float v[DB];
-  row_prefetch<DB>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
+  row_prefetch<DB, K>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
   pdl_wait();
   if (ctl && !ctl[1]) return;
-  row_gather<HT, LPR, DB>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
+  row_gather<HT, LPR, DB, K>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
   __syncthreads();
   const int er = t % RB, q = t / RB;
   float o[16 / LPR];
@@ -760,7 +766,7 @@ k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float
   if (r0 + er < n) RowTraits<HT, LPR>::store(Hout, r0 + er, q, o);
 }
 
-template <class HT, int FORM, int LPR, int DB>
+template <class HT, int FORM, int LPR, int DB, int K = 1>
 __global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
 k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
                 const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
@@ -773,7 +779,7 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
   const int gr = t / LPR, p = t % LPR;
   int rs, deg, c[DB];
   float v[DB];
-  row_prefetch<DB>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
+  row_prefetch<DB, K>(rp, col, valhat, r0 + gr, n, rs, deg, c, v);
   pdl_wait();
   if (ctl && !ctl[1]) return;
   __shared__ float s_back;
@@ -781,7 +787,7 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
     const double tv = *tau;
     s_back = (float)(tv > 0.0 ? tv / sqrt_n : 0.0);
   }
-  row_gather<HT, LPR, DB>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
+  row_gather<HT, LPR, DB, K>(sm, col, valhat, Hin, r0 + gr, gr, p, rs, deg, c, v);
   __syncthreads();
   const int er = t % RB, q = t / RB;
   const bool valid = r0 + er < n;
@@ -1051,6 +1057,54 @@ static int row_kernel_mode(const gnp_mat* A) {
   const int forced = env_int("GNP_ROW_DB", 0);
   const int db = forced == 4 || forced == 5 ? forced : (A->max_deg <= 4 ? 4 : 5);
   return (env_int("GNP_ROW_LPR", 4) == 2 ? 20 : 40) + db;
+}
+
+// The L layers of the K-system GNP (multi-right-hand-side FGMRES) on the short-row
+// kernels: the [n K, 16] float32 hidden block is a one-system block over n K pairs whose
+// pair (i, s) gathers pairs (c, s); the last layer applies the decoder and writes
+// z = column zp (pairs in node-major order), scaled by *tau_one / sqrt(n) = 1 / sqrt(n).
+template <int FORM, int K>
+static int multi_row_layers_k(gnp_model* M, float* H0, float* H1, ColPtr zp, const double* tau_one,
+                              const int* ctl, cudaStream_t st) {
+  const gnp_mat* A = M->A;
+  const int L = M->cfg.L;
+  const int np = A->n * K;
+  constexpr int LPR = 4, DB = 5;
+  constexpr int RB = TILE / LPR;
+  const int nb = (np + RB - 1) / RB;
+  const double sqrt_n = std::sqrt((double)A->n);
+  for (int l = 0; l < L - 1; ++l) {
+    LayerWT lw;
+    fill_layer_wt(M->w_host, l, lw);
+    GNP_TRY_CUDA(launch_pdl(k_gconv_row<float, FORM, LPR, DB, K>, nb, 0, st, A->rp, A->col,
+                            (const float*)M->valhat, (const float*)H0, H1, np, ctl, lw));
+    std::swap(H0, H1);
+  }
+  LayerWT lw;
+  fill_layer_wt(M->w_host, L - 1, lw);
+  DecWT dwt;
+  fill_dec_wt(M->w_host, L, dwt);
+  GNP_TRY_CUDA(launch_pdl(k_gconv_row_dec<float, FORM, LPR, DB, K>, nb, 0, st, A->rp, A->col,
+                          (const float*)M->valhat, (const float*)H0, zp, tau_one, sqrt_n, np, ctl, lw, dwt));
+  return GNP_OK;
+}
+
+bool multi_row_ok(const gnp_model* M) { return M->cfg.L >= 1 && row_kernel_mode(M->A) != 0; }
+
+int multi_row_layers(gnp_model* M, int K, float* H0, float* H1, ColPtr zp, const double* tau_one, const int* ctl,
+                     cudaStream_t st) {
+  const bool paper = M->cfg.form == GNP_LAYER_PAPER;
+  switch (K) {
+    case 2: return paper ? multi_row_layers_k<GNP_LAYER_PAPER, 2>(M, H0, H1, zp, tau_one, ctl, st)
+                         : multi_row_layers_k<GNP_LAYER_RESID, 2>(M, H0, H1, zp, tau_one, ctl, st);
+    case 4: return paper ? multi_row_layers_k<GNP_LAYER_PAPER, 4>(M, H0, H1, zp, tau_one, ctl, st)
+                         : multi_row_layers_k<GNP_LAYER_RESID, 4>(M, H0, H1, zp, tau_one, ctl, st);
+    case 8: return paper ? multi_row_layers_k<GNP_LAYER_PAPER, 8>(M, H0, H1, zp, tau_one, ctl, st)
+                         : multi_row_layers_k<GNP_LAYER_RESID, 8>(M, H0, H1, zp, tau_one, ctl, st);
+    default:
+      set_error("multi_row_layers: K = %d", K);
+      return GNP_ERR_INVALID_ARG;
+  }
 }
 
 // One Res-GCONV layer l on caller buffers, with the kernel the apply runs for its

@@ -114,6 +114,12 @@ void fill_layer_w(const std::vector<float>& w, int l, LayerW& lw);
 void fill_layer_wt(const std::vector<float>& w, int l, LayerWT& lw);
 void fill_dec_wt(const std::vector<float>& w, int L, DecWT& dw);
 
+// The L Res-GCONV layers of a K-system GNP on the short-row kernels (multi-right-hand-side
+// FGMRES), when multi_row_ok(M): hidden blocks [n K, 16] float32, z = column zp ([n][K]).
+bool multi_row_ok(const gnp_model* M);
+int multi_row_layers(gnp_model* M, int K, float* H0, float* H1, ColPtr zp, const double* tau_one, const int* ctl,
+                     cudaStream_t st);
+
 // Make the host copy of the weights current (after training).
 int model_sync_host(gnp_model* M);
 // Everything apply_launch needs that is not a stream operation (host weights, kernel

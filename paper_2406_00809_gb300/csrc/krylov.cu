@@ -73,7 +73,7 @@ void solver_free(Solver* s) {
 }
 
 size_t solver_bytes(int n, int m, int maxiters) {
-  const size_t maxb = (size_t)std::max(red_blocks(n), (n + TILE - 1) / TILE);
+  const size_t maxb = (size_t)std::max(4 * NUM_SMS_GB300, (n + TILE - 1) / TILE);
   return (size_t)n * (m + 1) * 8 + (size_t)n * m * 4 + (size_t)n * 8 + sizeof(DevState) +
          (size_t)(m + 1) * m * 8 * 2 + (size_t)(4 * m + 8) * 8 + (size_t)(maxiters + 1) * 16 +
          maxb * (m + 2) * 8 + 8;
@@ -113,7 +113,7 @@ int solver_create(int n, int m, int maxiters, Solver** out) {
     if ((e = dev_alloc(&s->h2, (size_t)m + 2)) != GNP_OK) break;
     if ((e = dev_alloc(&s->hist, (size_t)maxiters + 1)) != GNP_OK) break;
     if ((e = dev_alloc(&s->thist, (size_t)maxiters + 1)) != GNP_OK) break;
-    const int maxb = std::max(red_blocks(n), (n + TILE - 1) / TILE);
+    const int maxb = std::max(4 * NUM_SMS_GB300, (n + TILE - 1) / TILE);  // >= dot_blocks(n)
     if ((e = red_alloc(s->red, maxb, m + 2)) != GNP_OK) break;
     if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) {
       set_error("cudaStreamCreate failed");

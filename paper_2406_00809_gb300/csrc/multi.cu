@@ -11,9 +11,13 @@
 // device memory, so one captured CUDA graph replays a whole restart cycle):
 //   k_mencode, (L-1) x k_mgconv, k_mgconv_dec   z_r = M(v_r) for every active system
 //   (M = I: k_mvscale only normalises v_r)
-//   k_mspmv       w_r = A z_r (one tile gather for all systems)
-//   k_mcgs<1..3>  CGS2 per system; the last block of pass 3 runs the Givens update of
-//                 every active system (one thread per system) and the cycle decision.
+//   k_mspmv       w_r = A z_r (one tile gather for all systems) and CGS2 pass 1
+//                 (h1 = V^T w_r, ||w_r||^2)
+//   k_mcgs<2>     pass 2 (w1 = w - V h1, h2 = V^T w1, ||w1||^2); its last block forms
+//                 h_{j+1,j} = sqrt(||w1||^2 - ||h2||^2) (reading c29) and runs the Givens
+//                 update of every active system (one thread per system) and the cycle
+//                 decision
+//   k_mcgs<3>     column j+1 = w1 - V h2 (no reduction)
 // Cycle end: k_mxupdate (y_r = R_r^{-1} g_r, x_r += Z y_r) and k_mresidual (r = b - A x,
 // beta_r, restart).  A system whose cycle ended early waits, inactive, for the others;
 // its iterates and counts are those of a solve on its own.
@@ -21,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "gconv_common.cuh"
 #include "solver.h"
 
 namespace gnp {
@@ -37,7 +42,8 @@ struct MultiSolver {
   float* Hg[2] = {nullptr, nullptr};  // GNP hidden blocks [n K 16]
   DevState* st = nullptr;       // [K]
   DevState* st_host = nullptr;  // pinned [K]
-  int* ctl = nullptr;           // {j, any system active}
+  int* ctl = nullptr;           // {j, any system active, j of the column k_mcgs<K, 3> forms}
+  double* one = nullptr;        // device 1.0: tau of the unit-norm basis vectors
   int* done = nullptr;          // [K] device flags: system finished
   int* done_host = nullptr;     // pinned [K]
   double* H = nullptr;   // [K][(m+1) m]
@@ -225,7 +231,7 @@ k_mgconv(const int* __restrict__ rp, const int* __restrict__ col, const float* _
   tile_load_rp<TR>(sm.g, rp, r0, rows);
   mtile_copy<false>(sm.stile, const_cast<float*>(Hin) + (size_t)r0 * K * 16, rows * K);
   __syncthreads();
-  tile_gather<TR>(sm.g, rows, col, valhat, Hin);
+  tile_gather<TR, TileSmem<TrHidM<K>, ROWS>, 8>(sm.g, rows, col, valhat, Hin);  // 8 rows in flight per lane
   __syncthreads();
   const int t = threadIdx.x;  // pair (row t / K, system t % K)
   const int row = t / K, sys = t % K;
@@ -239,18 +245,19 @@ k_mgconv(const int* __restrict__ rp, const int* __restrict__ col, const float* _
       h[4 * q] = v.x; h[4 * q + 1] = v.y; h[4 * q + 2] = v.z; h[4 * q + 3] = v.w;
     }
     tile_row_sum<TR, 16>(sm.g, row, 16 * sys, agg);
+    // two outputs per paired multiply-add (each lane an fmaf, inputs in order)
 #pragma unroll
     for (int k = 0; k < 16; ++k) o[k] = 0.0f;
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) o[k] = fmaf(agg[c], lw.W[c * 16 + k], o[k]);
+      for (int k = 0; k < 16; k += 2) ffma2(o[k], o[k + 1], agg[c], agg[c], lw.W[c * 16 + k], lw.W[c * 16 + k + 1]);
     }
     if (FORM == GNP_LAYER_PAPER) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) o[k] = fmaf(h[c], lw.U[c * 16 + k], o[k]);
+        for (int k = 0; k < 16; k += 2) ffma2(o[k], o[k + 1], h[c], h[c], lw.U[c * 16 + k], lw.U[c * 16 + k + 1]);
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) o[k] = fmaxf(o[k], 0.0f);
@@ -286,15 +293,21 @@ k_mgconv(const int* __restrict__ rp, const int* __restrict__ col, const float* _
 
 // ---------------------------------------------------------------- SpMV, residual
 
-// w = A z for the K systems; z is column j of Z (float32) or of V (float64).
-template <int K, class XT>
+// w = A z for the K systems; z is column j of Z (float32) or of V (float64).  With DOTS
+// the kernel is also CGS2 pass 1: h1 = V_j^T w and ||w||^2 per system, each block adding
+// its own rows' products (KC per register chunk, a fixed-order block reduction) and the
+// last block the blocks' partials in order.
+template <int K, class XT, bool DOTS>
 __global__ void __launch_bounds__(TILE)
 k_mspmv(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-        const XT* __restrict__ Xbase, double* __restrict__ w, int n, const int* __restrict__ ctl) {
+        const XT* __restrict__ Xbase, double* __restrict__ w, int n, const int* __restrict__ ctl,
+        const double* __restrict__ V, DevState* st, double* __restrict__ h1, double* __restrict__ partials,
+        unsigned* counter) {
   using TR = TrSpmvM<K, XT>;
   if (!ctl[1]) return;
   __shared__ TileSmem<TR, MROWS> sm;
-  const XT* x = Xbase + (size_t)mstep(ctl) * n * K;
+  const int j = mstep(ctl);
+  const XT* x = Xbase + (size_t)j * n * K;
   const int r0 = blockIdx.x * MROWS;
   const int rows = min(MROWS, n - r0);
   tile_load_rp<TR>(sm, rp, r0, rows);
@@ -302,12 +315,50 @@ k_mspmv(const int* __restrict__ rp, const int* __restrict__ col, const double* _
   tile_gather<TR>(sm, rows, col, val, x);
   __syncthreads();
   const int t = threadIdx.x;
+  double s[K];
+#pragma unroll
+  for (int r = 0; r < K; ++r) s[r] = 0.0;
   if (t < rows) {
-    double s[K];
     tile_row_sum<TR, K>(sm, t, 0, s);
     double2* wo = reinterpret_cast<double2*>(w + (size_t)(r0 + t) * K);
 #pragma unroll
     for (int u = 0; u < K / 2; ++u) wo[u] = make_double2(s[2 * u], s[2 * u + 1]);
+  }
+  if constexpr (DOTS) {
+    constexpr int CC = KC / K;  // columns per reduction
+    __shared__ double sred[RED_SH];
+    __shared__ double shtot[(GNP_MAX_RESTART_MULTI + 2) * K];
+    const int Kc = j + 2;  // V_j^T w and, as column j+1, ||w||^2
+    for (int c0 = 0; c0 < Kc; c0 += CC) {
+      double a[KC];
+#pragma unroll
+      for (int k = 0; k < KC; ++k) a[k] = 0.0;
+      if (t < rows) {
+        const size_t i = (size_t)(r0 + t);
+#pragma unroll
+        for (int cl = 0; cl < CC; ++cl) {
+          const int c = c0 + cl;
+          if (c == j + 1) {
+#pragma unroll
+            for (int r = 0; r < K; ++r) a[cl * K + r] = s[r] * s[r];
+          } else if (c <= j) {
+            const double2* vp = reinterpret_cast<const double2*>(V + ((size_t)c * n + i) * K);
+#pragma unroll
+            for (int u = 0; u < K / 2; ++u) {
+              const double2 vv = vp[u];
+              a[cl * K + 2 * u] = vv.x * s[2 * u];
+              a[cl * K + 2 * u + 1] = vv.y * s[2 * u + 1];
+            }
+          }
+        }
+      }
+      block_reduce_kc<false>(a, sred, partials + (size_t)blockIdx.x * Kc * K + c0 * K, min(KC, (Kc - c0) * K));
+    }
+    if (!last_block_arrive(counter)) return;
+    reduce_partials(partials, gridDim.x, Kc * K, shtot);
+    for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h1[k] = shtot[k];
+    if (threadIdx.x < K && st[threadIdx.x].active) st[threadIdx.x].wnorm0 = sqrt(shtot[(j + 1) * K + threadIdx.x]);
+    if (threadIdx.x == 0) *counter = 0;
   }
 }
 
@@ -413,22 +464,116 @@ __device__ __forceinline__ void mdots(const double* __restrict__ V, const double
   }
 }
 
-// PASS 1: h1 = V_j^T w and ||w||^2.  PASS 2: w1 = w - V_j h1 (in place), h2 = V_j^T w1.
-// PASS 3: w2 = w1 - V_j h2 -> column j+1, ||w2||; its last block finishes the step of
-// every active system (arnoldi_step_finish, one thread per system).
+// k_mspmv for matrices whose rows are short (at most ROW_DMAX_M nonzeros): one thread per
+// row forms its K sums with eight nonzeros' loads in flight (four at K = 8; no tile),
+// then the pass-1 dots run over the same grid-stride rows (mdots re-reads only the w this
+// thread wrote).
+constexpr int ROW_DMAX_M = 16;
+
+template <int K, class XT>
+__device__ __forceinline__ void mload_k(const XT* __restrict__ x, int c, double (&h)[K]) {
+  const XT* p = x + (size_t)c * K;
+  if constexpr (sizeof(XT) == 8) {
+#pragma unroll
+    for (int u = 0; u < K / 2; ++u) {
+      const double2 t = __ldg(reinterpret_cast<const double2*>(p) + u);
+      h[2 * u] = t.x;
+      h[2 * u + 1] = t.y;
+    }
+  } else if constexpr (K == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    h[0] = t.x;
+    h[1] = t.y;
+  } else {
+#pragma unroll
+    for (int u = 0; u < K / 4; ++u) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + u);
+      h[4 * u] = t.x; h[4 * u + 1] = t.y; h[4 * u + 2] = t.z; h[4 * u + 3] = t.w;
+    }
+  }
+}
+
+template <int K, class XT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_mspmv_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+            const XT* __restrict__ Xbase, double* __restrict__ w, int n, const int* __restrict__ ctl,
+            const double* __restrict__ V, DevState* st, double* __restrict__ h1, double* __restrict__ partials,
+            unsigned* counter) {
+  if (!ctl[1]) return;
+  constexpr int CC = KC / K;
+  constexpr int NF = K >= 8 ? 4 : 8;  // nonzeros in flight (registers: NF x K doubles)
+  __shared__ double sred[RED_SH];
+  __shared__ double shtot[(GNP_MAX_RESTART_MULTI + 2) * K];
+  const int j = mstep(ctl);
+  const XT* x = Xbase + (size_t)j * n * K;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gstride = gridDim.x * blockDim.x;
+  for (int i = gtid; i < n; i += gstride) {
+    const int rs = __ldg(rp + i), re = __ldg(rp + i + 1);
+    double s[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) s[r] = 0.0;
+    for (int e0 = rs; e0 < re; e0 += NF) {  // NF nonzeros' loads in flight, added in order
+      int c[NF];
+      double v[NF];
+#pragma unroll
+      for (int u = 0; u < NF; ++u) {
+        const bool ok = e0 + u < re;
+        c[u] = ok ? __ldg(col + e0 + u) : 0;
+        v[u] = ok ? __ldg(val + e0 + u) : 0.0;
+      }
+      double xv[NF][K];
+#pragma unroll
+      for (int u = 0; u < NF; ++u)
+        if (e0 + u < re) mload_k<K, XT>(x, c[u], xv[u]);
+#pragma unroll
+      for (int u = 0; u < NF; ++u)
+        if (e0 + u < re) {
+#pragma unroll
+          for (int r = 0; r < K; ++r) s[r] = fma(v[u], xv[u][r], s[r]);
+        }
+    }
+    double2* wo = reinterpret_cast<double2*>(w + (size_t)i * K);
+#pragma unroll
+    for (int u = 0; u < K / 2; ++u) wo[u] = make_double2(s[2 * u], s[2 * u + 1]);
+  }
+  const int Kc = j + 2;  // V_j^T w and, as column j+1, ||w||^2
+  for (int c0 = 0; c0 < Kc; c0 += CC) {
+    double a[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) a[k] = 0.0;
+    mdots<K, CC>(V, w, n, j, c0, Kc, a);
+    block_reduce_kc<false>(a, sred, partials + (size_t)blockIdx.x * Kc * K + c0 * K, min(KC, (Kc - c0) * K));
+  }
+  if (!last_block_arrive(counter)) return;
+  reduce_partials(partials, gridDim.x, Kc * K, shtot);
+  for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h1[k] = shtot[k];
+  if (threadIdx.x < K && st[threadIdx.x].active) st[threadIdx.x].wnorm0 = sqrt(shtot[(j + 1) * K + threadIdx.x]);
+  if (threadIdx.x == 0) *counter = 0;
+}
+
+// (Pass 1, h1 = V_j^T w and ||w||^2, runs inside k_mspmv.)
+// PASS 2: w1 = w - V_j h1 (in place), h2 = V_j^T w1
+// and ||w1||^2; its last block finishes the step of every active system
+// (arnoldi_step_finish, one thread per system) with column j = h1 + h2 and
+// h_{j+1,j} = sqrt(||w1||^2 - ||h2||^2) (reading c29, as in the one-system solver: V has
+// orthonormal columns and h2 = V^T w1, so this equals ||w1 - V h2|| to rounding), and
+// advances the step.  PASS 3: column j+1 = w1 - V_j h2 (normalised by the next step's
+// first kernel, which divides by the system's vscale = h_{j+1,j}); no reduction.
 template <int K, int PASS>
 __global__ void __launch_bounds__(RED_THREADS)
 k_mcgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, int* ctl, double* __restrict__ h1,
        double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
        double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
        unsigned long long* __restrict__ thist, MStrides ms, double* __restrict__ partials, unsigned* counter) {
+  static_assert(PASS == 2 || PASS == 3, "pass 1 is fused into k_mspmv");
   constexpr int CC = KC / K;  // columns per reduction
   if (!ctl[1]) return;
   __shared__ double sred[RED_SH];
   __shared__ double shh[(GNP_MAX_RESTART_MULTI + 2) * K];
   __shared__ double shtot[(GNP_MAX_RESTART_MULTI + 2) * K];
   __shared__ int anyact;
-  const int j = mstep(ctl);
+  const int j = (PASS == 3) ? ctl[2] : mstep(ctl);  // pass 2 has advanced ctl[0] already
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gstride = gridDim.x * blockDim.x;
   if (PASS >= 2) {
@@ -450,46 +595,26 @@ k_mcgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, int*
       for (int r = 0; r < K; ++r) out[(size_t)i * K + r] = xv[r];
     }
   }
-  // dot products: PASS 1 over j+2 columns (with the norm), PASS 2 over j+1, PASS 3 the
-  // norm of the new column only
-  const double* y = (PASS == 3) ? V + (size_t)(j + 1) * n * K : w;
-  const int Kc = (PASS == 1) ? j + 2 : (PASS == 2 ? j + 1 : 1);
+  if (PASS == 3) return;  // the new column is formed; pass 2 finished the step
+  // dot products over j+2 "columns": V_j^T y and, as column j+1, ||y_r||^2
+  const double* y = w;
+  const int Kc = j + 2;
   for (int c0 = 0; c0 < Kc; c0 += CC) {
     double a[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) a[k] = 0.0;
-    if (PASS == 3) {
-      // the "column" is y itself: ||y_r||^2
-      for (int i = gtid; i < n; i += gstride) {
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-          const double v = y[(size_t)i * K + r];
-          a[r] += v * v;
-        }
-      }
-    } else {
-      mdots<K, CC>(V, y, n, (PASS == 1) ? j : -2, c0, Kc, a);
-    }
+    mdots<K, CC>(V, y, n, j, c0, Kc, a);
     block_reduce_kc<false>(a, sred, partials + (size_t)blockIdx.x * Kc * K + c0 * K, min(KC, (Kc - c0) * K));
   }
   if (!last_block_arrive(counter)) return;
   reduce_partials(partials, gridDim.x, Kc * K, shtot);
-  if (PASS == 1) {
-    for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h1[k] = shtot[k];
-    if (threadIdx.x < K && st[threadIdx.x].active) st[threadIdx.x].wnorm0 = sqrt(shtot[(j + 1) * K + threadIdx.x]);
-    if (threadIdx.x == 0) *counter = 0;
-    return;
-  }
-  if (PASS == 2) {
-    for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h2[k] = shtot[k];
-    if (threadIdx.x == 0) *counter = 0;
-    return;
-  }
-  // PASS 3: stage column j of every system (h1 + h2) in shared memory (reuse shh)
+  // PASS 2: h2 for pass 3; stage column j of every system (h1 + h2) in shared memory
+  // (reuse shh) and finish the step
+  for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h2[k] = shtot[k];
   __syncthreads();
   for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) {
     const int c = k / K, r = k % K;
-    shh[r * (GNP_MAX_RESTART_MULTI + 2) + c] = h1[k] + h2[k];
+    shh[r * (GNP_MAX_RESTART_MULTI + 2) + c] = h1[k] + shtot[k];
   }
   if (threadIdx.x == 0) anyact = 0;
   __syncthreads();
@@ -497,9 +622,12 @@ k_mcgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, int*
     const int r = threadIdx.x;
     DevState* s = st + r;
     if (s->active) {
+      double h2sq = 0.0;
+      for (int c = 0; c <= j; ++c) h2sq += shtot[c * K + r] * shtot[c * K + r];
+      const double hn = sqrt(fmax(shtot[(j + 1) * K + r] - h2sq, 0.0));
       double* csr = cs + (size_t)r * ms.ms;
       double* snr = sn + (size_t)r * ms.ms;
-      arnoldi_step_finish(s, j, shh + r * (GNP_MAX_RESTART_MULTI + 2), sqrt(shtot[r]), csr, snr,
+      arnoldi_step_finish(s, j, shh + r * (GNP_MAX_RESTART_MULTI + 2), hn, csr, snr,
                           H + (size_t)r * ms.hs, R + (size_t)r * ms.hs, csr, snr, g + (size_t)r * ms.gs,
                           hist + (size_t)r * ms.hist, thist + (size_t)r * ms.hist);
       if (s->active) atomicOr(&anyact, 1);
@@ -507,6 +635,7 @@ k_mcgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, int*
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    ctl[2] = j;
     ctl[0] = j + 1;
     ctl[1] = anyact;
     *counter = 0;
@@ -628,6 +757,7 @@ void multi_solver_free(MultiSolver* s) {
   dev_free(s->st);
   if (s->st_host) cudaFreeHost(s->st_host);
   dev_free(s->ctl);
+  dev_free(s->one);
   dev_free(s->done);
   if (s->done_host) cudaFreeHost(s->done_host);
   dev_free(s->H);
@@ -659,7 +789,16 @@ static int multi_create(int n, int K, int m, int maxiters, MultiSolver** out) {
     if ((e = dev_alloc(&s->Hg[0], nK * 16)) != GNP_OK) break;
     if ((e = dev_alloc(&s->Hg[1], nK * 16)) != GNP_OK) break;
     if ((e = dev_alloc(&s->st, (size_t)K)) != GNP_OK) break;
-    if ((e = dev_alloc(&s->ctl, 2)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->ctl, 3)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->one, 1)) != GNP_OK) break;
+    {
+      const double one = 1.0;
+      if (cudaMemcpy(s->one, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("multi_create: cudaMemcpy failed");
+        e = GNP_ERR_CUDA;
+        break;
+      }
+    }
     if ((e = dev_alloc(&s->done, (size_t)K)) != GNP_OK) break;
     if ((e = dev_alloc(&s->H, (size_t)K * (m + 1) * m)) != GNP_OK) break;
     if ((e = dev_alloc(&s->R, (size_t)K * (m + 1) * m)) != GNP_OK) break;
@@ -670,7 +809,7 @@ static int multi_create(int n, int K, int m, int maxiters, MultiSolver** out) {
     if ((e = dev_alloc(&s->h2, (size_t)K * (m + 2))) != GNP_OK) break;
     if ((e = dev_alloc(&s->hist, (size_t)K * (maxiters + 1))) != GNP_OK) break;
     if ((e = dev_alloc(&s->thist, (size_t)K * (maxiters + 1))) != GNP_OK) break;
-    const int maxb = std::max(red_blocks(n), (n + MROWS - 1) / MROWS);
+    const int maxb = std::max(4 * NUM_SMS_GB300, (n + MROWS - 1) / MROWS);  // >= dot_blocks(n)
     if ((e = red_alloc(s->red, maxb, (m + 2) * K)) != GNP_OK) break;
     if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMallocHost(reinterpret_cast<void**>(&s->st_host), sizeof(DevState) * K) != cudaSuccess ||
@@ -716,6 +855,11 @@ static void launch_mgnp(gnp_model* M, MultiSolver* S, cudaStream_t st) {
   fill_enc_dec(M->w_host, L, ew, dw);
   const int ne = (int)std::min<long long>(((long long)n * K + RED_THREADS - 1) / RED_THREADS, 8LL * NUM_SMS_GB300);
   k_mencode<K><<<ne, RED_THREADS, 0, st>>>(S->V, n, S->st, S->ctl, sqrt_n, S->Hg[0], ew);
+  if (multi_row_ok(M)) {  // rows of at most 16 nonzeros: the short-row kernels over n K pairs
+    const ColPtr zp{S->Z, sizeof(float) * (size_t)n * K, S->ctl, 0};
+    multi_row_layers(M, K, S->Hg[0], S->Hg[1], zp, S->one, S->ctl, st);  // launch errors: check_launch
+    return;
+  }
   const int smem = (int)sizeof(MGconvSmem<K>);
   const int nt = (n + MGconvSmem<K>::ROWS - 1) / MGconvSmem<K>::ROWS;
   float* H0 = S->Hg[0];
@@ -741,17 +885,27 @@ static int launch_mcycle(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cudaSt
   const int nb = red_blocks(n);
   const int ncg = dot_blocks(n);
   const MStrides ms = mstrides(S->m_cap, S->maxit_cap);
+  const bool short_rows = A->max_deg <= ROW_DMAX_M;
   for (int j = 0; j < m; ++j) {
+    // w = A z with CGS2 pass 1 (h1, ||w||^2) in the same kernel
     if (M) {
       if (M->cfg.form == GNP_LAYER_PAPER) launch_mgnp<K, GNP_LAYER_PAPER>(M, S, st);
       else launch_mgnp<K, GNP_LAYER_RESID>(M, S, st);
-      k_mspmv<K, float><<<ntr, TILE, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl);
+      if (short_rows)
+        k_mspmv_row<K, float><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl, S->V,
+                                                           S->st, S->h1, S->red.partials, S->red.counter);
+      else
+        k_mspmv<K, float, true><<<ntr, TILE, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl, S->V, S->st,
+                                                      S->h1, S->red.partials, S->red.counter);
     } else {
       k_mvscale<K><<<nb, RED_THREADS, 0, st>>>(S->V, n, S->st, S->ctl);
-      k_mspmv<K, double><<<ntr, TILE, 0, st>>>(A->rp, A->col, A->val, S->V, S->w, n, S->ctl);
+      if (short_rows)
+        k_mspmv_row<K, double><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, S->V, S->w, n, S->ctl, S->V,
+                                                            S->st, S->h1, S->red.partials, S->red.counter);
+      else
+        k_mspmv<K, double, true><<<ntr, TILE, 0, st>>>(A->rp, A->col, A->val, S->V, S->w, n, S->ctl, S->V,
+                                                       S->st, S->h1, S->red.partials, S->red.counter);
     }
-    k_mcgs<K, 1><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->ctl, S->h1, S->h2, S->H, S->R, S->cs,
-                                              S->sn, S->g, S->hist, S->thist, ms, S->red.partials, S->red.counter);
     k_mcgs<K, 2><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->ctl, S->h1, S->h2, S->H, S->R, S->cs,
                                               S->sn, S->g, S->hist, S->thist, ms, S->red.partials, S->red.counter);
     k_mcgs<K, 3><<<ncg, RED_THREADS, 0, st>>>(S->V, n, S->w, S->st, S->ctl, S->h1, S->h2, S->H, S->R, S->cs,

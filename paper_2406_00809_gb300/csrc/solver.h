@@ -50,14 +50,16 @@ constexpr double BREAKDOWN_REL = 1e-14;
 // systems) up to four per SM on larger ones.  The float64 pipes of all SMs share the
 // work evenly; a second block per SM hides part of the latency of the other's block
 // reduction (65,536 rows: 100.4 against 101.2 us per FGMRES step with one block per SM).
-// Never more than red_blocks(n), the capacity of the partial-sum scratch.
-// GNP_DOT_BLOCKS_PER_SM=1..4 in the environment forces the blocks per SM (for tuning).
+// Capped at red_blocks(n), one row per thread: a grid of whole blocks per SM instead
+// (304 blocks of 216 rows at 65,536 rows, not 256 of 256) measured slower, 92 against
+// 89 us per step.  GNP_DOT_BLOCKS_PER_SM=1..4 in the environment forces the blocks per SM
+// (for tuning).
 inline int dot_blocks(int n) {
   static const char* e = getenv("GNP_DOT_BLOCKS_PER_SM");
   static const int forced = e ? atoi(e) : 0;
   const int per = (n + NUM_SMS_GB300 * RED_THREADS - 1) / (NUM_SMS_GB300 * RED_THREADS);
   const int bps = (forced >= 1 && forced <= 4) ? forced : std::max(1, std::min(4, per));
-  return std::min(red_blocks(n), NUM_SMS_GB300 * bps);
+  return forced >= 1 && forced <= 4 ? NUM_SMS_GB300 * bps : std::min(red_blocks(n), NUM_SMS_GB300 * bps);
 }
 
 constexpr int KC = 8;  // basis columns per register chunk

@@ -587,11 +587,12 @@ k_dec_bwd(const float* __restrict__ HL, const float* __restrict__ dz, const doub
 
 // Layer backward, row part: Gp = G * 1[pre > 0] (pre recomputed from X and AGG exactly
 // as the forward did), Y = Gp W^T, local = Gp U^T (paper) or G (residual).  Four threads
-// per row, thread j owning entries 4j..4j+3 of every output: it forms those four
-// pre-activations from a 16 x 4 slice of W and of U, its quarter of Gp, gathers the other
-// three quarters of Gp from its quad with shuffles, and forms entries 4j..4j+3 of Y and
-// local from the same slices of W^T and U^T (kept transposed in shared memory, so every
-// 16-byte weight load of a quad is a broadcast without bank conflicts).
+// per row, thread j owning entries 4j..4j+3 of every output: it loads quarter j of the
+// AGG, X and G rows, takes the other quarters of AGG and X from its quad with shuffles,
+// forms its four pre-activations from a 16 x 4 slice of W and of U, its quarter of Gp,
+// gathers the other three quarters of Gp from its quad, and forms entries 4j..4j+3 of Y
+// and local from the same slices of W^T and U^T (kept transposed in shared memory, so
+// every 16-byte weight load of a quad is a broadcast without bank conflicts).
 template <int FORM>
 __global__ void __launch_bounds__(256)
 k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G,
@@ -616,29 +617,33 @@ k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, con
   const float4* U4 = reinterpret_cast<const float4*>(sU);
   const float4* Wt4 = reinterpret_cast<const float4*>(sWt);
   const float4* Ut4 = reinterpret_cast<const float4*>(sUt);
+  // each thread loads its own quarter of the AGG, X and G rows (one 16-byte load each,
+  // all in flight together) and takes the other quarters from its quad
+  const float4 a_own = __ldg(reinterpret_cast<const float4*>(AGG + r * 16) + j);
+  const float4 x_own = FORM == GNP_LAYER_PAPER ? __ldg(reinterpret_cast<const float4*>(X + r * 16) + j)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 g = __ldg(reinterpret_cast<const float4*>(G + r * 16) + j);
   float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
-  {
-    const float4* ap = reinterpret_cast<const float4*>(AGG + r * 16);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 v = __ldg(ap + q);
-      const float av[4] = {v.x, v.y, v.z, v.w};
+  for (int q = 0; q < 4; ++q) {
+    const float av[4] = {__shfl_sync(0xffffffffu, a_own.x, qbase + q), __shfl_sync(0xffffffffu, a_own.y, qbase + q),
+                         __shfl_sync(0xffffffffu, a_own.z, qbase + q), __shfl_sync(0xffffffffu, a_own.w, qbase + q)};
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float4 w = W4[(4 * q + e) * 4 + j];
-        pre.x = fmaf(av[e], w.x, pre.x);
-        pre.y = fmaf(av[e], w.y, pre.y);
-        pre.z = fmaf(av[e], w.z, pre.z);
-        pre.w = fmaf(av[e], w.w, pre.w);
-      }
+    for (int e = 0; e < 4; ++e) {
+      const float4 w = W4[(4 * q + e) * 4 + j];
+      pre.x = fmaf(av[e], w.x, pre.x);
+      pre.y = fmaf(av[e], w.y, pre.y);
+      pre.z = fmaf(av[e], w.z, pre.z);
+      pre.w = fmaf(av[e], w.w, pre.w);
     }
   }
   if (FORM == GNP_LAYER_PAPER) {
-    const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float4 v = __ldg(xp + q);
-      const float xv[4] = {v.x, v.y, v.z, v.w};
+      const float xv[4] = {__shfl_sync(0xffffffffu, x_own.x, qbase + q),
+                           __shfl_sync(0xffffffffu, x_own.y, qbase + q),
+                           __shfl_sync(0xffffffffu, x_own.z, qbase + q),
+                           __shfl_sync(0xffffffffu, x_own.w, qbase + q)};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float4 u = U4[(4 * q + e) * 4 + j];
@@ -649,7 +654,6 @@ k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, con
       }
     }
   }
-  const float4 g = __ldg(reinterpret_cast<const float4*>(G + r * 16) + j);
   const float4 gp = make_float4(pre.x > 0.f ? g.x : 0.f, pre.y > 0.f ? g.y : 0.f, pre.z > 0.f ? g.z : 0.f,
                                 pre.w > 0.f ? g.w : 0.f);
   if (ok) reinterpret_cast<float4*>(Gp_out + r * 16)[j] = gp;
@@ -736,9 +740,11 @@ k_enc_bwd(const float* __restrict__ u, const float* __restrict__ dH0, long long 
 // (g, p, q0) accumulates outputs (p, q0..q0+TN) over the rows g, g+RG, ... of every
 // tile (TN = 4 columns per thread: one broadcast A load and one 16-byte B load per four
 // FMAs); the RG row-group partials are added in a fixed order at the end, and
-// k_wgrad_final adds the block partials in float64, also in a fixed order.
-constexpr int WG_CHUNK = 2048;
-constexpr int WG_KT = 64;
+// k_wgrad_final adds the block partials in float64, also in a fixed order.  Tiles of
+// 128 rows (two 16-byte loads of each operand in flight per thread) and 1,024-row chunks
+// (twice the blocks of 2,048) keep enough bytes in flight to stream the operands.
+constexpr int WG_CHUNK = 1024;
+constexpr int WG_KT = 128;
 
 template <int P, int Q>
 struct WgShape {
@@ -754,9 +760,13 @@ struct WgShape {
   static constexpr int LB = (B4 + 255) / 256;
 };
 
+// A2 (may be null): A's rows are [A[r, :P/2], A2[r, :P/2]] (two row-major arrays of P/2
+// columns each), so that one pass over B gives the gradients of two weight matrices that
+// share it (the layer's U and W).
 template <int P, int Q>
 __global__ void __launch_bounds__(256)
-k_wgrad(const float* __restrict__ A, const float* __restrict__ Bm, long long R, float* __restrict__ partials) {
+k_wgrad(const float* __restrict__ A, const float* __restrict__ A2, const float* __restrict__ Bm, long long R,
+        float* __restrict__ partials) {
   using S = WgShape<P, Q>;
   constexpr int TN = S::TN, NQ = S::NQ, NP = S::NP, TPG = S::TPG, RG = S::RG;
   __shared__ __align__(16) float sA[WG_KT * P + 4];
@@ -775,12 +785,25 @@ k_wgrad(const float* __restrict__ A, const float* __restrict__ Bm, long long R, 
   float4 ra[S::LA], rb[S::LB];
   auto load = [&](int kt) {
     const int nr = min(WG_KT, rows - kt * WG_KT);
-    const float4* a4 = reinterpret_cast<const float4*>(A + (r0 + (long long)kt * WG_KT) * P);
     const float4* b4 = reinterpret_cast<const float4*>(Bm + (r0 + (long long)kt * WG_KT) * Q);
+    if (A2 == nullptr) {
+      const float4* a4 = reinterpret_cast<const float4*>(A + (r0 + (long long)kt * WG_KT) * P);
 #pragma unroll
-    for (int u = 0; u < S::LA; ++u) {
-      const int i = t + 256 * u;
-      ra[u] = (i < S::A4 && i < nr * P / 4) ? __ldg(a4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int u = 0; u < S::LA; ++u) {
+        const int i = t + 256 * u;
+        ra[u] = (i < S::A4 && i < nr * P / 4) ? __ldg(a4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {  // float4 i of the tile: row i / (P/4), its half from A or A2
+      constexpr int H4 = P / 8;  // float4 per half row
+      const float4* a4 = reinterpret_cast<const float4*>(A + (r0 + (long long)kt * WG_KT) * (P / 2));
+      const float4* c4 = reinterpret_cast<const float4*>(A2 + (r0 + (long long)kt * WG_KT) * (P / 2));
+#pragma unroll
+      for (int u = 0; u < S::LA; ++u) {
+        const int i = t + 256 * u;
+        const int row = i / (2 * H4), k = i % (2 * H4);
+        const float4* src = k < H4 ? a4 + row * H4 + k : c4 + row * H4 + (k - H4);
+        ra[u] = (i < S::A4 && i < nr * P / 4) ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
 #pragma unroll
     for (int u = 0; u < S::LB; ++u) {
@@ -1111,7 +1134,8 @@ static int forward_batch(gnp_model* M, const float* b, cudaStream_t st) {
 }
 
 template <int P, int Q>
-static int wgrad(TrainState* T, const float* A, const float* Bm, float* Wout, float* bias, cudaStream_t st) {
+static int wgrad(TrainState* T, const float* A, const float* Bm, float* Wout, float* bias, cudaStream_t st,
+                 const float* A2 = nullptr) {
   const int nblk = (int)((T->R + WG_CHUNK - 1) / WG_CHUNK);
   const int PQ = (P + 1) * Q;
   if (T->part_cap < nblk * 33 * 32) {
@@ -1120,7 +1144,7 @@ static int wgrad(TrainState* T, const float* A, const float* Bm, float* Wout, fl
     GNP_TRY(dev_alloc(&T->partials, (size_t)nblk * 33 * 32));
     T->part_cap = nblk * 33 * 32;
   }
-  k_wgrad<P, Q><<<nblk, 256, 0, st>>>(A, Bm, T->R, T->partials);
+  k_wgrad<P, Q><<<nblk, 256, 0, st>>>(A, A2, Bm, T->R, T->partials);
   k_wgrad_final<<<(PQ * 32 + 255) / 256, 256, 0, st>>>(T->partials, nblk, P, Q, Wout, bias);
   return check_launch("wgrad");
 }
@@ -1155,9 +1179,12 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
     GNP_TRY(spmm_nodes(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->y16), n, B * 4,
                        1.0f, reinterpret_cast<const float4*>(Gn), 1.0f, reinterpret_cast<float4*>(Gn), st));
     float* gl = g + layer_off(l);
-    if (M->cfg.form == GNP_LAYER_PAPER) GNP_TRY((wgrad<16, 16>(T, X, T->gp16, gl, nullptr, st)));  // dU
-    else GNP_TRY_CUDA(cudaMemsetAsync(gl, 0, sizeof(float) * 256, st));
-    GNP_TRY((wgrad<16, 16>(T, AG, T->gp16, gl + 256, nullptr, st)));  // dW
+    if (M->cfg.form == GNP_LAYER_PAPER) {
+      GNP_TRY((wgrad<32, 16>(T, X, T->gp16, gl, nullptr, st, AG)));  // dU (rows 0-15), dW (16-31)
+    } else {
+      GNP_TRY_CUDA(cudaMemsetAsync(gl, 0, sizeof(float) * 256, st));
+      GNP_TRY((wgrad<16, 16>(T, AG, T->gp16, gl + 256, nullptr, st)));  // dW
+    }
     std::swap(G, Gn);
   }
   // encoder: r1 -> s32a, da1 -> s32b
