@@ -275,6 +275,57 @@ k_encode_vn(const VNext vn, int n, double sqrt_n, int noscale, double* __restric
   tile_copy<HT, true>(stile, H, r0, rows);
 }
 
+// The encoder of the overlapped-CGS2 step s + 1 >= 1 (vn.dcgs; s = st->jd, whose first
+// pass just finished; V_s is final): for its rows,
+//   v'_{s+1} = (w_s - V_s h_s) / rho_s   (-> V[:, s+1], rho_s as normalised by the pass),
+// encoded as k_encode_vn encodes its vector (unit norm: u = sqrt(n) v', tau = 1;
+// noscale: u = v', tau = sqrt(n)).  After a breakdown 1/rho_s is 0 and v'_{s+1} = 0; the
+// cycle has ended by then, and every later kernel returns.
+template <class HT>
+__global__ void __launch_bounds__(TILE)
+k_encode_dv(const VNext vn, int n, double sqrt_n, int noscale, double* __restrict__ tau, HT* __restrict__ H,
+            const __grid_constant__ EncW ew) {
+  const DevState* st = vn.st;
+  if (!st->active) return;
+  __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
+  __shared__ double sh[GNP_MAX_RESTART + 4];
+  __shared__ double s_rho;
+  const int s = st->jd;
+  const int t = threadIdx.x;
+  for (int k = t; k <= s; k += blockDim.x) sh[k] = vn.h2[k];
+  if (t == 0) {
+    s_rho = st->rho_inv;
+    if (blockIdx.x == 0) *tau = noscale ? sqrt_n : 1.0;
+  }
+  __syncthreads();
+  const double rho_inv = s_rho;
+  const double f = noscale ? 1.0 : sqrt_n;
+  const int r0 = blockIdx.x * TILE;
+  const int rows = min(TILE, n - r0);
+  if (t < rows) {
+    const size_t ld = (size_t)n;
+    const int i = r0 + t;
+    double y = vn.w[i];
+#pragma unroll 8
+    for (int k = 0; k <= s; ++k) y -= vn.V[k * ld + i] * sh[k];
+    y = y * rho_inv;
+    vn.V[(size_t)(s + 1) * ld + i] = y;
+    const float u = (float)(y * f);
+    float h[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) h[c] = ew.b2[c];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float a = fmaxf(fmaf(u, ew.W1[k], ew.b1[k]), 0.0f);
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) ffma2(h[c], h[c + 1], a, a, ew.W2[k * 16 + c], ew.W2[k * 16 + c + 1]);
+    }
+    stage_row<HT>(stile, t, h);
+  }
+  __syncthreads();
+  tile_copy<HT, true>(stile, H, r0, rows);
+}
+
 // ---------------------------------------------------------------- k_gconv
 //
 // One block of TILE threads per ROWS consecutive rows (ROWS = 256: one epilogue thread per
@@ -1156,7 +1207,8 @@ static int layer_impl(gnp_model* M, int l, const HT* Hin, HT* Hout, cudaStream_t
 
 template <class HT, int FORM>
 static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const VNext* vn) {
+                      const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs& W, const VNext* vn,
+                      cudaEvent_t fork, cudaStream_t side) {
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
   const double sqrt_n = std::sqrt((double)n);
@@ -1171,8 +1223,13 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
   fill_enc_dec(M->w_host, L, ew, dw);
   HT* H0 = static_cast<HT*>(W.H[0]);
   HT* H1 = static_cast<HT*>(W.H[1]);
-  if (vn) k_encode_vn<HT><<<nt + 1, TILE, 0, st>>>(*vn, n, sqrt_n, noscale, W.tau, H0, ew);
+  if (vn && vn->dcgs) k_encode_dv<HT><<<nt, TILE, 0, st>>>(*vn, n, sqrt_n, noscale, W.tau, H0, ew);
+  else if (vn) k_encode_vn<HT><<<nt + 1, TILE, 0, st>>>(*vn, n, sqrt_n, noscale, W.tau, H0, ew);
   else k_encode<HT><<<nt, TILE, 0, st>>>(v, vscale, W.tau, ctl, n, sqrt_n, noscale, H0, ew);
+  if (fork) {
+    GNP_TRY_CUDA(cudaEventRecord(fork, st));
+    GNP_TRY_CUDA(cudaStreamWaitEvent(side, fork, 0));
+  }
   if (trace) k_hidden_to_f32<HT><<<4 * NUM_SMS_GB300, 256, 0, st>>>(H0, trace, (long long)n * 16);
   switch (row_kernel_mode(A)) {
     case 24: GNP_TRY((launch_layers_row<HT, FORM, 2, 4>(M, H0, H1, z, trace, ctl, st, ev, W, dw, sqrt_n))); break;
@@ -1189,17 +1246,19 @@ static int apply_impl(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, fl
 }
 
 int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
-                 const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs* ws, const VNext* vn) {
+                 const int* ctl, cudaStream_t st, cudaEvent_t* ev, const ApplyWs* ws, const VNext* vn,
+                 cudaEvent_t fork, cudaStream_t side) {
   GNP_TRY(model_sync_host(M));
   const ApplyWs& W = ws ? *ws : M->ws;
   const int form = M->cfg.form;
   if (M->hprec == GNP_H_BF16) {
     return form == GNP_LAYER_PAPER
-               ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W, vn)
-               : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W, vn);
+               ? apply_impl<uint16_t, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W, vn, fork, side)
+               : apply_impl<uint16_t, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W, vn, fork, side);
   }
-  return form == GNP_LAYER_PAPER ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W, vn)
-                                 : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W, vn);
+  return form == GNP_LAYER_PAPER
+             ? apply_impl<float, GNP_LAYER_PAPER>(M, v, vscale, z, trace, ctl, st, ev, W, vn, fork, side)
+             : apply_impl<float, GNP_LAYER_RESID>(M, v, vscale, z, trace, ctl, st, ev, W, vn, fork, side);
 }
 
 int apply_ws_alloc(ApplyWs& ws, int n) {

@@ -55,6 +55,12 @@ struct VNext {
   double* g;
   double* hist;
   unsigned long long* thist;
+  // Overlapped CGS2 (dcgs = 1): h1 holds a_s = V_{s-1}^T v'_s, h2 the first-pass h_s
+  // = V_s^T w_s, hf the finished column s-1; the encoder forms v'_{s+1} = (w_s - V_s h_s)
+  // / rho_s and encodes it (no finishing block: the reorthogonalisation branch finishes
+  // the columns).
+  const double* hf;
+  int dcgs;
 };
 
 // Mutable scratch of one GNP application: hidden ping-pong blocks (n x 16 float32 each,
@@ -104,9 +110,12 @@ namespace gnp {
 // vn (may be null): the encoder first forms the pending basis vector of that FGMRES step
 // (written to V[:, jv+1], normalised) and encodes it, while one extra block finishes the
 // step (v and vscale are then unused).
+// fork (may be null): recorded on `st` right after the encoder, and `side` made to wait
+// for it, so that work launched on `side` next overlaps the Res-GCONV layers.
 int apply_launch(gnp_model* M, ColPtr v, const double* vscale, ColPtr z, float* trace,
                  const int* ctl, cudaStream_t st, cudaEvent_t* ev = nullptr,
-                 const ApplyWs* ws = nullptr, const VNext* vn = nullptr);
+                 const ApplyWs* ws = nullptr, const VNext* vn = nullptr, cudaEvent_t fork = nullptr,
+                 cudaStream_t side = nullptr);
 
 // Kernel-parameter copies of the encoder/decoder and of layer l's weights.
 void fill_enc_dec(const std::vector<float>& w, int L, EncW& ew, DecW& dw);

@@ -66,16 +66,20 @@ void solver_free(Solver* s) {
   dev_free(s->g);
   dev_free(s->h1);
   dev_free(s->h2);
+  dev_free(s->hf);
   dev_free(s->hist);
   dev_free(s->thist);
   red_free(s->red);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->fork) cudaEventDestroy(s->fork);
+  if (s->join) cudaEventDestroy(s->join);
   delete s;
 }
 
 size_t solver_bytes(int n, int m, int maxiters) {
   const size_t maxb = (size_t)std::max(4 * NUM_SMS_GB300, (n + TILE - 1) / TILE);
   return (size_t)n * (m + 1) * 8 + (size_t)n * m * 4 + (size_t)n * 8 + sizeof(DevState) +
-         (size_t)(m + 1) * m * 8 * 2 + (size_t)(4 * m + 8) * 8 + (size_t)(maxiters + 1) * 16 +
+         (size_t)(m + 1) * m * 8 * 2 + (size_t)(5 * m + 10) * 8 + (size_t)(maxiters + 1) * 16 +
          maxb * (m + 2) * 8 + 8;
 }
 
@@ -111,6 +115,7 @@ int solver_create(int n, int m, int maxiters, Solver** out) {
     if ((e = dev_alloc(&s->g, (size_t)m + 1)) != GNP_OK) break;
     if ((e = dev_alloc(&s->h1, (size_t)m + 2)) != GNP_OK) break;
     if ((e = dev_alloc(&s->h2, (size_t)m + 2)) != GNP_OK) break;
+    if ((e = dev_alloc(&s->hf, (size_t)m + 2)) != GNP_OK) break;
     if ((e = dev_alloc(&s->hist, (size_t)maxiters + 1)) != GNP_OK) break;
     if ((e = dev_alloc(&s->thist, (size_t)maxiters + 1)) != GNP_OK) break;
     const int maxb = std::max(4 * NUM_SMS_GB300, (n + TILE - 1) / TILE);  // >= dot_blocks(n)
@@ -246,24 +251,18 @@ k_spmv_dot(const int* __restrict__ rp, const int* __restrict__ col, const double
 // time, as k_cgs<1> does.  Same result layout and last-block reduction as k_spmv_dot.
 constexpr int SPMV_ROW_DMAX = 32;
 
+// w_i = sum_j a_ij x_j for the rows i = blockIdx.x * blockDim.x + threadIdx.x + c * gridDim.x
+// * blockDim.x, one thread per row, in column order with eight nonzeros' loads in flight.
 template <class XT>
-__global__ void __launch_bounds__(RED_THREADS)
-k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-               ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
-               double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
-  if (!st->active) return;
-  __shared__ double sred[RED_SH];
-  __shared__ double shtot[GNP_MAX_RESTART + 2];
-  const int j = st->j;
-  const int K = j + 2;  // h1[0..j] and ||w||^2
-  const size_t ld = (size_t)n;
-  const XT* x = static_cast<const XT*>(colptr_k(xp));
+__device__ __forceinline__ void row_spmv(const int* __restrict__ rp, const int* __restrict__ col,
+                                         const double* __restrict__ val, const XT* __restrict__ x,
+                                         double* __restrict__ w, int n) {
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gstride = gridDim.x * blockDim.x;
   for (int i = gtid; i < n; i += gstride) {
     const int rs = __ldg(rp + i), re = __ldg(rp + i + 1);
     double s = 0.0;
-    for (int e0 = rs; e0 < re; e0 += 8) {  // eight nonzeros' loads in flight, added in order
+    for (int e0 = rs; e0 < re; e0 += 8) {
       int c[8];
       double v[8];
       XT xv[8];
@@ -281,6 +280,20 @@ k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const do
     }
     w[i] = s;
   }
+}
+
+template <class XT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+               ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
+               double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
+  if (!st->active) return;
+  __shared__ double sred[RED_SH];
+  __shared__ double shtot[GNP_MAX_RESTART + 2];
+  const int j = st->j;
+  const int K = j + 2;  // h1[0..j] and ||w||^2
+  const size_t ld = (size_t)n;
+  row_spmv(rp, col, val, static_cast<const XT*>(colptr_k(xp)), w, n);
   block_dots(V, w, n, K, j + 1, sred, partials + (size_t)blockIdx.x * K);
   if (!last_block_arrive(counter)) return;
   reduce_partials(partials, gridDim.x, K, shtot);
@@ -289,6 +302,210 @@ k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const do
     st->wnorm0 = sqrt(shtot[j + 1]);
     *counter = 0;
   }
+}
+
+// ---------------------------------------------------------------- overlapped CGS2
+//
+// CGS2 with delayed reorthogonalisation (Bielich, Langou, Thomas, Swirydowicz, Yamazaki,
+// Boman 2022), arranged so that the second pass runs beside the GNP.  The encoder of step
+// s forms v'_s, the first-pass (once orthogonalised, Pythagorean-normalised) vector, and
+// z_s = M(v'_s): FGMRES needs only A Z = V_{m+1} H_bar (Sec. 2.1), so any z_s is a valid
+// direction.  While the Res-GCONV layers of step s run (float32, on the L2), a second
+// stream takes the float64 second pass of v'_s:
+//   k_reorth_dots:   a_s = V_{s-1}^T v'_s, beta = ||v'_s||^2 (one grid reduction), nu_s =
+//                    sqrt(beta - ||a_s||^2); as v'_s = V_{s-1} a_s + nu_s v_s, column s-1 of
+//                    H_bar is [h_{s-1} + rho_{s-1} a_s; rho_{s-1} nu_s]: its Givens update
+//                    and the continue decision follow in the same last block;
+//   k_reorth_update: v_s = (v'_s - V_{s-1} a_s) / nu_s, in place.
+// The main stream then joins it: k_spmv_rdot(_row) forms w_s = A z_s and the first pass
+// against the final V_s, h_s = V_s^T w_s and ||w_s||^2 (one grid reduction), rho_s =
+// sqrt(||w_s||^2 - ||h_s||^2); the encoder of step s+1 forms v'_{s+1} = (w_s - V_s h_s) /
+// rho_s.  The critical path keeps one grid reduction and the first pass; the other half
+// of the float64 work overlaps the float32 layers.  The last column of a cycle keeps its
+// first-pass values [h_{m-1}; rho_{m-1}] (v'_m is never used; the cycle ends with the
+// true residual), finished by k_dfinish.  In exact arithmetic a_s = 0 and nu_s = 1, so
+// the steps are those of CGS2; only rounding differs.
+
+// The Pythagorean rho_s loses its digits to cancellation once rho_s / ||w_s|| falls below
+// about sqrt(eps) (it can clamp to 0 where the true value is 1e-10 ||w_s||).  Any
+// normalisation of v'_{s+1} keeps w_s = V_s h_s + rho v'_{s+1} exact, so v'_{s+1} is divided
+// by max(rho_s, RHO_FLOOR ||w_s||), and nu_{s+1} (an explicit norm after reorthogonalisation)
+// gives the true subdiagonal rho nu_{s+1} of column s: an exact breakdown shows there, one
+// step later, instead of restarting the cycle early on noise.
+constexpr double RHO_FLOOR = 1e-7;
+
+// Finish column j of H_bar (col: j+1 entries, global; hn its subdiagonal) with the whole
+// block, in lagged form (the step counter belongs to the reductions).
+__device__ __forceinline__ void finish_col(const VNext& a, int j, const double* col, double hn, double wn0) {
+  __shared__ double scol[GNP_MAX_RESTART + 4];
+  __shared__ double scs[GNP_MAX_RESTART + 4];
+  __shared__ double ssn[GNP_MAX_RESTART + 4];
+  __shared__ double sxs[GNP_MAX_RESTART + 4];
+  __shared__ double sbs[GNP_MAX_RESTART + 4];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) scol[i] = col[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    scs[i] = a.cs[i];
+    ssn[i] = a.sn[i];
+  }
+  __syncthreads();
+  arnoldi_step_finish_block(a.st, j, scol, hn, scs, ssn, sxs, sbs, a.H, a.R, a.cs, a.sn, a.g, a.hist, a.thist, true,
+                            wn0);
+}
+
+// The last block of the first pass of step s: h_s (-> a.h2), rho_s and the state the next
+// encoder reads.  The step breaks down only when w_s = 0 or something is not finite;
+// column s is then finished at once with its first-pass values (column s-1 was finished
+// by the reorthogonalisation branch before this kernel started), which ends the cycle.
+__device__ __forceinline__ void rdot_tail(const VNext& a, const double* partials, int nblocks, int s,
+                                          unsigned* counter) {
+  __shared__ double tot[GNP_MAX_RESTART + 4];
+  __shared__ int s_brk;
+  DevState* st = a.st;
+  const int K = s + 2;  // h_s[0..s] and ||w_s||^2
+  reduce_partials(partials, nblocks, K, tot);
+  if (threadIdx.x < 32) {
+    double bb = 0.0;
+    for (int k = threadIdx.x; k <= s; k += 32) bb = fma(tot[k], tot[k], bb);
+    bb = warp_sum(bb);
+    if (threadIdx.x == 0) {
+      const double omega = tot[s + 1];
+      const double rho = sqrt(fmax(omega - bb, 0.0));
+      const double wn = sqrt(omega);
+      const double rho_n = fmax(rho, RHO_FLOOR * wn);  // the normalisation of v'_{s+1}
+      const bool brk = !(rho_n > 0.0) || !isfinite(rho_n) || !isfinite(bb);
+      st->rho = rho_n;
+      st->rho_est = rho;
+      st->rho_inv = brk ? 0.0 : 1.0 / rho_n;
+      st->wnorm0 = wn;
+      st->jd = s;
+      st->j = s + 1;
+      s_brk = brk ? 1 : 0;
+      *counter = 0;
+    }
+  }
+  double* h2 = const_cast<double*>(a.h2);
+  for (int k = threadIdx.x; k <= s; k += blockDim.x) h2[k] = tot[k];
+  __syncthreads();
+  if (s_brk && st->active) finish_col(a, s, a.h2, st->rho_est, st->wnorm0);
+}
+
+// w = A z and the first pass of step s = st->j (short rows: one thread per row).
+template <class XT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_spmv_rdot_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val, ColPtr xp,
+                int n, const VNext a, double* __restrict__ partials, unsigned* counter) {
+  if (!a.st->active) return;
+  __shared__ double sred[RED_SH];
+  const int s = a.st->j;
+  const int K = s + 2;
+  double* w = const_cast<double*>(a.w);
+  row_spmv(rp, col, val, static_cast<const XT*>(colptr_k(xp)), w, n);
+  block_dots(a.V, w, n, K, s + 1, sred, partials + (size_t)blockIdx.x * K);
+  if (!last_block_arrive(counter)) return;
+  rdot_tail(a, partials, gridDim.x, s, counter);
+}
+
+// The same with the tile gather (any row lengths): blocks loop over tiles of TILE rows,
+// thread t owning row r0 + t, so that the dots see the rows this thread wrote.
+template <class XT>
+__global__ void __launch_bounds__(TILE)
+k_spmv_rdot(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val, ColPtr xp,
+            int n, const VNext a, double* __restrict__ partials, unsigned* counter) {
+  static_assert(TILE == RED_THREADS, "tile rows = reduction threads");
+  if (!a.st->active) return;
+  using TR = TrSpmv<XT>;
+  __shared__ TileSmem<TR> sm;
+  __shared__ double sred[RED_SH];
+  const int s = a.st->j;
+  const int K = s + 2;
+  double* w = const_cast<double*>(a.w);
+  const XT* x = static_cast<const XT*>(colptr_k(xp));
+  const int nt = (n + TILE - 1) / TILE;
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int r0 = tile * TILE;
+    const int rows = min(TILE, n - r0);
+    __syncthreads();
+    tile_load_rp<TR>(sm, rp, r0, rows);
+    __syncthreads();
+    tile_gather<TR>(sm, rows, col, val, x);
+    __syncthreads();
+    if (threadIdx.x < rows) {
+      double s1[1];
+      tile_row_sum<TR, 1>(sm, threadIdx.x, 0, s1);
+      w[r0 + threadIdx.x] = s1[0];
+    }
+  }
+  block_dots(a.V, w, n, K, s + 1, sred, partials + (size_t)blockIdx.x * K);
+  if (!last_block_arrive(counter)) return;
+  rdot_tail(a, partials, gridDim.x, s, counter);
+}
+
+// Second pass of step s = st->j >= 1 (reorthogonalisation branch): a_s, nu_s, the finished
+// column s-1 and its Givens update (last block).
+__global__ void __launch_bounds__(RED_THREADS)
+k_reorth_dots(int n, const VNext a, double* __restrict__ partials, unsigned* counter) {
+  DevState* st = a.st;
+  if (!st->active) return;
+  __shared__ double sred[RED_SH];
+  __shared__ double tot[GNP_MAX_RESTART + 4];
+  __shared__ double s_nu;
+  const int s = st->j;
+  const int K = s + 1;  // a_s[0..s-1] and ||v'_s||^2
+  const size_t ld = (size_t)n;
+  block_dots(a.V, a.V + (size_t)s * ld, n, K, s, sred, partials + (size_t)blockIdx.x * K);
+  if (!last_block_arrive(counter)) return;
+  reduce_partials(partials, gridDim.x, K, tot);
+  if (threadIdx.x < 32) {
+    double aa = 0.0;
+    for (int k = threadIdx.x; k < s; k += 32) aa = fma(tot[k], tot[k], aa);
+    aa = warp_sum(aa);
+    if (threadIdx.x == 0) {
+      const double nu = sqrt(fmax(tot[s] - aa, 0.0));
+      s_nu = nu;
+      st->nu_inv = 1.0 / nu;
+      *counter = 0;
+    }
+  }
+  __syncthreads();
+  const double rp = st->rho;  // rho_{s-1}, the normalisation of v'_s
+  double* hf = const_cast<double*>(a.hf);
+  double* ha = const_cast<double*>(a.h1);
+  for (int k = threadIdx.x; k < s; k += blockDim.x) {
+    ha[k] = tot[k];
+    hf[k] = fma(rp, tot[k], a.h2[k]);  // h_{s-1}[k] + rho_{s-1} a_k
+  }
+  __syncthreads();
+  finish_col(a, s - 1, hf, rp * s_nu, st->wnorm0);
+}
+
+// v_s = (v'_s - V_{s-1} a_s) / nu_s in place (s = st->j >= 1), after k_reorth_dots.
+__global__ void __launch_bounds__(RED_THREADS)
+k_reorth_update(int n, const VNext a) {
+  const DevState* st = a.st;
+  if (!st->active) return;
+  __shared__ double sa[GNP_MAX_RESTART + 4];
+  __shared__ double s_inv;
+  const int s = st->j;
+  for (int k = threadIdx.x; k < s; k += blockDim.x) sa[k] = a.h1[k];
+  if (threadIdx.x == 0) s_inv = st->nu_inv;
+  __syncthreads();
+  const double inv = s_inv;
+  const size_t ld = (size_t)n;
+  double* V = a.V;
+  double* vs = V + (size_t)s * ld;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double x = vs[i];
+#pragma unroll 8
+    for (int k = 0; k < s; ++k) x -= V[k * ld + i] * sa[k];
+    vs[i] = x * inv;
+  }
+}
+
+// End of an overlapped cycle: the last column, [h_{m-1}; rho_{m-1}] (one block).
+__global__ void __launch_bounds__(RED_THREADS) k_dfinish(const VNext a) {
+  DevState* st = a.st;
+  if (!st->active) return;
+  finish_col(a, st->jd, a.h2, st->rho_est, st->wnorm0);
 }
 
 // r = b - A x -> V[:, 0], beta = ||r||; the last block restarts the cycle state.
@@ -565,8 +782,28 @@ int solver_ensure_zd(Solver* S, int m) {
   return GNP_OK;
 }
 
-static VNext vnext_args(Solver* S) {
-  return VNext{S->V, S->w, S->h1, S->h2, S->st, S->H, S->R, S->cs, S->sn, S->g, S->hist, S->thist};
+// The reorthogonalisation stream (highest priority, so that its short kernels take SM
+// slots as the layers' blocks retire) and the fork/join events, made on first use.
+static int solver_side(Solver* S) {
+  if (S->side) return GNP_OK;
+  int lo = 0, hi = 0;
+  GNP_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  GNP_TRY_CUDA(cudaStreamCreateWithPriority(&S->side, cudaStreamNonBlocking, hi));
+  GNP_TRY_CUDA(cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming));
+  GNP_TRY_CUDA(cudaEventCreateWithFlags(&S->join, cudaEventDisableTiming));
+  return GNP_OK;
+}
+
+static VNext vnext_args(Solver* S, int dcgs = 0) {
+  return VNext{S->V, S->w, S->h1, S->h2, S->st, S->H, S->R, S->cs, S->sn, S->g, S->hist, S->thist, S->hf, dcgs};
+}
+
+// The GNP step's orthogonalisation: CGS2 with its second pass overlapped with the GNP
+// (GNP_ORTHO=dcgs2 in the environment) or CGS2 with both passes after the SpMV
+// (otherwise).  Read at every cycle launch; the captured cycle graph is keyed on it.
+static bool dcgs_enabled() {
+  const char* e = getenv("GNP_ORTHO");
+  return e && strcmp(e, "dcgs2") == 0;
 }
 
 // Row-per-thread SpMV for matrices without long rows (GNP_SPMV_ROWK=0 in the environment
@@ -601,6 +838,36 @@ int launch_cycle(gnp_mat* A, Solver* S, const Prec& P, int m, const double* b, d
   const bool short_rows = spmv_short_rows(A);
   const bool f64z = P.kind == GNP_PRECOND_JACOBI || P.kind == GNP_PRECOND_GMRES;
   if (f64z) GNP_REQUIRE(S->Zd && S->zd_m >= m, "launch_cycle: float64 directions not allocated");
+  if (P.kind == GNP_PRECOND_GNP && dcgs_enabled()) {
+    // overlapped CGS2 (see the kernels above): the second pass of v'_j runs on S->side
+    // beside the layers of step j
+    GNP_TRY(solver_side(S));
+    gnp_model* M = P.M;
+    const VNext vd = vnext_args(S, 1);
+    for (int j = 0; j < m; ++j) {
+      ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
+      ColPtr z{S->Z, sizeof(float) * (size_t)n, jptr, 0};
+      cudaEvent_t* ev = prof ? S->events.data() + (size_t)2 * j * M->cfg.L : nullptr;
+      GNP_TRY(apply_launch(M, v, &S->st->vscale, z, nullptr, ctl, st, ev, ws, j > 0 ? &vd : nullptr,
+                           j > 0 ? S->fork : nullptr, S->side));
+      if (j > 0) {
+        k_reorth_dots<<<ncg, RED_THREADS, 0, S->side>>>(n, vd, S->red.partials, S->red.counter);
+        k_reorth_update<<<nb, RED_THREADS, 0, S->side>>>(n, vd);
+        GNP_TRY_CUDA(cudaEventRecord(S->join, S->side));
+        GNP_TRY_CUDA(cudaStreamWaitEvent(st, S->join, 0));
+      }
+      if (short_rows)
+        k_spmv_rdot_row<float><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, z, n, vd, S->red.partials,
+                                                            S->red.counter);
+      else
+        k_spmv_rdot<float><<<ndot, TILE, 0, st>>>(A->rp, A->col, A->val, z, n, vd, S->red.partials, S->red.counter);
+    }
+    k_dfinish<<<1, RED_THREADS, 0, st>>>(vd);
+    k_xupdate<float><<<nb, RED_THREADS, (int)sizeof(double) * m * m, st>>>(S->Z, x, n, S->st, S->R, S->g);
+    k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist, S->thist,
+                                    S->red.partials, S->red.counter);
+    return check_launch("fgmres cycle (overlapped CGS2)");
+  }
   for (int j = 0; j < m; ++j) {
     ColPtr v{S->V, sizeof(double) * (size_t)n, jptr, 0};
     if (P.kind == GNP_PRECOND_GNP) {
@@ -916,7 +1183,7 @@ static int solve_impl(gnp_mat* A, const double* b, double* x, const Prec& P, int
         const unsigned long long ver = M ? model_version(M) : 0ull;
         if (!S->gexec || S->g_model != P.key || S->g_kind != P.kind || S->g_version != ver || S->g_m != restart ||
             S->g_hprec != (M ? M->hprec : -1) || S->g_b != b || S->g_x != x || S->g_stream != st ||
-            S->g_prof != prof) {
+            S->g_prof != prof || S->g_dcgs != dcgs_enabled()) {
           if (S->gexec) cudaGraphExecDestroy(S->gexec);
           S->gexec = nullptr;
           cudaGraph_t graph;
@@ -944,6 +1211,7 @@ static int solve_impl(gnp_mat* A, const double* b, double* x, const Prec& P, int
           S->g_x = x;
           S->g_stream = st;
           S->g_prof = prof;
+          S->g_dcgs = dcgs_enabled();
         }
         GNP_TRY_CUDA(cudaGraphLaunch(S->gexec, st));
       } else {

@@ -35,6 +35,12 @@ struct DevState {
   double w1sq;     // ||w1||^2 of step jv (k_cgs<4>)
   unsigned long long t0;          // %globaltimer (ns) when the solve began
   unsigned long long timeout_ns;  // 0: no time limit
+  // Overlapped CGS2 (delayed reorthogonalisation): the first pass of step jd wrote
+  int jd;          // the step whose first pass finished last
+  double rho;      // the normalisation of v'_{s+1}: max(rho_s, RHO_FLOOR ||w_s||)
+  double rho_est;  // rho_s = ||w_s - V_s h_s|| by the first pass (Pythagorean)
+  double rho_inv;  // 1 / rho (0 after a breakdown)
+  double nu_inv;   // 1 / nu_s, nu_s = ||v'_s - V_{s-1} a_s|| (the second pass of step s)
 };
 
 // Device clock in nanoseconds (the PTX %globaltimer register, common to all SMs).
@@ -161,9 +167,13 @@ __device__ __forceinline__ void block_dots(const double* __restrict__ V, const d
 // estimate |g_{j+1}| (Sec. 4), the iteration's residual and device time, and whether the
 // cycle continues.  The state and g_j come in with one batch of loads and go back at the
 // end, so that no store to R, g or the histories forces a reload of a state field.
+// lagged (one-reduction CGS2): column j is finished one step late, so the step counter
+// (advanced by the reduction) and vscale are left alone and wn0 is the column's own ||w||;
+// otherwise wn0 < 0 takes st->wnorm0.
 __device__ __forceinline__ void arnoldi_step_decide(DevState* st, int j, double a, double hn, bool finite,
                                                     double* R, double* cs, double* sn, double* g,
-                                                    double* hist, unsigned long long* thist) {
+                                                    double* hist, unsigned long long* thist,
+                                                    bool lagged = false, double wn0_in = -1.0) {
   DevState s = *st;
   const double gj = g[j];
   const int m = s.m;
@@ -180,7 +190,7 @@ __device__ __forceinline__ void arnoldi_step_decide(DevState* st, int j, double 
   s.iters = iters;
   const unsigned long long elapsed = global_ns() - s.t0;
   thist[iters] = elapsed;
-  const double wn0 = s.wnorm0;
+  const double wn0 = wn0_in >= 0.0 ? wn0_in : s.wnorm0;
   int flags = 0;
   int jj;
   if (!finite || !isfinite(rho)) {
@@ -211,7 +221,7 @@ __device__ __forceinline__ void arnoldi_step_decide(DevState* st, int j, double 
   s.flags = flags;
   if (flags) {
     s.active = 0;
-  } else {
+  } else if (!lagged) {
     s.j = j + 1;
     s.vscale = hn;
   }
@@ -253,7 +263,8 @@ __device__ __forceinline__ void arnoldi_step_finish_block(DevState* st, int j, c
                                                           const double* scs, const double* ssn, double* xs,
                                                           double* bs, double* H, double* R, double* cs,
                                                           double* sn, double* g, double* hist,
-                                                          unsigned long long* thist) {
+                                                          unsigned long long* thist, bool lagged = false,
+                                                          double wn0 = -1.0) {
   const int t = threadIdx.x;
   const int ldh = st->m + 1;
   for (int i = t; i <= j; i += blockDim.x) H[(size_t)j * ldh + i] = col[i];
@@ -276,7 +287,7 @@ __device__ __forceinline__ void arnoldi_step_finish_block(DevState* st, int j, c
     bad = bad || !isfinite(ti);
   }
   bad = __syncthreads_or(bad) != 0;
-  if (t == 0) arnoldi_step_decide(st, j, xs[j], hn, !bad, R, cs, sn, g, hist, thist);
+  if (t == 0) arnoldi_step_decide(st, j, xs[j], hn, !bad, R, cs, sn, g, hist, thist, lagged, wn0);
 }
 
 
@@ -317,7 +328,6 @@ __device__ __forceinline__ void vnext_finish(const VNext& a) {
   arnoldi_step_finish_block(st, j, shh, shn, scs, ssn, sxs, sbs, a.H, a.R, a.cs, a.sn, a.g, a.hist, a.thist);
 }
 
-
 struct Solver {
   int n = 0, m_cap = 0, maxit_cap = -1;
   double* V = nullptr;   // [n*(m+1)] column-major basis
@@ -332,6 +342,7 @@ struct Solver {
   double* g = nullptr;   // [m+1]
   double* h1 = nullptr;  // [m+2]
   double* h2 = nullptr;  // [m+2]
+  double* hf = nullptr;  // [m+2] overlapped CGS2: the finished column s-1
   double* Zd = nullptr;   // [n*m] float64 directions (Jacobi and inner-GMRES preconditioners)
   int zd_m = 0;
   double* hist = nullptr;  // [maxiters+1]
@@ -351,6 +362,10 @@ struct Solver {
   std::vector<cudaEvent_t> events;
   int ev_L = 0, ev_m = 0;
   bool g_prof = false;
+  bool g_dcgs = false;
+  // overlapped CGS2: the reorthogonalisation stream and its fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 

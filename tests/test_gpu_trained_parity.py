@@ -6,7 +6,8 @@ steps on the 64 x 64 problem).  With them the oracle's own iteration count moves
 z = M(v) changes at float32 level (rounded to float32, or multiplied by 1 + 1e-7 N(0, 1)),
 so the GPU's count -- float32 arithmetic, or a bfloat16 hidden block -- must lie within
 that spread, +-2: tests/golden/make_iteration_bands.py records it from the oracle.  Both
-hidden-block precisions must reach rtol 1e-8 in the true residual.
+hidden-block precisions, under both orthogonalisation schedules of the step (CGS2, and
+the one-reduction form), must reach rtol 1e-8 in the true residual.
 """
 import json
 import os
@@ -45,9 +46,11 @@ def band(record):
     return min(its), max(its)
 
 
+@pytest.mark.parametrize("ortho", ["cgs2", "dcgs2"])
 @pytest.mark.parametrize("hprec", [0, 1])
-def test_iterations_within_oracle_band_at_65536_rows(gnp, hprec):
+def test_iterations_within_oracle_band_at_65536_rows(gnp, hprec, ortho, monkeypatch):
     import torch
+    monkeypatch.setenv("GNP_ORTHO", ortho)
     A = I.convdiff2d(256, 100.0)
     b = I.spmv(A, I.gaussian(A.n, seed=0))
     Mt = gnp.mat_from_csr(A)
