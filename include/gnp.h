@@ -405,6 +405,16 @@ int gnp_gamma_noalloc(int n, long long nnz, const int* row_ptr_dev, const int* c
  * time to the solve, so keep it off when timing the solve itself.  Process-wide. */
 int gnp_profile_gconv(int on);
 
+/* How many bounded device-side waits have given up since the last reset (reset != 0
+ * clears the count after reading it), or -1 when the count cannot be read.  The
+ * TMA-gather Res-GCONV layer (Sec. 2.3, Eq. 7; used on matrices with rows of more than 16
+ * nonzeros when GNP_GCONV_TMA=1 is set) waits for its copies on mbarriers with a limit of
+ * 2 s of device time; a block that reaches the limit counts it here, waits (again
+ * bounded) for its copies still in flight and returns, leaving its output rows
+ * unwritten.  A non-zero count means the results of the launches since the last reset
+ * are not to be used.  Synchronous (reads a device counter). */
+int gnp_kernel_faults(int reset);
+
 #ifdef __cplusplus
 }
 #endif

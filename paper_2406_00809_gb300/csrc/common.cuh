@@ -98,6 +98,17 @@ inline int red_blocks(long long n) {
 struct Solver;       // FGMRES workspace (krylov.cu)
 struct MultiSolver;  // multi-right-hand-side FGMRES workspace (multi.cu)
 
+// Work items of the TMA-gather Res-GCONV layer (gconv_tma.cu) for one matrix and one
+// hidden-block precision: items[off[b] .. off[b+1]) = {tile, first nonzero, end, flags}
+// for persistent block b (flags: 1 first chunk of the tile, 2 last chunk).
+struct TmaSched {
+  int4* items = nullptr;
+  int* off = nullptr;
+  int grid = 0;
+  int cap = 0;
+  long long nitems = 0;
+};
+
 struct CscView {
   int* ptr = nullptr;   // [n+1] column pointers of A (= row pointers of A^T)
   int* idx = nullptr;   // [nnz] row index of each entry
@@ -119,6 +130,8 @@ struct gnp_mat {
   gnp::MultiSolver* msolver = nullptr;
   gnp::RedScratch red;       // for gnp_gamma / small reductions
   double* scratch_d = nullptr;   // [n] float64 scratch (column sums)
+  gnp::TmaSched tma[2];      // TMA-gather layer schedule: [0] float32, [1] bfloat16 hidden block
+  bool tma_built = false;
 };
 
 namespace gnp {

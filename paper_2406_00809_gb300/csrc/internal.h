@@ -129,6 +129,19 @@ bool multi_row_ok(const gnp_model* M);
 int multi_row_layers(gnp_model* M, int K, float* H0, float* H1, ColPtr zp, const double* tau_one, const int* ctl,
                      cudaStream_t st);
 
+// The TMA-gather Res-GCONV layer (gconv_tma.cu), for matrices with rows too long for the
+// short-row kernels.  tma_prepare builds the matrix's schedules (host, synchronous; call
+// before any stream capture); tma_active says whether the layers use it (schedule built
+// and GNP_GCONV_TMA=1 in the environment).  tma_layer_launch: one layer Hin -> Hout, or
+// with dec the decoder-fused last layer Hin -> z (column zp, tau for tau / sqrt(n)).
+int tma_prepare(gnp_mat* A);
+bool tma_active(const gnp_mat* A);
+void tma_sched_free(TmaSched& s);
+template <class HT>
+int tma_layer_launch(const gnp_mat* A, int form, bool dec, const float* valhat, const HT* Hin, HT* Hout, ColPtr zp,
+                     const double* tau, double sqrt_n, const int* ctl, const LayerW& lw, const DecW& dw,
+                     cudaStream_t st);
+
 // Make the host copy of the weights current (after training).
 int model_sync_host(gnp_model* M);
 // Everything apply_launch needs that is not a stream operation (host weights, kernel

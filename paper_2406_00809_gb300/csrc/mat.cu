@@ -279,6 +279,8 @@ void gnp_mat_destroy(gnp_mat* A) {
   dev_free(A->csc.perm);
   dev_free(A->scratch_d);
   red_free(A->red);
+  tma_sched_free(A->tma[0]);
+  tma_sched_free(A->tma[1]);
   delete A;
 }
 

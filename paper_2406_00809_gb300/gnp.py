@@ -109,6 +109,7 @@ def lib():
         "gnp_iter_auc": (d, [C.POINTER(C.c_double), i, d]),
         "gnp_time_auc": (d, [C.POINTER(C.c_double), C.POINTER(C.c_double), i, d]),
         "gnp_profile_gconv": (i, [i]),
+        "gnp_kernel_faults": (i, [i]),
         "gnp_gamma_noalloc": (i, [i, C.c_longlong, vp, vp, vp, vp, vp]),
         "gnp_server_create": (i, [C.POINTER(_ServerConfig), pp]),
         "gnp_server_submit": (i, [vp, vp, vp, vp, vp, d, i, C.POINTER(C.c_longlong)]),
@@ -422,6 +423,11 @@ def gnp_train_history(M: Model, steps: int, stream=None):
 
 def gnp_profile_gconv(on: bool):
     _check(lib().gnp_profile_gconv(1 if on else 0))
+
+
+def gnp_kernel_faults(reset: bool = True) -> int:
+    """Bounded device waits that gave up since the last reset (-1: unreadable)."""
+    return int(lib().gnp_kernel_faults(1 if reset else 0))
 
 
 @dataclass

@@ -136,6 +136,7 @@ VARIANTS = {  # Res-GCONV kernel variants, chosen through the library's tuning v
     "row2": {"GNP_GCONV_ROWK": "1", "GNP_ROW_LPR": "2", "GNP_ROW_DB": "5"},
     "tile256": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_ROWS": "256"},  # nnz-balanced tiles
     "tile128": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_ROWS": "128"},
+    "tma": {"GNP_GCONV_ROWK": "0", "GNP_GCONV_TMA": "1"},  # TMA-gather layer (64-row tiles, chunked)
 }
 
 
@@ -146,7 +147,8 @@ VARIANTS = {  # Res-GCONV kernel variants, chosen through the library's tuning v
 def test_apply_all_layer_kernels(gnp, variant, name, hprec, form, monkeypatch):
     """Every Res-GCONV kernel variant (the short-row kernel with four or two lanes per row and
     four or five neighbour loads in flight, the nnz-balanced tile kernel with 256- and 128-row
-    tiles) against the oracle, including
+    tiles, the TMA-gather kernel with its rows copied into shared memory) against the oracle,
+    including
     the decoder-fused last layer and the traced per-layer hidden blocks; every variant
     agrees with the default to float32 rounding.  Rows of more than 16 nonzeros
     (powerlaw12k) always take the tile kernel."""
@@ -168,20 +170,24 @@ def test_apply_all_layer_kernels(gnp, variant, name, hprec, form, monkeypatch):
         hg = hid.cpu().numpy().reshape(L + 1, A.n, 16)
         for l in range(L + 1):
             assert rel(hg[l], Hs[l]) <= F32_TOL, l
-    for k in ("GNP_GCONV_ROWK", "GNP_ROW_LPR", "GNP_ROW_DB", "GNP_GCONV_ROWS"):
+    assert gnp.gnp_kernel_faults(reset=True) == 0
+    for k in ("GNP_GCONV_ROWK", "GNP_ROW_LPR", "GNP_ROW_DB", "GNP_GCONV_ROWS", "GNP_GCONV_TMA"):
         monkeypatch.delenv(k, raising=False)
     z2, _ = run_apply(gnp, A, blob, L, form, hprec, v)
     assert rel(z2, z) <= (2e-6 if hprec == 0 else 1e-2)
 
 
+@pytest.mark.parametrize("tma", ["0", "1"])
 @pytest.mark.parametrize("name", ["convdiff45", "powerlaw12k", "aniso9"])
 @pytest.mark.parametrize("form", [0, 1])
 @pytest.mark.parametrize("hprec", [0, 1])
-def test_layer_apply_matches_oracle(gnp, name, form, hprec):
+def test_layer_apply_matches_oracle(gnp, name, form, hprec, tma, monkeypatch):
     """gnp_layer_apply: one Res-GCONV layer (Eq. 7) on the oracle's own H^l (rounded to the
     hidden block's precision) against the oracle's H^(l+1), per layer; bfloat16 compares
-    with the oracle's layer evaluated on the same rounded input."""
+    with the oracle's layer evaluated on the same rounded input.  tma = 1: the TMA-gather
+    kernel where the matrix has rows of more than 16 nonzeros (powerlaw12k)."""
     import torch
+    monkeypatch.setenv("GNP_GCONV_TMA", tma)
     A = MATS[name]()
     L = 3
     blob = I.init_weights(L, seed=11)
@@ -204,6 +210,7 @@ def test_layer_apply_matches_oracle(gnp, name, form, hprec):
         got = out.float().cpu().numpy().astype(np.float64)
         tol = 8e-3 if hprec else F32_TOL   # bfloat16: one rounding of the stored output (2^-8)
         assert rel(got, ref) <= tol, (name, form, hprec, l, rel(got, ref))
+    assert gnp.gnp_kernel_faults(reset=True) == 0
 
 
 def test_layer_apply_rejects_bad_arguments(gnp):

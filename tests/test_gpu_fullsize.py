@@ -64,8 +64,12 @@ def test_fgmres_identity_convdiff256(gnp, convdiff256):
     np.testing.assert_allclose(info.history, ir["history"], rtol=1e-10, atol=1e-14)
 
 
-def test_apply_and_sampled_layer_powerlaw1m(gnp):
+@pytest.mark.parametrize("tma", ["0", "1"])
+def test_apply_and_sampled_layer_powerlaw1m(gnp, tma, monkeypatch):
+    """The float32 apply on the 2^20-row power-law matrix within 1e-5 of the oracle, and one
+    layer's 2,048 sampled rows from the GPU's own H^0; tma = 1: the TMA-gather kernel."""
     import torch
+    monkeypatch.setenv("GNP_GCONV_TMA", tma)
     A, _ = I.workload("powerlaw1m")
     L = 8
     blob = I.init_weights(L, seed=4)
@@ -91,13 +95,16 @@ def test_apply_and_sampled_layer_powerlaw1m(gnp):
         agg = Ahat.data[s:e] @ H0[Ahat.indices[s:e]]
         ref = np.maximum(H0[i] @ U + agg @ W, 0.0)
         assert np.linalg.norm(H1[i] - ref) <= 1e-5 * max(np.linalg.norm(ref), 1e-3), i
+    assert gnp.gnp_kernel_faults(reset=True) == 0
 
 
-def test_apply_bf16_powerlaw1m(gnp):
+@pytest.mark.parametrize("tma", ["0", "1"])
+def test_apply_bf16_powerlaw1m(gnp, tma, monkeypatch):
     """The bfloat16 hidden block on the 2^20-row power-law matrix: within 2e-2 of the
     float64 oracle, and much closer to the oracle's bfloat16-store emulation (reading c18),
-    which rounds the same stored blocks."""
+    which rounds the same stored blocks; tma = 1: the TMA-gather kernel."""
     import torch
+    monkeypatch.setenv("GNP_GCONV_TMA", tma)
     A, _ = I.workload("powerlaw1m")
     L = 8
     blob = I.init_weights(L, seed=4)
@@ -113,3 +120,4 @@ def test_apply_bf16_powerlaw1m(gnp):
     zb = G.forward(Ahat, v, P, 0, hstore="bf16")
     assert rel(zg, z64) <= 2e-2, rel(zg, z64)
     assert rel(zg, zb) <= 0.25 * rel(zg, z64), (rel(zg, zb), rel(zg, z64))
+    assert gnp.gnp_kernel_faults(reset=True) == 0
