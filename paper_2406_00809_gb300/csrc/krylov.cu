@@ -329,10 +329,9 @@ k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const do
 // The Pythagorean rho_s loses its digits to cancellation once rho_s / ||w_s|| falls below
 // about sqrt(eps) (it can clamp to 0 where the true value is 1e-10 ||w_s||).  Any
 // normalisation of v'_{s+1} keeps w_s = V_s h_s + rho v'_{s+1} exact, so v'_{s+1} is divided
-// by max(rho_s, RHO_FLOOR ||w_s||), and nu_{s+1} (an explicit norm after reorthogonalisation)
-// gives the true subdiagonal rho nu_{s+1} of column s: an exact breakdown shows there, one
-// step later, instead of restarting the cycle early on noise.
-constexpr double RHO_FLOOR = 1e-7;
+// by max(rho_s, RHO_FLOOR ||w_s||) (solver.h), and nu_{s+1} (an explicit norm after
+// reorthogonalisation) gives the true subdiagonal rho nu_{s+1} of column s: an exact
+// breakdown shows there, one step later, instead of restarting the cycle early on noise.
 
 // Finish column j of H_bar (col: j+1 entries, global; hn its subdiagonal) with the whole
 // block, in lagged form (the step counter belongs to the reductions).
@@ -801,14 +800,9 @@ static VNext vnext_args(Solver* S, int dcgs = 0) {
   return VNext{S->V, S->w, S->h1, S->h2, S->st, S->H, S->R, S->cs, S->sn, S->g, S->hist, S->thist, S->hf, dcgs};
 }
 
-// The GNP step's orthogonalisation: CGS2 with its second pass overlapped with the GNP
-// (the default; 78.8 against 88.8 us per step at 65,536 rows), or CGS2 with both passes
-// after the SpMV (GNP_ORTHO=cgs2 in the environment).  Read at every cycle launch; the
-// captured cycle graph is keyed on it.
-static bool dcgs_enabled() {
-  const char* e = getenv("GNP_ORTHO");
-  return !(e && strcmp(e, "cgs2") == 0);
-}
+// The GNP step's orthogonalisation (ortho_overlapped, solver.h): the overlapped schedule
+// takes 78.8 against 88.8 us per step at 65,536 rows.
+static bool dcgs_enabled() { return ortho_overlapped(); }
 
 // Row-per-thread SpMV for matrices without long rows (GNP_SPMV_ROWK=0 in the environment
 // forces the tile kernel, for tuning).

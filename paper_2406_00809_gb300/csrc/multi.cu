@@ -61,7 +61,11 @@ struct MultiSolver {
   unsigned long long g_version = 0;
   int g_m = 0;
   cudaStream_t g_stream = nullptr;
+  bool g_ortho = false;
   cudaStream_t own = nullptr;
+  // overlapped CGS2: the reorthogonalisation stream and its fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 // Per-system strides of the small arrays (sized by the caps).
@@ -192,6 +196,50 @@ k_mencode(double* __restrict__ V, int n, const DevState* st, const int* ctl, dou
     float4* o = reinterpret_cast<float4*>(H0 + e * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) o[q] = make_float4(h[4 * q], h[4 * q + 1], h[4 * q + 2], h[4 * q + 3]);
+  }
+}
+
+// The encoder of overlapped-CGS2 step s >= 1 (s = ctl[0]; V_{s-1} final, h_{s-1} in h):
+// v'_s = (w - V_{s-1} h_{s-1}) / rho_{s-1} per active system into column s, encoded as
+// k_mencode encodes (unit norm, tau = 1).  One thread per (node, system).
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS)
+k_mencode_d(double* __restrict__ V, const double* __restrict__ w, int n, const DevState* st, const int* ctl,
+            const double* __restrict__ h, double sqrt_n, float* __restrict__ H0, const __grid_constant__ EncW ew) {
+  if (!ctl[1]) return;
+  __shared__ double sh[(GNP_MAX_RESTART_MULTI + 2) * K];
+  __shared__ double rinv[K];
+  __shared__ int act[K];
+  const int s = mstep(ctl);
+  for (int k = threadIdx.x; k < s * K; k += blockDim.x) sh[k] = h[k];
+  if (threadIdx.x < K) {
+    rinv[threadIdx.x] = st[threadIdx.x].rho_inv;
+    act[threadIdx.x] = st[threadIdx.x].active;
+  }
+  __syncthreads();
+  double* vout = V + (size_t)s * n * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % K);
+    if (!act[r]) continue;
+    const long long i = e / K;
+    double y = w[e];
+    for (int c = 0; c < s; ++c) y -= V[((size_t)c * n + i) * K + r] * sh[c * K + r];
+    y = y * rinv[r];
+    vout[e] = y;
+    const float u = (float)(y * sqrt_n);
+    float hh[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) hh[c] = ew.b2[c];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+      const float a = fmaxf(fmaf(u, ew.W1[k], ew.b1[k]), 0.0f);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) hh[c] = fmaf(a, ew.W2[k * 16 + c], hh[c]);
+    }
+    float4* o = reinterpret_cast<float4*>(H0 + e * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(hh[4 * q], hh[4 * q + 1], hh[4 * q + 2], hh[4 * q + 3]);
   }
 }
 
@@ -493,12 +541,63 @@ __device__ __forceinline__ void mload_k(const XT* __restrict__ x, int c, double 
   }
 }
 
-template <int K, class XT>
+// RDOT (the overlapped schedule; j = s, V_s final): the last block keeps h_s = V_s^T w in h1
+// and per active system rho_s by Pythagoras, normalised as in the one-system step
+// (RHO_FLOOR), 1/rho, ||w||; a system whose step broke down (w = 0 or not finite) has
+// its column s finished at once with the first-pass values, which ends its cycle.  It
+// then advances the step (ctl[0] = s + 1) and the any-active flag.
+template <int K>
+__device__ __forceinline__ void mrdot_tail(int s, const double* shtot, DevState* st, int* ctl, double* h,
+                                           double* H, double* R, double* cs, double* sn, double* g, double* hist,
+                                           unsigned long long* thist, MStrides ms) {
+  __shared__ double scol[K][GNP_MAX_RESTART_MULTI + 2];
+  __shared__ int anyact;
+  for (int k = threadIdx.x; k < (s + 1) * K; k += blockDim.x) h[k] = shtot[k];
+  if (threadIdx.x == 0) anyact = 0;
+  __syncthreads();
+  if (threadIdx.x < K) {
+    const int r = threadIdx.x;
+    DevState* sr = st + r;
+    if (sr->active) {
+      double bb = 0.0;
+      for (int c = 0; c <= s; ++c) bb = fma(shtot[c * K + r], shtot[c * K + r], bb);
+      const double omega = shtot[(s + 1) * K + r];
+      const double rho = sqrt(fmax(omega - bb, 0.0));
+      const double wn = sqrt(omega);
+      const double rho_n = fmax(rho, RHO_FLOOR * wn);
+      const bool brk = !(rho_n > 0.0) || !isfinite(rho_n) || !isfinite(bb);
+      sr->rho = rho_n;
+      sr->rho_est = rho;
+      sr->rho_inv = brk ? 0.0 : 1.0 / rho_n;
+      sr->wnorm0 = wn;
+      sr->jd = s;
+      if (brk) {
+        for (int c = 0; c <= s; ++c) scol[r][c] = shtot[c * K + r];
+        double* csr = cs + (size_t)r * ms.ms;
+        double* snr = sn + (size_t)r * ms.ms;
+        arnoldi_step_finish(sr, s, scol[r], rho, csr, snr, H + (size_t)r * ms.hs, R + (size_t)r * ms.hs, csr, snr,
+                            g + (size_t)r * ms.gs, hist + (size_t)r * ms.hist, thist + (size_t)r * ms.hist, true,
+                            wn);
+      }
+      if (sr->active) atomicOr(&anyact, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[0] = s + 1;
+    ctl[1] = anyact;
+  }
+}
+
+template <int K, class XT, bool RDOT = false>
 __global__ void __launch_bounds__(RED_THREADS)
 k_mspmv_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-            const XT* __restrict__ Xbase, double* __restrict__ w, int n, const int* __restrict__ ctl,
+            const XT* __restrict__ Xbase, double* __restrict__ w, int n, int* __restrict__ ctl,
             const double* __restrict__ V, DevState* st, double* __restrict__ h1, double* __restrict__ partials,
-            unsigned* counter) {
+            unsigned* counter, double* __restrict__ H = nullptr, double* __restrict__ R = nullptr,
+            double* __restrict__ cs = nullptr, double* __restrict__ sn = nullptr, double* __restrict__ g = nullptr,
+            double* __restrict__ hist = nullptr, unsigned long long* __restrict__ thist = nullptr,
+            MStrides ms = MStrides{0, 0, 0, 0}) {
   if (!ctl[1]) return;
   constexpr int CC = KC / K;
   constexpr int NF = K >= 8 ? 4 : 8;  // nonzeros in flight (registers: NF x K doubles)
@@ -547,9 +646,118 @@ k_mspmv_row(const int* __restrict__ rp, const int* __restrict__ col, const doubl
   }
   if (!last_block_arrive(counter)) return;
   reduce_partials(partials, gridDim.x, Kc * K, shtot);
+  if (threadIdx.x == 0) *counter = 0;
+  if constexpr (RDOT) {
+    mrdot_tail<K>(j, shtot, st, ctl, h1, H, R, cs, sn, g, hist, thist, ms);
+    return;
+  }
   for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h1[k] = shtot[k];
   if (threadIdx.x < K && st[threadIdx.x].active) st[threadIdx.x].wnorm0 = sqrt(shtot[(j + 1) * K + threadIdx.x]);
-  if (threadIdx.x == 0) *counter = 0;
+}
+
+// The reorthogonalisation branch of overlapped step s = ctl[0] >= 1, beside the layers:
+// a_s = V_{s-1}^T v'_s and ||v'_s||^2 per system (mdots with column s standing for v'_s
+// itself); the last block forms nu_s, keeps a_s in ha, and for every active system
+// finishes column s-1 of H_bar, [h_{s-1} + rho_{s-1} a_s; rho_{s-1} nu_s] (lagged:
+// arnoldi_step_finish leaves the step counter to the first pass), then the any-active flag.
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS)
+k_mreorth_dots(const double* __restrict__ V, int n, DevState* st, int* ctl, double* __restrict__ ha,
+               const double* __restrict__ h, double* __restrict__ H, double* __restrict__ R,
+               double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+               double* __restrict__ hist, unsigned long long* __restrict__ thist, MStrides ms,
+               double* __restrict__ partials, unsigned* counter) {
+  if (!ctl[1]) return;
+  constexpr int CC = KC / K;
+  __shared__ double sred[RED_SH];
+  __shared__ double shtot[(GNP_MAX_RESTART_MULTI + 2) * K];
+  __shared__ double scol[K][GNP_MAX_RESTART_MULTI + 2];
+  __shared__ int anyact;
+  const int s = mstep(ctl);
+  const double* y = V + (size_t)s * n * K;
+  const int Kc = s + 1;  // a_s and, as column s, ||v'_s||^2
+  for (int c0 = 0; c0 < Kc; c0 += CC) {
+    double a[KC];
+#pragma unroll
+    for (int k = 0; k < KC; ++k) a[k] = 0.0;
+    mdots<K, CC>(V, y, n, s - 1, c0, Kc, a);
+    block_reduce_kc<false>(a, sred, partials + (size_t)blockIdx.x * Kc * K + c0 * K, min(KC, (Kc - c0) * K));
+  }
+  if (!last_block_arrive(counter)) return;
+  reduce_partials(partials, gridDim.x, Kc * K, shtot);
+  for (int k = threadIdx.x; k < s * K; k += blockDim.x) ha[k] = shtot[k];
+  if (threadIdx.x == 0) anyact = 0;
+  __syncthreads();
+  if (threadIdx.x < K) {
+    const int r = threadIdx.x;
+    DevState* sr = st + r;
+    if (sr->active) {
+      double aa = 0.0;
+      for (int c = 0; c < s; ++c) aa = fma(shtot[c * K + r], shtot[c * K + r], aa);
+      const double nu = sqrt(fmax(shtot[s * K + r] - aa, 0.0));
+      sr->nu_inv = 1.0 / nu;
+      const double rp = sr->rho;  // rho_{s-1}, the normalisation of v'_s
+      for (int c = 0; c < s; ++c) scol[r][c] = fma(rp, shtot[c * K + r], h[c * K + r]);
+      double* csr = cs + (size_t)r * ms.ms;
+      double* snr = sn + (size_t)r * ms.ms;
+      arnoldi_step_finish(sr, s - 1, scol[r], rp * nu, csr, snr, H + (size_t)r * ms.hs, R + (size_t)r * ms.hs, csr,
+                          snr, g + (size_t)r * ms.gs, hist + (size_t)r * ms.hist, thist + (size_t)r * ms.hist, true,
+                          sr->wnorm0);
+      if (sr->active) atomicOr(&anyact, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[1] = anyact;
+    *counter = 0;
+  }
+}
+
+// v_s = (v'_s - V_{s-1} a_s) / nu_s in place for the active systems (after k_mreorth_dots).
+template <int K>
+__global__ void __launch_bounds__(RED_THREADS)
+k_mreorth_update(double* __restrict__ V, int n, const DevState* st, const int* ctl, const double* __restrict__ ha) {
+  if (!ctl[1]) return;
+  __shared__ double sa[(GNP_MAX_RESTART_MULTI + 2) * K];
+  __shared__ double ninv[K];
+  __shared__ int act[K];
+  const int s = mstep(ctl);
+  for (int k = threadIdx.x; k < s * K; k += blockDim.x) sa[k] = ha[k];
+  if (threadIdx.x < K) {
+    ninv[threadIdx.x] = st[threadIdx.x].nu_inv;
+    act[threadIdx.x] = st[threadIdx.x].active;
+  }
+  __syncthreads();
+  double* vs = V + (size_t)s * n * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % K);
+    if (!act[r]) continue;
+    const long long i = e / K;
+    double x = vs[e];
+    for (int c = 0; c < s; ++c) x -= V[((size_t)c * n + i) * K + r] * sa[c * K + r];
+    vs[e] = x * ninv[r];
+  }
+}
+
+// End of an overlapped cycle: the last column of every active system, [h_{m-1}; rho_{m-1}].
+template <int K>
+__global__ void k_mdfinish(DevState* st, const int* ctl, const double* __restrict__ h, double* __restrict__ H,
+                           double* __restrict__ R, double* __restrict__ cs, double* __restrict__ sn,
+                           double* __restrict__ g, double* __restrict__ hist, unsigned long long* __restrict__ thist,
+                           MStrides ms) {
+  __shared__ double scol[K][GNP_MAX_RESTART_MULTI + 2];
+  if (!ctl[1] || threadIdx.x >= K) return;
+  const int r = threadIdx.x;
+  DevState* sr = st + r;
+  if (!sr->active) return;
+  const int s = sr->jd;
+  for (int c = 0; c <= s; ++c) scol[r][c] = h[c * K + r];
+  double* csr = cs + (size_t)r * ms.ms;
+  double* snr = sn + (size_t)r * ms.ms;
+  arnoldi_step_finish(sr, s, scol[r], sr->rho_est, csr, snr, H + (size_t)r * ms.hs, R + (size_t)r * ms.hs, csr, snr,
+                      g + (size_t)r * ms.gs, hist + (size_t)r * ms.hist, thist + (size_t)r * ms.hist, true,
+                      sr->wnorm0);
 }
 
 // (Pass 1, h1 = V_j^T w and ||w||^2, runs inside k_mspmv.)
@@ -747,6 +955,9 @@ void multi_solver_free(MultiSolver* s) {
   if (!s) return;
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   if (s->own) cudaStreamDestroy(s->own);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->fork) cudaEventDestroy(s->fork);
+  if (s->join) cudaEventDestroy(s->join);
   dev_free(s->V);
   dev_free(s->Z);
   dev_free(s->w);
@@ -877,9 +1088,70 @@ static void launch_mgnp(gnp_model* M, MultiSolver* S, cudaStream_t st) {
   }
 }
 
+// The reorthogonalisation stream of the overlapped schedule (highest priority) and its
+// fork/join events, made on first use.
+static int multi_side(MultiSolver* S) {
+  if (S->side) return GNP_OK;
+  int lo = 0, hi = 0;
+  GNP_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  GNP_TRY_CUDA(cudaStreamCreateWithPriority(&S->side, cudaStreamNonBlocking, hi));
+  GNP_TRY_CUDA(cudaEventCreateWithFlags(&S->fork, cudaEventDisableTiming));
+  GNP_TRY_CUDA(cudaEventCreateWithFlags(&S->join, cudaEventDisableTiming));
+  return GNP_OK;
+}
+
+// The overlapped schedule applies to the GNP on the short-row kernels.
+static bool multi_overlapped(const gnp_mat* A, const gnp_model* M) {
+  return M && A->max_deg <= ROW_DMAX_M && multi_row_ok(M) && ortho_overlapped();
+}
+
+// One overlapped restart cycle (the one-system schedule of krylov.cu for K systems): per
+// step the encoder forms v'_j, the second pass of v'_j runs on S->side beside the layers,
+// and k_mspmv_row<RDOT> makes the first pass against the final V_j.
+template <int K>
+static int launch_mcycle_ovl(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cudaStream_t st) {
+  const int n = A->n;
+  const int ntr = (n + MROWS - 1) / MROWS;
+  const int nb = red_blocks(n);
+  const int ncg = dot_blocks(n);
+  const MStrides ms = mstrides(S->m_cap, S->maxit_cap);
+  const double sqrt_n = std::sqrt((double)n);
+  GNP_TRY(multi_side(S));
+  EncW ew;
+  DecW dw;
+  fill_enc_dec(M->w_host, M->cfg.L, ew, dw);
+  const int ne = (int)std::min<long long>(((long long)n * K + RED_THREADS - 1) / RED_THREADS, 8LL * NUM_SMS_GB300);
+  const ColPtr zp{S->Z, sizeof(float) * (size_t)n * K, S->ctl, 0};
+  for (int j = 0; j < m; ++j) {
+    if (j == 0) {
+      k_mencode<K><<<ne, RED_THREADS, 0, st>>>(S->V, n, S->st, S->ctl, sqrt_n, S->Hg[0], ew);
+    } else {
+      k_mencode_d<K><<<ne, RED_THREADS, 0, st>>>(S->V, S->w, n, S->st, S->ctl, S->h2, sqrt_n, S->Hg[0], ew);
+      GNP_TRY_CUDA(cudaEventRecord(S->fork, st));
+      GNP_TRY_CUDA(cudaStreamWaitEvent(S->side, S->fork, 0));
+      k_mreorth_dots<K><<<ncg, RED_THREADS, 0, S->side>>>(S->V, n, S->st, S->ctl, S->h1, S->h2, S->H, S->R, S->cs,
+                                                          S->sn, S->g, S->hist, S->thist, ms, S->red.partials,
+                                                          S->red.counter);
+      k_mreorth_update<K><<<nb, RED_THREADS, 0, S->side>>>(S->V, n, S->st, S->ctl, S->h1);
+      GNP_TRY_CUDA(cudaEventRecord(S->join, S->side));
+    }
+    GNP_TRY(multi_row_layers(M, K, S->Hg[0], S->Hg[1], zp, S->one, S->ctl, st));
+    if (j > 0) GNP_TRY_CUDA(cudaStreamWaitEvent(st, S->join, 0));
+    k_mspmv_row<K, float, true><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl, S->V,
+                                                             S->st, S->h2, S->red.partials, S->red.counter, S->H,
+                                                             S->R, S->cs, S->sn, S->g, S->hist, S->thist, ms);
+  }
+  k_mdfinish<K><<<1, 32, 0, st>>>(S->st, S->ctl, S->h2, S->H, S->R, S->cs, S->sn, S->g, S->hist, S->thist, ms);
+  k_mxupdate<K, float><<<nb, RED_THREADS, 0, st>>>(S->Z, S->x, n, S->st, S->R, S->g, ms, m);
+  k_mresidual<K><<<ntr, TILE, 0, st>>>(A->rp, A->col, A->val, S->x, S->b, S->V, n, S->st, S->ctl, S->done, S->g,
+                                       S->hist, S->thist, ms, S->red.partials, S->red.counter);
+  return check_launch("multi cycle (overlapped CGS2)");
+}
+
 // One restart cycle for all systems: m Arnoldi steps, x update, residual.
 template <int K>
 static int launch_mcycle(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cudaStream_t st) {
+  if (multi_overlapped(A, M)) return launch_mcycle_ovl<K>(A, S, M, m, st);
   const int n = A->n;
   const int ntr = (n + MROWS - 1) / MROWS;
   const int nb = red_blocks(n);
@@ -1010,7 +1282,8 @@ static int solve_multi(gnp_mat* A, const double* B, double* X, int k, gnp_model*
   }
   const unsigned long long ver = M ? model_version(M) : 0ull;
   while (remaining > 0) {
-    if (!S->gexec || S->g_model != M || S->g_version != ver || S->g_m != restart || S->g_stream != st) {
+    if (!S->gexec || S->g_model != M || S->g_version != ver || S->g_m != restart || S->g_stream != st ||
+        S->g_ortho != ortho_overlapped()) {
       if (S->gexec) cudaGraphExecDestroy(S->gexec);
       S->gexec = nullptr;
       cudaGraph_t graph;
@@ -1033,6 +1306,7 @@ static int solve_multi(gnp_mat* A, const double* B, double* X, int k, gnp_model*
       S->g_version = ver;
       S->g_m = restart;
       S->g_stream = st;
+      S->g_ortho = ortho_overlapped();
     }
     for (int r = 0; r < K; ++r) beta_prev[r] = S->st_host[r].beta;
     GNP_TRY_CUDA(cudaGraphLaunch(S->gexec, st));

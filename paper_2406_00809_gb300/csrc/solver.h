@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
 #include "internal.h"
 
@@ -51,6 +52,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 constexpr double BREAKDOWN_REL = 1e-14;
+
+// The overlapped CGS2 schedule of the GNP-preconditioned step (the default; GNP_ORTHO=cgs2
+// in the environment selects CGS2 with both passes after the SpMV).  Read at every cycle
+// launch; the captured cycle graphs are keyed on it.
+inline bool ortho_overlapped() {
+  const char* e = getenv("GNP_ORTHO");
+  return !(e && strcmp(e, "cgs2") == 0);
+}
+
+// The Pythagorean rho_s = sqrt(||w_s||^2 - ||h_s||^2) of the overlapped schedule loses its
+// digits to cancellation once rho_s / ||w_s|| falls below about sqrt(eps); v'_{s+1} is
+// normalised by max(rho_s, RHO_FLOOR ||w_s||) (see krylov.cu).
+constexpr double RHO_FLOOR = 1e-7;
 
 // Grid of the CGS2 kernels: about one row per thread, from one block per SM (small
 // systems) up to four per SM on larger ones.  The float64 pipes of all SMs share the
@@ -236,7 +250,8 @@ __device__ __forceinline__ void arnoldi_step_decide(DevState* st, int j, double 
 __device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double* col, double hn,
                                                     const double* scs, const double* ssn, double* H,
                                                     double* R, double* cs, double* sn, double* g,
-                                                    double* hist, unsigned long long* thist) {
+                                                    double* hist, unsigned long long* thist,
+                                                    bool lagged = false, double wn0 = -1.0) {
   const int ldh = st->m + 1;
   for (int i = 0; i <= j; ++i) H[(size_t)j * ldh + i] = col[i];
   H[(size_t)j * ldh + j + 1] = hn;
@@ -248,7 +263,7 @@ __device__ __forceinline__ void arnoldi_step_finish(DevState* st, int j, double*
     R[(size_t)j * ldh + i] = t;
     finite = finite && isfinite(t);
   }
-  arnoldi_step_decide(st, j, col[j], hn, finite, R, cs, sn, g, hist, thist);
+  arnoldi_step_decide(st, j, col[j], hn, finite, R, cs, sn, g, hist, thist, lagged, wn0);
 }
 
 // arnoldi_step_finish with the whole block (every thread calls it; col, scs, ssn, xs and

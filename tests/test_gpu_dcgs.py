@@ -107,3 +107,30 @@ def test_exact_breakdown(gnp, rtol, monkeypatch):
         r = b - A.to_scipy() @ xx
         assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
     assert np.all(np.isfinite(info.history))
+
+
+@pytest.mark.parametrize("m", [1, 2, 5])
+def test_multi_short_restarts_match_oracle(gnp, m, monkeypatch):
+    """The k-system solver (three systems, untrained GNP, 16 x 16 Poisson) on the
+    overlapped schedule with restart lengths 1, 2 and 5: each system's first 8 residuals
+    agree with the oracle's FGMRES on that system alone to 1e-5, and its status and
+    iteration count equal the two-reduction k-system solve's."""
+    import torch
+    A = I.poisson2d(16)
+    L = 2
+    blob = I.init_weights(L, seed=3)
+    B = np.stack([I.spmv(A, I.gaussian(A.n, seed=s)) for s in (1, 2, 3)], axis=1)
+    Mt = gnp.mat_from_csr(A)
+    Mg = gnp.gnp_create(Mt, gnp.make_config(L=L), blob)
+    runs = {}
+    for ortho in ("dcgs2", "cgs2"):
+        monkeypatch.setenv("GNP_ORTHO", ortho)
+        X = torch.zeros((A.n, 3), dtype=torch.float64, device="cuda")
+        runs[ortho] = gnp.fgmres_solve_multi(Mt, torch.from_numpy(B).cuda(), X, Mg, restart=m, rtol=1e-30,
+                                             maxiters=30)
+    M64 = lambda v: G.forward(G.normalise(A.to_scipy()), v, G.unpack(blob, L), 0)  # noqa: E731
+    for r in range(3):
+        _, ir = K.fgmres(A.to_scipy(), B[:, r], M64, m=m, rtol=1e-30, maxiters=30)
+        got = runs["dcgs2"][r]
+        np.testing.assert_allclose(got.history[:9], np.asarray(ir["history"])[:9], rtol=1e-5)
+        assert got.status == runs["cgs2"][r].status and got.iters == runs["cgs2"][r].iters

@@ -107,13 +107,16 @@ def test_identity_zero_rhs_and_cap(gnp):
         np.testing.assert_allclose(infos[r].history, ir["history"], rtol=1e-10, atol=1e-14)
 
 
+@pytest.mark.parametrize("ortho", ["cgs2", "dcgs2"])
 @pytest.mark.parametrize("k", [2, 4, 8])
-def test_gnp_iterations_within_oracle_band_per_system(gnp, k):
+def test_gnp_iterations_within_oracle_band_per_system(gnp, k, ortho, monkeypatch):
     """Every system of a k-system GNP solve (oracle-trained weights, 64 x 64 problem,
     FGMRES(20), rtol 1e-8) against the oracle's FGMRES on that system alone: the count
     within the spread that float32-level changes of the oracle's z cause, +-2
-    (tests/golden/make_iteration_bands.py), and the true residual meets rtol."""
+    (tests/golden/make_iteration_bands.py), and the true residual meets rtol; under both
+    orthogonalisation schedules (CGS2, and the second pass overlapped with the layers)."""
     import torch
+    monkeypatch.setenv("GNP_ORTHO", ortho)
     A = I.convdiff2d(64, 100.0)
     Mt = gnp.mat_from_csr(A)
     M = gnp.gnp_create(Mt, gnp.make_config(L=8), golden_weights())
