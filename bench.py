@@ -143,7 +143,7 @@ def gconv_source_hash():
     is used only while they are unchanged)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("gconv.cu", "gconv_common.cuh", "common.cuh", "internal.h"):
+    for f in ("gconv.cu", "gconv_rows.cuh", "gconv_common.cuh", "common.cuh", "internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2406_00809_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
