@@ -575,12 +575,15 @@ def run_ours(args, wl):
 def run_serve(args):
     """--workload serve: the continuous-batching server under a Poisson stream of solve
     requests (paper_2406_00809_gb300.serve_bench): a pool of 12 problems (2-D Poisson,
-    2-D convection-diffusion, power-law general sparse in turn; n log-uniform in [1e4, 2e6]),
-    each with its own GNP trained on its own matrix for a stated budget of Adam steps and
-    applied with a bfloat16 hidden block; `serve_requests` requests per rate, FGMRES(30) to
-    rtol 1e-8, at most 1000 iterations; rates at the given multiples of the sequential
-    capacity (1 / mean latency of each pool problem solved alone).  One JSON line: value =
-    p99 latency at the first rate; every rate's p50/p99, solves/s and status counts."""
+    2-D convection-diffusion, power-law general sparse in turn; n log-uniform in
+    [1e4, 2.5e5]), each with its own GNP trained on its own matrix for a stated budget of
+    Adam steps and applied with a bfloat16 hidden block; `serve_requests` requests per rate,
+    FGMRES(30) to rtol 1e-8, at most 3000 iterations; rates at the given multiples of the
+    sequential capacity (1 / mean latency of each pool problem solved alone).  The
+    power-law family here takes the diagonal shift 1.25 x its spectral radius (spectrum
+    right of the origin): with the configured cond ~1e6 shift it stagnates with and without
+    the GNP, so its requests could never finish.  One JSON line: value = p99 latency at the
+    first rate; every rate's p50/p99, solves/s and status counts."""
     import torch
     from paper_2406_00809_gb300 import build
     from paper_2406_00809_gb300 import serve_bench as SB
@@ -588,9 +591,9 @@ def run_serve(args):
     torch.cuda.set_device(local)
     build.build()
     from paper_2406_00809_gb300 import gnp as g
-    sa = argparse.Namespace(requests=args.serve_requests, pool=12, nmin=1e4, nmax=2e6,
+    sa = argparse.Namespace(requests=args.serve_requests, pool=12, nmin=1e4, nmax=2.5e5,
                             train_steps=args.serve_train_steps, batch=8, hprec="bf16", rtol=1e-8,
-                            maxiters=1000, max_active=64, max_gb=120.0, seed=0)
+                            maxiters=3000, max_active=64, max_gb=120.0, seed=0, powerlaw_shift=1.25)
     rng = np.random.default_rng(0)
     t0 = time.perf_counter()
     pool = SB.build_pool(g, sa, rng)
@@ -611,8 +614,10 @@ def run_serve(args):
             "steps": len(rates), "warmup": 1, "ms_per_step": first["p99_s"] * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic",
             "config": {"workload": "serving: Poisson stream of solve requests, 12-problem pool over 2-D Poisson, "
-                                   "2-D convection-diffusion and power-law general sparse, n log-uniform in "
-                                   "[1e4, 2e6], own GNP per problem (bfloat16 hidden), FGMRES(30) to 1e-8",
+                                   "2-D convection-diffusion and power-law general sparse (diagonal shift 1.25 x "
+                                   "spectral radius), n log-uniform in [1e4, 2.5e5], own GNP per problem "
+                                   "(bfloat16 hidden), FGMRES(30) to 1e-8",
+                       "powerlaw_shift_fraction": sa.powerlaw_shift, "n_range": [sa.nmin, sa.nmax],
                        "requests_per_rate": sa.requests, "loads": args.serve_loads,
                        "train_steps_per_problem": sa.train_steps, "maxiters": sa.maxiters,
                        "parallelism": f"replicas{ws}"},

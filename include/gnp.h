@@ -341,9 +341,11 @@ double gnp_time_auc(const double* res_history, const double* time_history, int l
  * serves any number of right-hand sides; here also many matrices at once).  A server
  * thread admits queued requests in FIFO order while fewer than max_active run and their
  * device-memory footprint (Krylov basis n*(restart+1) float64, directions n*restart
- * float32, GNP hidden blocks 2*n*16 float32, reduction scratch) fits in max_bytes; each
- * round launches one CUDA graph holding the next restart cycle of every running
- * request.  Results are the same as a lone fgmres_solve of the request. */
+ * float32, GNP hidden blocks 2*n*16 float32, reduction scratch) fits in max_bytes.  Every
+ * running request has its own stream and its restart cycle captured as a CUDA graph;
+ * whenever one of its cycles ends, the server applies its stopping rules and launches its
+ * next cycle or retires it at once, without waiting for the other requests.  Results
+ * are the same as a lone fgmres_solve of the request. */
 typedef struct gnp_server_config {
   size_t max_bytes; /* device-memory budget for the running requests' workspaces */
   int max_active;   /* requests running at once (slots) */
@@ -353,7 +355,8 @@ typedef struct gnp_server_config {
 typedef struct gnp_server_stats_t {
   int queued, active;
   size_t used_bytes;
-  long long rounds, completed, max_active_seen;
+  long long rounds; /* restart cycles launched */
+  long long completed, max_active_seen;
 } gnp_server_stats_t;
 
 int gnp_server_create(const gnp_server_config* cfg, gnp_server** out);

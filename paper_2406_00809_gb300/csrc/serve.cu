@@ -1,14 +1,15 @@
 // Continuous-batching solve server: a persistent host loop that runs many GNP-FGMRES
 // solves at once on one GPU.  Each request brings its own matrix, model, right-hand
 // side and solution buffer.  Requests wait in a FIFO queue and are admitted as slots and
-// device memory free up; an admitted request gets its own Krylov workspace and GNP
-// scratch (the model's weights and A_hat are shared read-only), and its restart cycle
-// is captured once as a CUDA graph.  Every round the loop launches ONE graph holding the
-// next cycle of every active request as parallel branches (their work overlaps on the
-// device), followed by copies of their solver states to pinned host memory; it then
-// applies the stopping rules to each request, retires the finished ones and admits new
-// ones.  A request's result does not depend on what else runs: every kernel reads only
-// its own request's data and all reductions have a fixed order.
+// device memory free up; an admitted request gets its own Krylov workspace, GNP scratch
+// (the model's weights and A_hat are shared read-only) and stream, and its restart cycle
+// is captured once as a CUDA graph.  Each running request has one cycle in flight on its
+// stream: the graph, then a copy of its solver state to pinned host memory and an event.
+// The loop polls the events; the moment a request's cycle ends it applies that request's
+// stopping rules and either launches its next cycle or retires it, freeing its slot for
+// the queue, so no request waits for another's cycle (the requests' work overlaps on the
+// device).  A request's result does not depend on what else runs: every kernel reads
+// only its own request's data and all reductions have a fixed order.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -38,8 +39,11 @@ struct Request {
   Solver* S = nullptr;
   ApplyWs ws;
   cudaGraph_t cycle = nullptr;
+  cudaGraphExec_t exec = nullptr;  // the instantiated cycle
+  cudaStream_t stream = nullptr;   // the request's own stream
+  cudaEvent_t ev = nullptr;        // recorded after each cycle's state copy
   CycleCtl ctl;
-  DevState* mirror = nullptr;  // pinned copy of the device state, written by the round graph
+  DevState* mirror = nullptr;  // pinned copy of the device state, written after each cycle
   double beta = 0.0;
   // result: `result` is set by the loop thread, `status` (read by poll/wait) only under
   // the server lock when the request is published as finished
@@ -51,7 +55,6 @@ struct Request {
 struct Server {
   gnp_server_config cfg{};
   int device = 0;
-  cudaStream_t stream = nullptr;
   std::thread loop;
   std::mutex mu;
   std::condition_variable cv;       // wakes the loop
@@ -63,10 +66,7 @@ struct Server {
   long long next_ticket = 1;
   size_t used_bytes = 0;
   bool stop = false;
-  // the round graph, rebuilt when the active set changes
-  cudaGraphExec_t round = nullptr;
-  bool round_dirty = true;
-  // statistics
+  // statistics (`rounds`: restart cycles launched)
   long long rounds = 0, completed = 0, admitted = 0, max_active_seen = 0;
   int error = GNP_OK;
   char errmsg[256] = {0};
@@ -77,8 +77,14 @@ static size_t request_footprint(const gnp_mat* A, int m, int maxiters) {
 }
 
 static void release(Request* r) {
+  if (r->exec) cudaGraphExecDestroy(r->exec);
+  r->exec = nullptr;
   if (r->cycle) cudaGraphDestroy(r->cycle);
   r->cycle = nullptr;
+  if (r->ev) cudaEventDestroy(r->ev);
+  r->ev = nullptr;
+  if (r->stream) cudaStreamDestroy(r->stream);
+  r->stream = nullptr;
   solver_free(r->S);
   r->S = nullptr;
   apply_ws_free(r->ws);
@@ -94,21 +100,29 @@ static void finish(Server* sv, Request* r, int status) {
   r->info.seconds = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
 }
 
-// Allocate the request's workspace, run its initial residual, capture its cycle graph.
-// Returns true when the request is still running afterwards.
+// Allocate the request's workspace and stream, run its initial residual, capture and
+// instantiate its cycle graph.  Returns true when the request is still running afterwards.
 static bool setup(Server* sv, Request* r) {
-  int s = solver_create(r->A->n, r->m, r->maxiters, &r->S);
+  (void)sv;
+  int s = GNP_OK;
+  if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("server: stream or event creation failed");
+    s = GNP_ERR_CUDA;
+  }
+  if (s == GNP_OK) s = solver_create(r->A->n, r->m, r->maxiters, &r->S);
   if (s == GNP_OK && r->M) s = apply_ws_alloc(r->ws, r->A->n);
   if (s == GNP_OK && cudaMallocHost(reinterpret_cast<void**>(&r->mirror), sizeof(DevState)) != cudaSuccess) {
     set_error("server: cudaMallocHost failed");
     s = GNP_ERR_OOM;
   }
+  cudaStream_t st = r->stream;
   if (s == GNP_OK && r->M) s = apply_prepare(r->M);
-  if (s == GNP_OK) s = solve_init_launch(r->A, r->S, r->b, r->x, r->rtol, r->maxiters, r->m, 0.0, sv->stream);
-  if (s == GNP_OK && cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost,
-                                     sv->stream) != cudaSuccess)
+  if (s == GNP_OK) s = solve_init_launch(r->A, r->S, r->b, r->x, r->rtol, r->maxiters, r->m, 0.0, st);
+  if (s == GNP_OK && cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost, st) !=
+                         cudaSuccess)
     s = GNP_ERR_CUDA;
-  if (s == GNP_OK && cudaStreamSynchronize(sv->stream) != cudaSuccess) {
+  if (s == GNP_OK && cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("server: %s", cudaGetErrorString(cudaGetLastError()));
     s = GNP_ERR_CUDA;
   }
@@ -120,8 +134,8 @@ static bool setup(Server* sv, Request* r) {
   r->beta = hs.beta;
   r->info.iters = 0;
   if (hs.bnorm == 0.0) {
-    cudaMemsetAsync(r->x, 0, sizeof(double) * r->A->n, sv->stream);
-    cudaStreamSynchronize(sv->stream);
+    cudaMemsetAsync(r->x, 0, sizeof(double) * r->A->n, st);
+    cudaStreamSynchronize(st);
     finish(sv, r, GNP_OK);
     return false;
   }
@@ -139,7 +153,7 @@ static bool setup(Server* sv, Request* r) {
     return false;
   }
   // capture the restart cycle once; its device-side step state makes it replayable
-  if (cudaStreamBeginCapture(sv->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     set_error("server: begin capture failed");
     finish(sv, r, GNP_ERR_CUDA);
     return false;
@@ -148,45 +162,28 @@ static bool setup(Server* sv, Request* r) {
   P.kind = r->M ? GNP_PRECOND_GNP : GNP_PRECOND_IDENTITY;
   P.M = r->M;
   P.key = r->M;
-  s = launch_cycle(r->A, r->S, P, r->m, r->b, r->x, sv->stream, false, r->M ? &r->ws : nullptr);
-  cudaError_t ce = cudaStreamEndCapture(sv->stream, &r->cycle);
+  s = launch_cycle(r->A, r->S, P, r->m, r->b, r->x, st, false, r->M ? &r->ws : nullptr);
+  cudaError_t ce = cudaStreamEndCapture(st, &r->cycle);
+  if (ce == cudaSuccess && s == GNP_OK) ce = cudaGraphInstantiate(&r->exec, r->cycle, 0);
   if (s != GNP_OK || ce != cudaSuccess) {
-    if (ce != cudaSuccess) set_error("server: capture failed: %s", cudaGetErrorString(ce));
+    if (ce != cudaSuccess) set_error("server: capture or instantiation failed: %s", cudaGetErrorString(ce));
     finish(sv, r, s != GNP_OK ? s : GNP_ERR_CUDA);
     return false;
   }
   return true;
 }
 
-static int build_round(Server* sv) {
-  if (sv->round) cudaGraphExecDestroy(sv->round);
-  sv->round = nullptr;
-  cudaGraph_t g;
-  GNP_TRY_CUDA(cudaGraphCreate(&g, 0));
-  int s = GNP_OK;
-  for (Request* r : sv->running) {
-    cudaGraphNode_t child, copy;
-    cudaError_t e = cudaGraphAddChildGraphNode(&child, g, nullptr, 0, r->cycle);
-    if (e == cudaSuccess)
-      e = cudaGraphAddMemcpyNode1D(&copy, g, &child, 1, r->mirror, r->S->st, sizeof(DevState),
-                                   cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-      set_error("server: building the round graph: %s", cudaGetErrorString(e));
-      s = GNP_ERR_CUDA;
-      break;
-    }
+// Start the request's next restart cycle on its stream: the cycle, the copy of its state to
+// pinned memory, the event the loop polls.
+static int launch_next(Server* sv, Request* r) {
+  if (cudaGraphLaunch(r->exec, r->stream) != cudaSuccess ||
+      cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost, r->stream) != cudaSuccess ||
+      cudaEventRecord(r->ev, r->stream) != cudaSuccess) {
+    set_error("server: cycle launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return GNP_ERR_CUDA;
   }
-  if (s == GNP_OK) {
-    cudaError_t e = cudaGraphInstantiate(&sv->round, g, 0);
-    if (e != cudaSuccess) {
-      set_error("server: instantiating the round graph: %s", cudaGetErrorString(e));
-      s = GNP_ERR_CUDA;
-      sv->round = nullptr;
-    }
-  }
-  cudaGraphDestroy(g);
-  sv->round_dirty = false;
-  return s;
+  ++sv->rounds;
+  return GNP_OK;
 }
 
 static void fill_result(Request* r) {
@@ -227,55 +224,52 @@ static void server_loop(Server* sv) {
       continue;
     }
     lk.unlock();
+    bool progressed = !fresh.empty();
     for (Request* r : fresh) {
       ++sv->admitted;
-      if (setup(sv, r)) {
+      if (setup(sv, r) && launch_next(sv, r) == GNP_OK) {
         sv->running.push_back(r);
-        sv->round_dirty = true;
       } else {
+        if (r->result == GNP_OK && r->exec) finish(sv, r, GNP_ERR_CUDA);  // the first launch failed
         fill_result(r);
         ended.push_back(r);
       }
     }
-    if (!sv->running.empty()) {
-      sv->max_active_seen = std::max<long long>(sv->max_active_seen, (long long)sv->running.size());
-      int s = GNP_OK;
-      if (sv->round_dirty) s = build_round(sv);
-      std::vector<double> beta_prev;
-      for (Request* r : sv->running) beta_prev.push_back(r->beta);
-      if (s == GNP_OK && cudaGraphLaunch(sv->round, sv->stream) != cudaSuccess) {
-        set_error("server: round launch failed");
-        s = GNP_ERR_CUDA;
+    sv->max_active_seen = std::max<long long>(sv->max_active_seen, (long long)sv->running.size());
+    // every request whose cycle has ended: stopping rules, then its next cycle or retirement
+    std::vector<Request*> still;
+    for (Request* r : sv->running) {
+      const cudaError_t q = cudaEventQuery(r->ev);
+      if (q == cudaErrorNotReady) {
+        still.push_back(r);
+        continue;
       }
-      if (s == GNP_OK && cudaStreamSynchronize(sv->stream) != cudaSuccess) {
-        set_error("server: round failed: %s", cudaGetErrorString(cudaGetLastError()));
-        s = GNP_ERR_CUDA;
-      }
-      ++sv->rounds;
-      std::vector<Request*> still;
-      for (size_t k = 0; k < sv->running.size(); ++k) {
-        Request* r = sv->running[k];
-        int status = GNP_OK;
-        bool end = true;
-        if (s != GNP_OK) {
-          status = s;
-        } else {
-          ++r->ctl.cycles;
-          const DevState& hs = *r->mirror;
-          end = cycle_after(hs, beta_prev[k], r->maxiters, r->ctl, &status);
-          r->beta = hs.beta;
-        }
-        if (end) {
-          fill_result(r);
-          finish(sv, r, status);
-          ended.push_back(r);
-        } else {
-          still.push_back(r);
+      progressed = true;
+      int status = GNP_OK;
+      bool end = true;
+      if (q != cudaSuccess) {
+        set_error("server: cycle failed: %s", cudaGetErrorString(q));
+        status = GNP_ERR_CUDA;
+      } else {
+        ++r->ctl.cycles;
+        const DevState& hs = *r->mirror;
+        const double beta_prev = r->beta;
+        end = cycle_after(hs, beta_prev, r->maxiters, r->ctl, &status);
+        r->beta = hs.beta;
+        if (!end && launch_next(sv, r) != GNP_OK) {
+          status = GNP_ERR_CUDA;
+          end = true;
         }
       }
-      if (still.size() != sv->running.size()) sv->round_dirty = true;
-      sv->running.swap(still);
+      if (end) {
+        fill_result(r);
+        finish(sv, r, status);
+        ended.push_back(r);
+      } else {
+        still.push_back(r);
+      }
     }
+    sv->running.swap(still);
     for (Request* r : ended) release(r);
     lk.lock();
     for (Request* r : ended) {
@@ -285,6 +279,10 @@ static void server_loop(Server* sv) {
     }
     sv->n_active = (int)sv->running.size();
     if (!ended.empty()) sv->done_cv.notify_all();
+    if (!progressed) {
+      // no cycle ended and nothing was admitted: wait a little (new requests wake the loop)
+      sv->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
   }
 }
 
@@ -306,11 +304,6 @@ int gnp_server_create(const gnp_server_config* cfg, gnp_server** out) {
   Server* sv = new Server();
   sv->cfg = *cfg;
   cudaGetDevice(&sv->device);
-  if (cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
-    delete sv;
-    set_error("gnp_server_create: cudaStreamCreate failed");
-    return GNP_ERR_CUDA;
-  }
   sv->loop = std::thread(server_loop, sv);
   *out = new gnp_server{sv};
   return GNP_OK;
@@ -419,12 +412,10 @@ void gnp_server_destroy(gnp_server* h) {
   }
   sv->cv.notify_all();
   if (sv->loop.joinable()) sv->loop.join();
-  if (sv->round) cudaGraphExecDestroy(sv->round);
   for (auto& kv : sv->all) {
     release(kv.second);
     delete kv.second;
   }
-  cudaStreamDestroy(sv->stream);
   delete sv;
   delete h;
 }

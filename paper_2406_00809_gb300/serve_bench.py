@@ -4,7 +4,8 @@
         [--pool 12] [--nmin 1e4] [--nmax 2e6] [--train-steps 300] [--hprec bf16]
 
 A pool of `pool` problems is built first (not timed): the three generator families
-(2-D Poisson, 2-D convection-diffusion, power-law general sparse) in turn, n drawn
+(2-D Poisson, 2-D convection-diffusion, power-law general sparse, the latter with the
+diagonal shift --powerlaw-shift times its spectral radius when given) in turn, n drawn
 log-uniformly in [nmin, nmax] (grid side round(sqrt(n)) for the 2-D families), each
 with its own GNP (8 layers, hidden 16) trained for `train_steps` Adam steps on its own
 matrix and then applied with a bfloat16 hidden block.  Each of the `requests` solves
@@ -50,7 +51,7 @@ def build_pool(g, args, rng):
         elif fam == "convdiff":
             A = I.convdiff2d(max(8, int(round(np.sqrt(n)))), 100.0)
         else:
-            A = I.powerlaw(max(64, int(n)), seed=100 + i)
+            A = I.powerlaw(max(64, int(n)), seed=100 + i, shift_fraction=getattr(args, "powerlaw_shift", None))
         Mt = g.mat_from_csr(A)
         M = g.gnp_create(Mt, g.make_config(L=8, batch=args.batch, arnoldi_m=20, seed=i),
                          I.init_weights(8, seed=i))
@@ -157,6 +158,9 @@ def main():
     ap.add_argument("--hprec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--maxiters", type=int, default=1000)
+    ap.add_argument("--powerlaw-shift", type=float, default=None,
+                    help="diagonal shift of the power-law family as a fraction of its spectral radius "
+                         "(default: the calibrated cond ~1e6 shift)")
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--max-gb", type=float, default=120.0)
     ap.add_argument("--seed", type=int, default=0)
