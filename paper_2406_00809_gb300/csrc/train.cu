@@ -689,6 +689,114 @@ k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, con
   }
 }
 
+// The same with one thread per row.  Every lane of a warp then needs the same weight at
+// the same time, so each 16-byte weight load from shared memory is one broadcast (the quad
+// form above reads four different weight columns per warp load, which made the shared-memory
+// pipe its limit).  The row's AGG, X and G (and then Gp, Y, local) stay in registers;
+// the weights do not.  Same arithmetic per output as the quad form (inputs in the same
+// order), so the results are identical.
+template <int FORM>
+__global__ void __launch_bounds__(256)
+k_layer_bwd_row1(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G, long long R,
+                 const float* __restrict__ lw, float* __restrict__ Gp_out, float* __restrict__ Y_out,
+                 float* __restrict__ local_out) {
+  __shared__ __align__(16) float sU[256], sW[256], sUt[256], sWt[256];
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) {
+    const int c = k >> 4, o = k & 15;
+    sU[k] = lw[k];
+    sW[k] = lw[256 + k];
+    sUt[o * 16 + c] = lw[k];
+    sWt[o * 16 + c] = lw[256 + k];
+  }
+  __syncthreads();
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const float4* W4 = reinterpret_cast<const float4*>(sW);
+  const float4* U4 = reinterpret_cast<const float4*>(sU);
+  const float4* Wt4 = reinterpret_cast<const float4*>(sWt);
+  const float4* Ut4 = reinterpret_cast<const float4*>(sUt);
+  float a[16], x[16], g[16];
+  {
+    const float4* ap = reinterpret_cast<const float4*>(AGG + r * 16);
+    const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
+    const float4* gq = reinterpret_cast<const float4*>(G + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 t = __ldg(ap + q);
+      a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
+      const float4 u = FORM == GNP_LAYER_PAPER ? __ldg(xp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+      const float4 v = __ldg(gq + q);
+      g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+    }
+  }
+  // pre = AGG W (+ X U), accumulated per output over the inputs in order, as the quad form
+  float gp[16];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      const float4 w = W4[c * 4 + j];
+      pre.x = fmaf(a[c], w.x, pre.x);
+      pre.y = fmaf(a[c], w.y, pre.y);
+      pre.z = fmaf(a[c], w.z, pre.z);
+      pre.w = fmaf(a[c], w.w, pre.w);
+    }
+    if (FORM == GNP_LAYER_PAPER) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const float4 u = U4[c * 4 + j];
+        pre.x = fmaf(x[c], u.x, pre.x);
+        pre.y = fmaf(x[c], u.y, pre.y);
+        pre.z = fmaf(x[c], u.z, pre.z);
+        pre.w = fmaf(x[c], u.w, pre.w);
+      }
+    }
+    gp[4 * j] = pre.x > 0.f ? g[4 * j] : 0.f;
+    gp[4 * j + 1] = pre.y > 0.f ? g[4 * j + 1] : 0.f;
+    gp[4 * j + 2] = pre.z > 0.f ? g[4 * j + 2] : 0.f;
+    gp[4 * j + 3] = pre.w > 0.f ? g[4 * j + 3] : 0.f;
+  }
+  {
+    float4* o = reinterpret_cast<float4*>(Gp_out + r * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
+  }
+  // Y = Gp W^T, local = Gp U^T (paper form) or G (residual form)
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 loc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float4 w = Wt4[k * 4 + j];
+      y.x = fmaf(gp[k], w.x, y.x);
+      y.y = fmaf(gp[k], w.y, y.y);
+      y.z = fmaf(gp[k], w.z, y.z);
+      y.w = fmaf(gp[k], w.w, y.w);
+      if (FORM == GNP_LAYER_PAPER) {
+        const float4 u = Ut4[k * 4 + j];
+        loc.x = fmaf(gp[k], u.x, loc.x);
+        loc.y = fmaf(gp[k], u.y, loc.y);
+        loc.z = fmaf(gp[k], u.z, loc.z);
+        loc.w = fmaf(gp[k], u.w, loc.w);
+      }
+    }
+    reinterpret_cast<float4*>(Y_out + r * 16)[j] = y;
+    reinterpret_cast<float4*>(local_out + r * 16)[j] =
+        FORM == GNP_LAYER_PAPER ? loc : make_float4(g[4 * j], g[4 * j + 1], g[4 * j + 2], g[4 * j + 3]);
+  }
+}
+
+// The layer backward of the training step: one thread per row (the default), or the quad
+// form (GNP_TRAIN_BWD=quad in the environment, for comparison).
+static bool bwd_quad() {
+  static const char* e = getenv("GNP_TRAIN_BWD");
+  static const bool q = e && strcmp(e, "quad") == 0;
+  return q;
+}
+
 // Encoder backward (thread per row): r1 = ReLU(a1) and da1 = (dH0 W2^T) * 1[a1 > 0].
 __global__ void __launch_bounds__(256)
 k_enc_bwd(const float* __restrict__ u, const float* __restrict__ dH0, long long R, const float* __restrict__ w,
@@ -1133,6 +1241,128 @@ static int forward_batch(gnp_model* M, const float* b, cudaStream_t st) {
   return check_launch("forward_batch");
 }
 
+// k_wgrad for P x Q = 512 outputs (the layer's [X | AGG]^T Gp, 32 x 16, and the decoder's
+// 16 x 32) with a 4 x 4 register tile per lane: one warp owns the whole output, lane l
+// the rows 4 (l / (Q/4)) .. +3 and columns 4 (l % (Q/4)) .. +3, so a staged row costs the
+// warp two 16-byte shared loads for 16 multiply-adds per lane (k_wgrad's one output
+// column per thread was bound by its shared-memory loads).  The 8 warps split each tile's
+// rows; their sums meet in shared memory in warp order.  Same partials layout as k_wgrad
+// (row P = the bias), reduced by k_wgrad_final.
+template <int P, int Q>
+__global__ void __launch_bounds__(256)
+k_wgrad_t(const float* __restrict__ A, const float* __restrict__ A2, const float* __restrict__ Bm, long long R,
+          float* __restrict__ partials) {
+  using S = WgShape<P, Q>;
+  constexpr int NQB = Q / 4, NPB = P / 4;
+  static_assert(P % 4 == 0 && Q % 4 == 0 && NPB * NQB == 32, "one 4 x 4 tile per lane");
+  constexpr int NOUT = (P + 1) * Q;
+  __shared__ __align__(16) float sA[WG_KT * P + 4];
+  __shared__ __align__(16) float sB[WG_KT * Q];
+  __shared__ float sred[8 * NOUT];
+  const int t = threadIdx.x;
+  const int w = t >> 5, lane = t & 31;
+  const int pb = lane / NQB, qb = lane % NQB;
+  const long long r0 = (long long)blockIdx.x * WG_CHUNK;
+  const int rows = (int)min((long long)WG_CHUNK, R - r0);
+  const int ntiles = (rows + WG_KT - 1) / WG_KT;
+  float acc[4][4];
+  float bacc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+  float4 ra[S::LA], rb[S::LB];
+  auto load = [&](int kt) {
+    const int nr = min(WG_KT, rows - kt * WG_KT);
+    const float4* b4 = reinterpret_cast<const float4*>(Bm + (r0 + (long long)kt * WG_KT) * Q);
+    if (A2 == nullptr) {
+      const float4* a4 = reinterpret_cast<const float4*>(A + (r0 + (long long)kt * WG_KT) * P);
+#pragma unroll
+      for (int u = 0; u < S::LA; ++u) {
+        const int i = t + 256 * u;
+        ra[u] = (i < S::A4 && i < nr * P / 4) ? __ldg(a4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    } else {
+      constexpr int H4 = P / 8;
+      const float4* a4 = reinterpret_cast<const float4*>(A + (r0 + (long long)kt * WG_KT) * (P / 2));
+      const float4* c4 = reinterpret_cast<const float4*>(A2 + (r0 + (long long)kt * WG_KT) * (P / 2));
+#pragma unroll
+      for (int u = 0; u < S::LA; ++u) {
+        const int i = t + 256 * u;
+        const int row = i / (2 * H4), k = i % (2 * H4);
+        const float4* src = k < H4 ? a4 + row * H4 + k : c4 + row * H4 + (k - H4);
+        ra[u] = (i < S::A4 && i < nr * P / 4) ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < S::LB; ++u) {
+      const int i = t + 256 * u;
+      rb[u] = (i < S::B4 && i < nr * Q / 4) ? __ldg(b4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  load(0);
+  for (int kt = 0; kt < ntiles; ++kt) {
+    __syncthreads();  // the previous tile is consumed
+#pragma unroll
+    for (int u = 0; u < S::LA; ++u) {
+      const int i = t + 256 * u;
+      if (i < S::A4) reinterpret_cast<float4*>(sA)[i] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < S::LB; ++u) {
+      const int i = t + 256 * u;
+      if (i < S::B4) reinterpret_cast<float4*>(sB)[i] = rb[u];
+    }
+    __syncthreads();
+    if (kt + 1 < ntiles) load(kt + 1);
+    // rows past the end of the chunk were staged as zeros and add nothing
+#pragma unroll 4
+    for (int rr = w; rr < WG_KT; rr += 8) {
+      const float4 av = *reinterpret_cast<const float4*>(sA + rr * P + 4 * pb);
+      const float4 bv = *reinterpret_cast<const float4*>(sB + rr * Q + 4 * qb);
+      const float a4[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        acc[i][0] = fmaf(a4[i], bv.x, acc[i][0]);
+        acc[i][1] = fmaf(a4[i], bv.y, acc[i][1]);
+        acc[i][2] = fmaf(a4[i], bv.z, acc[i][2]);
+        acc[i][3] = fmaf(a4[i], bv.w, acc[i][3]);
+      }
+      if (pb == 0) {
+        bacc[0] += bv.x;
+        bacc[1] += bv.y;
+        bacc[2] += bv.z;
+        bacc[3] += bv.w;
+      }
+    }
+  }
+  float* my = sred + w * NOUT;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) my[(4 * pb + i) * Q + 4 * qb + k] = acc[i][k];
+  if (pb == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) my[P * Q + 4 * qb + k] = bacc[k];
+  }
+  __syncthreads();
+  float* out = partials + (size_t)blockIdx.x * NOUT;
+  for (int e = t; e < NOUT; e += 256) {
+    float v = 0.f;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) v += sred[ww * NOUT + e];
+    out[e] = v;
+  }
+}
+
+// The weight-gradient reduction: the tiled form where P x Q = 512 (GNP_TRAIN_WGRAD=col in
+// the environment keeps the one-column-per-thread form, for comparison).
+static bool wgrad_col() {
+  static const char* e = getenv("GNP_TRAIN_WGRAD");
+  static const bool c = e && strcmp(e, "col") == 0;
+  return c;
+}
+
 template <int P, int Q>
 static int wgrad(TrainState* T, const float* A, const float* Bm, float* Wout, float* bias, cudaStream_t st,
                  const float* A2 = nullptr) {
@@ -1144,7 +1374,12 @@ static int wgrad(TrainState* T, const float* A, const float* Bm, float* Wout, fl
     GNP_TRY(dev_alloc(&T->partials, (size_t)nblk * 33 * 32));
     T->part_cap = nblk * 33 * 32;
   }
-  k_wgrad<P, Q><<<nblk, 256, 0, st>>>(A, A2, Bm, T->R, T->partials);
+  if constexpr (P * Q == 512 && P % 4 == 0 && Q % 4 == 0) {
+    if (!wgrad_col()) k_wgrad_t<P, Q><<<nblk, 256, 0, st>>>(A, A2, Bm, T->R, T->partials);
+    else k_wgrad<P, Q><<<nblk, 256, 0, st>>>(A, A2, Bm, T->R, T->partials);
+  } else {
+    k_wgrad<P, Q><<<nblk, 256, 0, st>>>(A, A2, Bm, T->R, T->partials);
+  }
   k_wgrad_final<<<(PQ * 32 + 255) / 256, 256, 0, st>>>(T->partials, nblk, P, Q, Wout, bias);
   return check_launch("wgrad");
 }
@@ -1171,10 +1406,18 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
     const float* X = T->Hs + (size_t)l * R * 16;
     const float* AG = T->AGG + (size_t)l * R * 16;
     const float* lw = M->w_dev + layer_off(l);
-    if (M->cfg.form == GNP_LAYER_PAPER)
-      k_layer_bwd_rows<GNP_LAYER_PAPER><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
-    else
-      k_layer_bwd_rows<GNP_LAYER_RESID><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+    if (bwd_quad()) {
+      if (M->cfg.form == GNP_LAYER_PAPER)
+        k_layer_bwd_rows<GNP_LAYER_PAPER><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16,
+                                                                               Gn);
+      else
+        k_layer_bwd_rows<GNP_LAYER_RESID><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16,
+                                                                               Gn);
+    } else if (M->cfg.form == GNP_LAYER_PAPER) {
+      k_layer_bwd_row1<GNP_LAYER_PAPER><<<(int)((R + 255) / 256), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+    } else {
+      k_layer_bwd_row1<GNP_LAYER_RESID><<<(int)((R + 255) / 256), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+    }
     // dX = local + A_hat^T Y (gather through the canonical CSC)
     GNP_TRY(spmm_nodes(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->y16), n, B * 4,
                        1.0f, reinterpret_cast<const float4*>(Gn), 1.0f, reinterpret_cast<float4*>(Gn), st));
