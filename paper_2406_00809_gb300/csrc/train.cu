@@ -689,15 +689,17 @@ k_layer_bwd_rows(const float* __restrict__ X, const float* __restrict__ AGG, con
   }
 }
 
-// The same with one thread per row.  Every lane of a warp then needs the same weight at
-// the same time, so each 16-byte weight load from shared memory is one broadcast (the quad
-// form above reads four different weight columns per warp load, which made the shared-memory
-// pipe its limit).  The row's AGG, X and G (and then Gp, Y, local) stay in registers;
-// the weights do not.  Same arithmetic per output as the quad form (inputs in the same
-// order), so the results are identical.
+// The same with two rows per thread (rows r and r + 256 of a 512-row block, so that each
+// load instruction of a warp is coalesced).  Every lane of a warp needs the same weight at
+// the same time, so a 16-byte weight load from shared memory is one broadcast, and each
+// feeds the multiply-adds of both rows: the weight bytes the shared-memory pipe delivers
+// per multiply-add (what bounds these kernels) are a quarter of the quad form's and half
+// of one row per thread.  The rows' AGG, X and G (then Gp, Y, local) stay in registers.
+// Same arithmetic per output as the quad form (inputs in the same order): the results
+// are identical.
 template <int FORM>
 __global__ void __launch_bounds__(256)
-k_layer_bwd_row1(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G, long long R,
+k_layer_bwd_row2(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G, long long R,
                  const float* __restrict__ lw, float* __restrict__ Gp_out, float* __restrict__ Y_out,
                  float* __restrict__ local_out) {
   __shared__ __align__(16) float sU[256], sW[256], sUt[256], sWt[256];
@@ -709,87 +711,108 @@ k_layer_bwd_row1(const float* __restrict__ X, const float* __restrict__ AGG, con
     sWt[o * 16 + c] = lw[256 + k];
   }
   __syncthreads();
-  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (r >= R) return;
+  const long long rA = blockIdx.x * 512LL + threadIdx.x;
+  if (rA >= R) return;
+  const bool two = rA + 256 < R;
+  const long long rB = two ? rA + 256 : rA;  // a lone last row is computed twice, stored once
   const float4* W4 = reinterpret_cast<const float4*>(sW);
   const float4* U4 = reinterpret_cast<const float4*>(sU);
   const float4* Wt4 = reinterpret_cast<const float4*>(sWt);
   const float4* Ut4 = reinterpret_cast<const float4*>(sUt);
-  float a[16], x[16], g[16];
-  {
+  float a[2][16], x[2][16], g[2][16];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const long long r = h ? rB : rA;
     const float4* ap = reinterpret_cast<const float4*>(AGG + r * 16);
     const float4* xp = reinterpret_cast<const float4*>(X + r * 16);
     const float4* gq = reinterpret_cast<const float4*>(G + r * 16);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float4 t = __ldg(ap + q);
-      a[4 * q] = t.x; a[4 * q + 1] = t.y; a[4 * q + 2] = t.z; a[4 * q + 3] = t.w;
+      a[h][4 * q] = t.x; a[h][4 * q + 1] = t.y; a[h][4 * q + 2] = t.z; a[h][4 * q + 3] = t.w;
       const float4 u = FORM == GNP_LAYER_PAPER ? __ldg(xp + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-      x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+      x[h][4 * q] = u.x; x[h][4 * q + 1] = u.y; x[h][4 * q + 2] = u.z; x[h][4 * q + 3] = u.w;
       const float4 v = __ldg(gq + q);
-      g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
+      g[h][4 * q] = v.x; g[h][4 * q + 1] = v.y; g[h][4 * q + 2] = v.z; g[h][4 * q + 3] = v.w;
     }
   }
-  // pre = AGG W (+ X U), accumulated per output over the inputs in order, as the quad form
-  float gp[16];
+  float gp[2][16];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    float4 pre = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 pre[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
       const float4 w = W4[c * 4 + j];
-      pre.x = fmaf(a[c], w.x, pre.x);
-      pre.y = fmaf(a[c], w.y, pre.y);
-      pre.z = fmaf(a[c], w.z, pre.z);
-      pre.w = fmaf(a[c], w.w, pre.w);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        pre[h].x = fmaf(a[h][c], w.x, pre[h].x);
+        pre[h].y = fmaf(a[h][c], w.y, pre[h].y);
+        pre[h].z = fmaf(a[h][c], w.z, pre[h].z);
+        pre[h].w = fmaf(a[h][c], w.w, pre[h].w);
+      }
     }
     if (FORM == GNP_LAYER_PAPER) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const float4 u = U4[c * 4 + j];
-        pre.x = fmaf(x[c], u.x, pre.x);
-        pre.y = fmaf(x[c], u.y, pre.y);
-        pre.z = fmaf(x[c], u.z, pre.z);
-        pre.w = fmaf(x[c], u.w, pre.w);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          pre[h].x = fmaf(x[h][c], u.x, pre[h].x);
+          pre[h].y = fmaf(x[h][c], u.y, pre[h].y);
+          pre[h].z = fmaf(x[h][c], u.z, pre[h].z);
+          pre[h].w = fmaf(x[h][c], u.w, pre[h].w);
+        }
       }
     }
-    gp[4 * j] = pre.x > 0.f ? g[4 * j] : 0.f;
-    gp[4 * j + 1] = pre.y > 0.f ? g[4 * j + 1] : 0.f;
-    gp[4 * j + 2] = pre.z > 0.f ? g[4 * j + 2] : 0.f;
-    gp[4 * j + 3] = pre.w > 0.f ? g[4 * j + 3] : 0.f;
-  }
-  {
-    float4* o = reinterpret_cast<float4*>(Gp_out + r * 16);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) o[q] = make_float4(gp[4 * q], gp[4 * q + 1], gp[4 * q + 2], gp[4 * q + 3]);
+    for (int h = 0; h < 2; ++h) {
+      gp[h][4 * j] = pre[h].x > 0.f ? g[h][4 * j] : 0.f;
+      gp[h][4 * j + 1] = pre[h].y > 0.f ? g[h][4 * j + 1] : 0.f;
+      gp[h][4 * j + 2] = pre[h].z > 0.f ? g[h][4 * j + 2] : 0.f;
+      gp[h][4 * j + 3] = pre[h].w > 0.f ? g[h][4 * j + 3] : 0.f;
+    }
   }
-  // Y = Gp W^T, local = Gp U^T (paper form) or G (residual form)
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (h == 1 && !two) break;
+    float4* o = reinterpret_cast<float4*>(Gp_out + (h ? rB : rA) * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o[q] = make_float4(gp[h][4 * q], gp[h][4 * q + 1], gp[h][4 * q + 2], gp[h][4 * q + 3]);
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 loc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 y[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    float4 loc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const float4 w = Wt4[k * 4 + j];
-      y.x = fmaf(gp[k], w.x, y.x);
-      y.y = fmaf(gp[k], w.y, y.y);
-      y.z = fmaf(gp[k], w.z, y.z);
-      y.w = fmaf(gp[k], w.w, y.w);
-      if (FORM == GNP_LAYER_PAPER) {
-        const float4 u = Ut4[k * 4 + j];
-        loc.x = fmaf(gp[k], u.x, loc.x);
-        loc.y = fmaf(gp[k], u.y, loc.y);
-        loc.z = fmaf(gp[k], u.z, loc.z);
-        loc.w = fmaf(gp[k], u.w, loc.w);
+      const float4 u = FORM == GNP_LAYER_PAPER ? Ut4[k * 4 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        y[h].x = fmaf(gp[h][k], w.x, y[h].x);
+        y[h].y = fmaf(gp[h][k], w.y, y[h].y);
+        y[h].z = fmaf(gp[h][k], w.z, y[h].z);
+        y[h].w = fmaf(gp[h][k], w.w, y[h].w);
+        if (FORM == GNP_LAYER_PAPER) {
+          loc[h].x = fmaf(gp[h][k], u.x, loc[h].x);
+          loc[h].y = fmaf(gp[h][k], u.y, loc[h].y);
+          loc[h].z = fmaf(gp[h][k], u.z, loc[h].z);
+          loc[h].w = fmaf(gp[h][k], u.w, loc[h].w);
+        }
       }
     }
-    reinterpret_cast<float4*>(Y_out + r * 16)[j] = y;
-    reinterpret_cast<float4*>(local_out + r * 16)[j] =
-        FORM == GNP_LAYER_PAPER ? loc : make_float4(g[4 * j], g[4 * j + 1], g[4 * j + 2], g[4 * j + 3]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+      const long long r = h ? rB : rA;
+      reinterpret_cast<float4*>(Y_out + r * 16)[j] = y[h];
+      reinterpret_cast<float4*>(local_out + r * 16)[j] =
+          FORM == GNP_LAYER_PAPER ? loc[h] : make_float4(g[h][4 * j], g[h][4 * j + 1], g[h][4 * j + 2], g[h][4 * j + 3]);
+    }
   }
 }
 
-// The layer backward of the training step: one thread per row (the default), or the quad
+// The layer backward of the training step: two rows per thread (the default), or the quad
 // form (GNP_TRAIN_BWD=quad in the environment, for comparison).
 static bool bwd_quad() {
   static const char* e = getenv("GNP_TRAIN_BWD");
@@ -1414,9 +1437,9 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
         k_layer_bwd_rows<GNP_LAYER_RESID><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16,
                                                                                Gn);
     } else if (M->cfg.form == GNP_LAYER_PAPER) {
-      k_layer_bwd_row1<GNP_LAYER_PAPER><<<(int)((R + 255) / 256), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+      k_layer_bwd_row2<GNP_LAYER_PAPER><<<(int)((R + 511) / 512), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
     } else {
-      k_layer_bwd_row1<GNP_LAYER_RESID><<<(int)((R + 255) / 256), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+      k_layer_bwd_row2<GNP_LAYER_RESID><<<(int)((R + 511) / 512), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
     }
     // dX = local + A_hat^T Y (gather through the canonical CSC)
     GNP_TRY(spmm_nodes(A->csc.ptr, A->csc.idx, M->valhat_t, reinterpret_cast<const float4*>(T->y16), n, B * 4,
