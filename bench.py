@@ -528,11 +528,18 @@ def run_ours(args, wl):
         c4 = (c4_block(gnp, stream, peak, peak_kind, 50,
                        0.0 if (args.no_cpu_baseline or ws > 1) else args.ref_seconds)
               if (rank == 0 and not args.no_c4) else None)
-    # kernel launches inside the timed region: per cycle m steps of (encode, which from
-    # step 1 on also forms the basis vector and finishes the previous step; L Res-GCONV
-    # with the decoder in the last; SpMV + CGS2 pass 1; pass 2) + the last step's finish
-    # + x update + residual; per solve + norm and initial residual
-    per_cycle = m * (L + 3) + 3
+    # kernel launches inside the timed region, per restart cycle (the captured graph launches
+    # all m steps; a finished cycle's kernels return at once):
+    # * overlapped CGS2 (the default): step 0 = encode, L Res-GCONV (the decoder in the last),
+    #   SpMV + first pass; steps 1.. add the two reorthogonalisation kernels; then the last
+    #   column's finish, x update, residual;
+    # * GNP_ORTHO=cgs2: m steps of (encode, L Res-GCONV, SpMV + pass 1, pass 2), the last
+    #   step's finish, x update, residual;
+    # per solve also the norm of b and the initial residual
+    if os.environ.get("GNP_ORTHO") == "cgs2":
+        per_cycle = m * (L + 3) + 3
+    else:
+        per_cycle = (L + 2) + (m - 1) * (L + 4) + 3
     launches = sum(i.cycles * per_cycle + 2 for i in infos)
     cfg_out = base_config(wl, A)
     cfg_out.update({"train_steps": train_steps, "l2": "flushed (256 MB write) before every timed solve",
