@@ -345,12 +345,64 @@ k_mgconv(const int* __restrict__ rp, const int* __restrict__ col, const float* _
 // the kernel is also CGS2 pass 1: h1 = V_j^T w and ||w||^2 per system, each block adding
 // its own rows' products (KC per register chunk, a fixed-order block reduction) and the
 // last block the blocks' partials in order.
-template <int K, class XT, bool DOTS>
+// RDOT (the overlapped schedule; j = s, V_s final): the last block keeps h_s = V_s^T w in h1
+// and per active system rho_s by Pythagoras, normalised as in the one-system step
+// (RHO_FLOOR), 1/rho, ||w||; a system whose step broke down (w = 0 or not finite) has
+// its column s finished at once with the first-pass values, which ends its cycle.  It
+// then advances the step (ctl[0] = s + 1) and the any-active flag.
+template <int K>
+__device__ __forceinline__ void mrdot_tail(int s, const double* shtot, DevState* st, int* ctl, double* h,
+                                           double* H, double* R, double* cs, double* sn, double* g, double* hist,
+                                           unsigned long long* thist, MStrides ms) {
+  __shared__ double scol[K][GNP_MAX_RESTART_MULTI + 2];
+  __shared__ int anyact;
+  for (int k = threadIdx.x; k < (s + 1) * K; k += blockDim.x) h[k] = shtot[k];
+  if (threadIdx.x == 0) anyact = 0;
+  __syncthreads();
+  if (threadIdx.x < K) {
+    const int r = threadIdx.x;
+    DevState* sr = st + r;
+    if (sr->active) {
+      double bb = 0.0;
+      for (int c = 0; c <= s; ++c) bb = fma(shtot[c * K + r], shtot[c * K + r], bb);
+      const double omega = shtot[(s + 1) * K + r];
+      const double rho = sqrt(fmax(omega - bb, 0.0));
+      const double wn = sqrt(omega);
+      const double rho_n = fmax(rho, RHO_FLOOR * wn);
+      const bool brk = !(rho_n > 0.0) || !isfinite(rho_n) || !isfinite(bb);
+      sr->rho = rho_n;
+      sr->rho_est = rho;
+      sr->rho_inv = brk ? 0.0 : 1.0 / rho_n;
+      sr->wnorm0 = wn;
+      sr->jd = s;
+      if (brk) {
+        for (int c = 0; c <= s; ++c) scol[r][c] = shtot[c * K + r];
+        double* csr = cs + (size_t)r * ms.ms;
+        double* snr = sn + (size_t)r * ms.ms;
+        arnoldi_step_finish(sr, s, scol[r], rho, csr, snr, H + (size_t)r * ms.hs, R + (size_t)r * ms.hs, csr, snr,
+                            g + (size_t)r * ms.gs, hist + (size_t)r * ms.hist, thist + (size_t)r * ms.hist, true,
+                            wn);
+      }
+      if (sr->active) atomicOr(&anyact, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl[0] = s + 1;
+    ctl[1] = anyact;
+  }
+}
+
+template <int K, class XT, bool DOTS, bool RDOT = false>
 __global__ void __launch_bounds__(TILE)
 k_mspmv(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-        const XT* __restrict__ Xbase, double* __restrict__ w, int n, const int* __restrict__ ctl,
+        const XT* __restrict__ Xbase, double* __restrict__ w, int n, int* __restrict__ ctl,
         const double* __restrict__ V, DevState* st, double* __restrict__ h1, double* __restrict__ partials,
-        unsigned* counter) {
+        unsigned* counter, double* __restrict__ H = nullptr, double* __restrict__ R = nullptr,
+        double* __restrict__ cs = nullptr, double* __restrict__ sn = nullptr, double* __restrict__ g = nullptr,
+        double* __restrict__ hist = nullptr, unsigned long long* __restrict__ thist = nullptr,
+        MStrides ms = MStrides{0, 0, 0, 0}) {
+  static_assert(!RDOT || DOTS, "the first-pass tail needs the dots");
   using TR = TrSpmvM<K, XT>;
   if (!ctl[1]) return;
   __shared__ TileSmem<TR, MROWS> sm;
@@ -404,9 +456,13 @@ k_mspmv(const int* __restrict__ rp, const int* __restrict__ col, const double* _
     }
     if (!last_block_arrive(counter)) return;
     reduce_partials(partials, gridDim.x, Kc * K, shtot);
+    if (threadIdx.x == 0) *counter = 0;
+    if constexpr (RDOT) {
+      mrdot_tail<K>(j, shtot, st, ctl, h1, H, R, cs, sn, g, hist, thist, ms);
+      return;
+    }
     for (int k = threadIdx.x; k < (j + 1) * K; k += blockDim.x) h1[k] = shtot[k];
     if (threadIdx.x < K && st[threadIdx.x].active) st[threadIdx.x].wnorm0 = sqrt(shtot[(j + 1) * K + threadIdx.x]);
-    if (threadIdx.x == 0) *counter = 0;
   }
 }
 
@@ -538,54 +594,6 @@ __device__ __forceinline__ void mload_k(const XT* __restrict__ x, int c, double 
       const float4 t = __ldg(reinterpret_cast<const float4*>(p) + u);
       h[4 * u] = t.x; h[4 * u + 1] = t.y; h[4 * u + 2] = t.z; h[4 * u + 3] = t.w;
     }
-  }
-}
-
-// RDOT (the overlapped schedule; j = s, V_s final): the last block keeps h_s = V_s^T w in h1
-// and per active system rho_s by Pythagoras, normalised as in the one-system step
-// (RHO_FLOOR), 1/rho, ||w||; a system whose step broke down (w = 0 or not finite) has
-// its column s finished at once with the first-pass values, which ends its cycle.  It
-// then advances the step (ctl[0] = s + 1) and the any-active flag.
-template <int K>
-__device__ __forceinline__ void mrdot_tail(int s, const double* shtot, DevState* st, int* ctl, double* h,
-                                           double* H, double* R, double* cs, double* sn, double* g, double* hist,
-                                           unsigned long long* thist, MStrides ms) {
-  __shared__ double scol[K][GNP_MAX_RESTART_MULTI + 2];
-  __shared__ int anyact;
-  for (int k = threadIdx.x; k < (s + 1) * K; k += blockDim.x) h[k] = shtot[k];
-  if (threadIdx.x == 0) anyact = 0;
-  __syncthreads();
-  if (threadIdx.x < K) {
-    const int r = threadIdx.x;
-    DevState* sr = st + r;
-    if (sr->active) {
-      double bb = 0.0;
-      for (int c = 0; c <= s; ++c) bb = fma(shtot[c * K + r], shtot[c * K + r], bb);
-      const double omega = shtot[(s + 1) * K + r];
-      const double rho = sqrt(fmax(omega - bb, 0.0));
-      const double wn = sqrt(omega);
-      const double rho_n = fmax(rho, RHO_FLOOR * wn);
-      const bool brk = !(rho_n > 0.0) || !isfinite(rho_n) || !isfinite(bb);
-      sr->rho = rho_n;
-      sr->rho_est = rho;
-      sr->rho_inv = brk ? 0.0 : 1.0 / rho_n;
-      sr->wnorm0 = wn;
-      sr->jd = s;
-      if (brk) {
-        for (int c = 0; c <= s; ++c) scol[r][c] = shtot[c * K + r];
-        double* csr = cs + (size_t)r * ms.ms;
-        double* snr = sn + (size_t)r * ms.ms;
-        arnoldi_step_finish(sr, s, scol[r], rho, csr, snr, H + (size_t)r * ms.hs, R + (size_t)r * ms.hs, csr, snr,
-                            g + (size_t)r * ms.gs, hist + (size_t)r * ms.hist, thist + (size_t)r * ms.hist, true,
-                            wn);
-      }
-      if (sr->active) atomicOr(&anyact, 1);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ctl[0] = s + 1;
-    ctl[1] = anyact;
   }
 }
 
@@ -1056,21 +1064,22 @@ static int mgconv_attrs() {
   return GNP_OK;
 }
 
+// The L Res-GCONV layers of the K systems from S->Hg[0] (the last one fused with the
+// decoder, z into column j of Z): the short-row kernels over the n K (node, system) pairs
+// when every row has at most 16 nonzeros, else the K-node tile gather.
 template <int K, int FORM>
-static void launch_mgnp(gnp_model* M, MultiSolver* S, cudaStream_t st) {
+static void mgnp_layers(gnp_model* M, MultiSolver* S, cudaStream_t st) {
   const gnp_mat* A = M->A;
   const int n = A->n, L = M->cfg.L;
   const double sqrt_n = std::sqrt((double)n);
-  EncW ew;
-  DecW dw;
-  fill_enc_dec(M->w_host, L, ew, dw);
-  const int ne = (int)std::min<long long>(((long long)n * K + RED_THREADS - 1) / RED_THREADS, 8LL * NUM_SMS_GB300);
-  k_mencode<K><<<ne, RED_THREADS, 0, st>>>(S->V, n, S->st, S->ctl, sqrt_n, S->Hg[0], ew);
-  if (multi_row_ok(M)) {  // rows of at most 16 nonzeros: the short-row kernels over n K pairs
+  if (multi_row_ok(M)) {
     const ColPtr zp{S->Z, sizeof(float) * (size_t)n * K, S->ctl, 0};
     multi_row_layers(M, K, S->Hg[0], S->Hg[1], zp, S->one, S->ctl, st);  // launch errors: check_launch
     return;
   }
+  EncW ew;
+  DecW dw;
+  fill_enc_dec(M->w_host, L, ew, dw);
   const int smem = (int)sizeof(MGconvSmem<K>);
   const int nt = (n + MGconvSmem<K>::ROWS - 1) / MGconvSmem<K>::ROWS;
   float* H0 = S->Hg[0];
@@ -1088,6 +1097,19 @@ static void launch_mgnp(gnp_model* M, MultiSolver* S, cudaStream_t st) {
   }
 }
 
+// z_r = M(v_r) for every active system: the encoder (v_r normalised by vscale_r), then the
+// layers.
+template <int K, int FORM>
+static void launch_mgnp(gnp_model* M, MultiSolver* S, cudaStream_t st) {
+  const int n = M->A->n;
+  EncW ew;
+  DecW dw;
+  fill_enc_dec(M->w_host, M->cfg.L, ew, dw);
+  const int ne = (int)std::min<long long>(((long long)n * K + RED_THREADS - 1) / RED_THREADS, 8LL * NUM_SMS_GB300);
+  k_mencode<K><<<ne, RED_THREADS, 0, st>>>(S->V, n, S->st, S->ctl, std::sqrt((double)n), S->Hg[0], ew);
+  mgnp_layers<K, FORM>(M, S, st);
+}
+
 // The reorthogonalisation stream of the overlapped schedule (highest priority) and its
 // fork/join events, made on first use.
 static int multi_side(MultiSolver* S) {
@@ -1100,10 +1122,8 @@ static int multi_side(MultiSolver* S) {
   return GNP_OK;
 }
 
-// The overlapped schedule applies to the GNP on the short-row kernels.
-static bool multi_overlapped(const gnp_mat* A, const gnp_model* M) {
-  return M && A->max_deg <= ROW_DMAX_M && multi_row_ok(M) && ortho_overlapped();
-}
+// The overlapped schedule applies to the GNP (M = I keeps the two-reduction passes).
+static bool multi_overlapped(const gnp_model* M) { return M && ortho_overlapped(); }
 
 // One overlapped restart cycle (the one-system schedule of krylov.cu for K systems): per
 // step the encoder forms v'_j, the second pass of v'_j runs on S->side beside the layers,
@@ -1116,12 +1136,12 @@ static int launch_mcycle_ovl(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cu
   const int ncg = dot_blocks(n);
   const MStrides ms = mstrides(S->m_cap, S->maxit_cap);
   const double sqrt_n = std::sqrt((double)n);
+  const bool short_rows = A->max_deg <= ROW_DMAX_M;
   GNP_TRY(multi_side(S));
   EncW ew;
   DecW dw;
   fill_enc_dec(M->w_host, M->cfg.L, ew, dw);
   const int ne = (int)std::min<long long>(((long long)n * K + RED_THREADS - 1) / RED_THREADS, 8LL * NUM_SMS_GB300);
-  const ColPtr zp{S->Z, sizeof(float) * (size_t)n * K, S->ctl, 0};
   for (int j = 0; j < m; ++j) {
     if (j == 0) {
       k_mencode<K><<<ne, RED_THREADS, 0, st>>>(S->V, n, S->st, S->ctl, sqrt_n, S->Hg[0], ew);
@@ -1135,11 +1155,17 @@ static int launch_mcycle_ovl(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cu
       k_mreorth_update<K><<<nb, RED_THREADS, 0, S->side>>>(S->V, n, S->st, S->ctl, S->h1);
       GNP_TRY_CUDA(cudaEventRecord(S->join, S->side));
     }
-    GNP_TRY(multi_row_layers(M, K, S->Hg[0], S->Hg[1], zp, S->one, S->ctl, st));
+    if (M->cfg.form == GNP_LAYER_PAPER) mgnp_layers<K, GNP_LAYER_PAPER>(M, S, st);
+    else mgnp_layers<K, GNP_LAYER_RESID>(M, S, st);
     if (j > 0) GNP_TRY_CUDA(cudaStreamWaitEvent(st, S->join, 0));
-    k_mspmv_row<K, float, true><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl, S->V,
-                                                             S->st, S->h2, S->red.partials, S->red.counter, S->H,
-                                                             S->R, S->cs, S->sn, S->g, S->hist, S->thist, ms);
+    if (short_rows)
+      k_mspmv_row<K, float, true><<<ncg, RED_THREADS, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl, S->V,
+                                                               S->st, S->h2, S->red.partials, S->red.counter, S->H,
+                                                               S->R, S->cs, S->sn, S->g, S->hist, S->thist, ms);
+    else
+      k_mspmv<K, float, true, true><<<ntr, TILE, 0, st>>>(A->rp, A->col, A->val, S->Z, S->w, n, S->ctl, S->V, S->st,
+                                                          S->h2, S->red.partials, S->red.counter, S->H, S->R, S->cs,
+                                                          S->sn, S->g, S->hist, S->thist, ms);
   }
   k_mdfinish<K><<<1, 32, 0, st>>>(S->st, S->ctl, S->h2, S->H, S->R, S->cs, S->sn, S->g, S->hist, S->thist, ms);
   k_mxupdate<K, float><<<nb, RED_THREADS, 0, st>>>(S->Z, S->x, n, S->st, S->R, S->g, ms, m);
@@ -1151,7 +1177,7 @@ static int launch_mcycle_ovl(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cu
 // One restart cycle for all systems: m Arnoldi steps, x update, residual.
 template <int K>
 static int launch_mcycle(gnp_mat* A, MultiSolver* S, gnp_model* M, int m, cudaStream_t st) {
-  if (multi_overlapped(A, M)) return launch_mcycle_ovl<K>(A, S, M, m, st);
+  if (multi_overlapped(M)) return launch_mcycle_ovl<K>(A, S, M, m, st);
   const int n = A->n;
   const int ntr = (n + MROWS - 1) / MROWS;
   const int nb = red_blocks(n);

@@ -109,14 +109,17 @@ def test_exact_breakdown(gnp, rtol, monkeypatch):
     assert np.all(np.isfinite(info.history))
 
 
+@pytest.mark.parametrize("mat", ["poisson16", "powerlaw3000"])
 @pytest.mark.parametrize("m", [1, 2, 5])
-def test_multi_short_restarts_match_oracle(gnp, m, monkeypatch):
-    """The k-system solver (three systems, untrained GNP, 16 x 16 Poisson) on the
-    overlapped schedule with restart lengths 1, 2 and 5: each system's first 8 residuals
-    agree with the oracle's FGMRES on that system alone to 1e-5, and its status and
-    iteration count equal the two-reduction k-system solve's."""
+def test_multi_short_restarts_match_oracle(gnp, m, mat, monkeypatch):
+    """The k-system solver (three systems, untrained GNP) on the overlapped schedule with
+    restart lengths 1, 2 and 5, on the 16 x 16 Poisson matrix (short-row kernels) and a
+    3,000-row power-law matrix with rows of up to 999 nonzeros (tile kernels; shift 1.25 x
+    its spectral radius): each system's first 8 residuals agree with the oracle's FGMRES
+    on that system alone to 1e-5, and its status and iteration count equal the
+    two-reduction k-system solve's."""
     import torch
-    A = I.poisson2d(16)
+    A = I.poisson2d(16) if mat == "poisson16" else I.powerlaw(3000, seed=7, shift_fraction=1.25)
     L = 2
     blob = I.init_weights(L, seed=3)
     B = np.stack([I.spmv(A, I.gaussian(A.n, seed=s)) for s in (1, 2, 3)], axis=1)
