@@ -812,12 +812,187 @@ k_layer_bwd_row2(const float* __restrict__ X, const float* __restrict__ AGG, con
   }
 }
 
-// The layer backward of the training step: two rows per thread (the default), or the quad
-// form (GNP_TRAIN_BWD=quad in the environment, for comparison).
-static bool bwd_quad() {
-  static const char* e = getenv("GNP_TRAIN_BWD");
-  static const bool q = e && strcmp(e, "quad") == 0;
-  return q;
+// ---- tensor-core form of the layer backward
+//
+// Per warp, tiles of 32 rows: pre = [AGG | X] [W; U] (32 x 32 by 32 x 16) and then
+// [Y | local] = Gp [W^T | U^T] (32 x 16 by 16 x 32) on mma.sync m16n8k8 with TF32 operands
+// in three products (a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, hi = the operand rounded to
+// TF32, lo = the TF32 rounding of its remainder), which keeps float32 accuracy.  The weight
+// fragments stay in registers for the whole kernel; the row tiles pass through shared
+// memory (padded rows, so that the fragment loads are free of bank conflicts) from
+// coalesced 16-byte loads.  The residual form has pre = AGG W, Y = Gp W^T, local = G.
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += a b in three TF32 products (the small ones first)
+__device__ __forceinline__ void mma3_tf32(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                          const uint32_t (&bh)[2], const uint32_t (&bl)[2]) {
+  mma_tf32(d, al, bh[0], bh[1]);
+  mma_tf32(d, ah, bl[0], bl[1]);
+  mma_tf32(d, ah, bh[0], bh[1]);
+}
+
+// The A fragment (rows 16 mt + {g, g + 8}, columns 8 ks + {t, t + 4}) of a shared tile with
+// row stride ST, split into hi and lo.
+template <int ST>
+__device__ __forceinline__ void frag_a(const float* tile, int mt, int ks, int g, int t, uint32_t (&hi)[4],
+                                       uint32_t (&lo)[4]) {
+  const float* p = tile + (16 * mt + g) * ST + 8 * ks + t;
+  tf32_split(p[0], hi[0], lo[0]);
+  tf32_split(p[8 * ST], hi[1], lo[1]);
+  tf32_split(p[4], hi[2], lo[2]);
+  tf32_split(p[8 * ST + 4], hi[3], lo[3]);
+}
+
+template <int FORM>
+__global__ void __launch_bounds__(256)
+k_layer_bwd_tc(const float* __restrict__ X, const float* __restrict__ AGG, const float* __restrict__ G, long long R,
+               const float* __restrict__ lw, float* __restrict__ Gp_out, float* __restrict__ Y_out,
+               float* __restrict__ local_out) {
+  constexpr bool PAPER = FORM == GNP_LAYER_PAPER;
+  constexpr int KA = PAPER ? 32 : 16;   // inputs of pre: [AGG | X] or AGG
+  constexpr int NKS1 = KA / 8;
+  constexpr int NNT2 = PAPER ? 4 : 2;   // output tiles of phase 2: [Y | local] or Y
+  constexpr int AST = KA + 4;           // padded row strides (floats)
+  constexpr int GST = 20;
+  static_assert(GST <= AST, "the Gp tile reuses the [AGG | X] tile's space");
+  __shared__ __align__(16) float sA[8][32 * AST];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  // weight fragments: phase 1 B1[k][n] = [W; U][k][n] (k input, n output); phase 2
+  // B2[k][n] = [W^T | U^T][k][n] = W[n][k] (n < 16) or U[n - 16][k]
+  uint32_t b1h[NKS1][2][2], b1l[NKS1][2][2];
+#pragma unroll
+  for (int ks = 0; ks < NKS1; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int k = 8 * ks + t + 4 * e, nn = 8 * nt + g;
+        const float v = k < 16 ? lw[256 + k * 16 + nn] : lw[(k - 16) * 16 + nn];
+        tf32_split(v, b1h[ks][nt][e], b1l[ks][nt][e]);
+      }
+  uint32_t b2h[2][NNT2][2], b2l[2][NNT2][2];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < NNT2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int k = 8 * ks + t + 4 * e, nn = 8 * nt + g;
+        const float v = nn < 16 ? lw[256 + nn * 16 + k] : lw[(nn - 16) * 16 + k];
+        tf32_split(v, b2h[ks][nt][e], b2l[ks][nt][e]);
+      }
+  float* At = sA[w];
+  float* Gt = sA[w];  // after phase 1 the [AGG | X] tile is dead: the Gp tile takes its place
+  const long long ntile = (R + 31) / 32;
+  const float4* AG4 = reinterpret_cast<const float4*>(AGG);
+  const float4* X4 = reinterpret_cast<const float4*>(X);
+  for (long long tile = blockIdx.x * 8LL + w; tile < ntile; tile += gridDim.x * 8LL) {
+    const long long r0 = tile * 32;
+    const int rows = (int)min(32LL, R - r0);
+    // stage [AGG | X] (coalesced 16-byte loads; rows past the end as zeros)
+#pragma unroll
+    for (int q = lane; q < 32 * KA / 4; q += 32) {
+      const int r = q / (KA / 4), c4 = q % (KA / 4);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) v = c4 < 4 ? __ldg(AG4 + (r0 + r) * 4 + c4) : __ldg(X4 + (r0 + r) * 4 + (c4 - 4));
+      *reinterpret_cast<float4*>(At + r * AST + 4 * c4) = v;
+    }
+    __syncwarp();
+    float acc1[2][2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc1[mt][nt][i] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < NKS1; ++ks)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        uint32_t ah[4], al[4];
+        frag_a<AST>(At, mt, ks, g, t, ah, al);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) mma3_tf32(acc1[mt][nt], ah, al, b1h[ks][nt], b1l[ks][nt]);
+      }
+    __syncwarp();  // every lane has read its phase-1 fragments
+    // Gp = G where pre > 0 (the C layout: rows 16 mt + g (+8), columns 8 nt + 2t, +1)
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int r = 16 * mt + g + 8 * hf, c = 8 * nt + 2 * t;
+          float2 gv = make_float2(0.f, 0.f);
+          if (r < rows) gv = __ldg(reinterpret_cast<const float2*>(G + (r0 + r) * 16 + c));
+          const float2 gp = make_float2(acc1[mt][nt][2 * hf] > 0.f ? gv.x : 0.f,
+                                        acc1[mt][nt][2 * hf + 1] > 0.f ? gv.y : 0.f);
+          if (r < rows) {
+            *reinterpret_cast<float2*>(Gp_out + (r0 + r) * 16 + c) = gp;
+            if (!PAPER) *reinterpret_cast<float2*>(local_out + (r0 + r) * 16 + c) = gv;
+          }
+          *reinterpret_cast<float2*>(Gt + r * GST + c) = gp;
+        }
+    __syncwarp();
+    float acc2[2][NNT2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NNT2; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc2[mt][nt][i] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        uint32_t ah[4], al[4];
+        frag_a<GST>(Gt, mt, ks, g, t, ah, al);
+#pragma unroll
+        for (int nt = 0; nt < NNT2; ++nt) mma3_tf32(acc2[mt][nt], ah, al, b2h[ks][nt], b2l[ks][nt]);
+      }
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NNT2; ++nt)
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int r = 16 * mt + g + 8 * hf, c = 8 * (nt & 1) + 2 * t;
+          if (r < rows) {
+            float* dst = nt < 2 ? Y_out : local_out;
+            *reinterpret_cast<float2*>(dst + (r0 + r) * 16 + c) =
+                make_float2(acc2[mt][nt][2 * hf], acc2[mt][nt][2 * hf + 1]);
+          }
+        }
+    __syncwarp();  // the tiles are free for the next rows
+  }
+}
+
+// The layer backward of the training step: two rows per thread in float32 (the default),
+// or with GNP_TRAIN_BWD=tc / quad in the environment the tensor-core form or four threads
+// per row, for comparison (64^3 step: 22.8 ms, tc 23.9, quad 31.5).  Read at every launch.
+static int bwd_form() {
+  const char* e = getenv("GNP_TRAIN_BWD");
+  if (e && strcmp(e, "quad") == 0) return 2;
+  if (e && strcmp(e, "tc") == 0) return 0;
+  return 1;
 }
 
 // Encoder backward (thread per row): r1 = ReLU(a1) and da1 = (dH0 W2^T) * 1[a1 > 0].
@@ -1429,7 +1604,15 @@ static int backward_batch(gnp_model* M, const float* dz, cudaStream_t st) {
     const float* X = T->Hs + (size_t)l * R * 16;
     const float* AG = T->AGG + (size_t)l * R * 16;
     const float* lw = M->w_dev + layer_off(l);
-    if (bwd_quad()) {
+    const int bf = bwd_form();
+    if (bf == 0) {
+      const int tiles = (int)std::min<long long>((R + 31) / 32, 1LL << 30);
+      const int grid = std::min((tiles + 7) / 8, 4 * NUM_SMS_GB300 * 4);
+      if (M->cfg.form == GNP_LAYER_PAPER)
+        k_layer_bwd_tc<GNP_LAYER_PAPER><<<grid, 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+      else
+        k_layer_bwd_tc<GNP_LAYER_RESID><<<grid, 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16, Gn);
+    } else if (bf == 2) {
       if (M->cfg.form == GNP_LAYER_PAPER)
         k_layer_bwd_rows<GNP_LAYER_PAPER><<<(int)((R + 63) / 64), 256, 0, st>>>(X, AG, G, R, lw, T->gp16, T->y16,
                                                                                Gn);

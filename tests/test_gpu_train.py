@@ -103,9 +103,14 @@ def _batch(n, B, seed):
     return np.random.default_rng(seed).standard_normal((n, B))
 
 
+@pytest.mark.parametrize("bwd", ["tc", "row2", "quad"])
 @pytest.mark.parametrize("form", [0, 1])
-def test_forward_backward_batch_match_oracle(gnp, form):
+def test_forward_backward_batch_match_oracle(gnp, form, bwd, monkeypatch):
+    """The batched forward and the hand-written backward against the float64 oracle; the
+    layer backward in each of its forms (tensor cores with three TF32 products, float32
+    with two rows per thread, float32 with four threads per row)."""
     import torch
+    monkeypatch.setenv("GNP_TRAIN_BWD", bwd)
     A = I.convdiff2d(24, 100.0)
     n, B, L = A.n, 16, 3
     Mt, M, blob = _model(gnp, A, L, B=B, form=form)
