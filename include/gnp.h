@@ -341,21 +341,34 @@ double gnp_time_auc(const double* res_history, const double* time_history, int l
  * serves any number of right-hand sides; here also many matrices at once).  A server
  * thread admits queued requests in FIFO order while fewer than max_active run and their
  * device-memory footprint (Krylov basis n*(restart+1) float64, directions n*restart
- * float32, GNP hidden blocks 2*n*16 float32, reduction scratch) fits in max_bytes.  Every
- * running request has its own stream and its restart cycle captured as a CUDA graph;
- * whenever one of its cycles ends, the server applies its stopping rules and launches its
- * next cycle or retires it at once, without waiting for the other requests.  Results
- * are the same as a lone fgmres_solve of the request. */
+ * float32, GNP hidden blocks 2*n*16 float32, reduction scratch) fits in max_bytes.
+ *
+ * Per-request mode (grouped = 0): every running request has its own stream and its
+ * restart cycle captured as a CUDA graph; whenever one of its cycles ends, the server
+ * applies its stopping rules and launches its next cycle or retires it at once, without
+ * waiting for the other requests.  Results are the same as a lone fgmres_solve of the
+ * request.
+ *
+ * Grouped mode (grouped = 1): requests whose GNP runs on the short-row layer kernels (every
+ * row of A at most 16 nonzeros, L >= 1), at most 16 at once, advance together one FGMRES
+ * step per round on one stream: each kernel of the step (encoder, Res-GCONV layers, SpMV
+ * with CGS2 pass 1, pass 2) is launched once for all of them over a work table of the
+ * requests' own grids, the round captured as one CUDA graph per set of running requests;
+ * the requests whose restart cycle ends in a round get their cycle end in the same round.
+ * Requests are admitted and retired between rounds.  Each grouped request computes
+ * exactly what a lone fgmres_solve computes with the two-pass CGS2 schedule
+ * (GNP_ORTHO=cgs2 in the environment); the other requests run as in per-request mode. */
 typedef struct gnp_server_config {
   size_t max_bytes; /* device-memory budget for the running requests' workspaces */
   int max_active;   /* requests running at once (slots) */
   int restart;      /* FGMRES restart length of every request */
+  int grouped;      /* 1: grouped steps for the requests that allow them; 0: per request */
 } gnp_server_config;
 
 typedef struct gnp_server_stats_t {
   int queued, active;
   size_t used_bytes;
-  long long rounds; /* restart cycles launched */
+  long long rounds; /* restart cycles begun */
   long long completed, max_active_seen;
 } gnp_server_stats_t;
 

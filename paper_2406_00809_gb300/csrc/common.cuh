@@ -170,20 +170,51 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// The block's place in the grid a kernel body works on: the hardware grid for a stand-alone
+// launch, or one request's share of a grouped launch (several requests' grids laid end to
+// end in one launch, see GTable).  A body reads bid / nblk where a kernel reads blockIdx.x
+// / gridDim.x, so the same arithmetic runs in both.
+struct VGrid {
+  int bid;
+  int nblk;
+};
+__device__ __forceinline__ VGrid hw_grid() { return VGrid{(int)blockIdx.x, (int)gridDim.x}; }
+
+// Work table of a grouped launch (passed by value): entry i is request slot slot[i], whose
+// blocks are start[i] .. start[i+1]-1 of the launch.  Block b finds its entry by a scan of
+// at most GT_MAX entries; gt_entry returns the entry and sets the block's place in that
+// request's grid.
+constexpr int GT_MAX = 16;
+struct GTable {
+  int count;
+  int slot[GT_MAX];
+  int start[GT_MAX + 1];
+};
+__device__ __forceinline__ int gt_entry(const GTable& t, VGrid& g) {
+  const int b = (int)blockIdx.x;
+  int i = 0;
+  while (i + 1 < t.count && b >= t.start[i + 1]) ++i;
+  g.bid = b - t.start[i];
+  g.nblk = t.start[i + 1] - t.start[i];
+  return i;
+}
+
 // Last-block arrival: every block has written its partials; the block that arrives
-// last sees true (after a fence) and may read all partials.  It must reset *counter.
-__device__ __forceinline__ bool last_block_arrive(unsigned* counter) {
+// last (of nblk) sees true (after a fence) and may read all partials.  It must reset
+// *counter.
+__device__ __forceinline__ bool last_block_arrive(unsigned* counter, int nblk) {
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(counter, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nblk - 1u);
   }
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
 }
+__device__ __forceinline__ bool last_block_arrive(unsigned* counter) { return last_block_arrive(counter, gridDim.x); }
 
 // In the last block: out[k] = sum_b partials[b*K + k] for k < K, in a fixed order
 // (lane-strided over blocks, then a fixed shuffle tree).  out is shared memory.

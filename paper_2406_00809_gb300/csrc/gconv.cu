@@ -93,13 +93,13 @@ __device__ __forceinline__ void tile_copy(uint32_t* stile, HT* g, int r0, int ro
 // tau = 1 for the decoder's back-scaling).  noscale (the ablation without s): u = v, and
 // tau = sqrt(n) is stored so that the decoder's factor tau/sqrt(n) is 1.
 template <class HT>
-__global__ void __launch_bounds__(TILE)
-k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau, const int* __restrict__ ctl,
-         int n, double sqrt_n, int noscale, HT* __restrict__ H, const __grid_constant__ EncW ew) {
+__device__ __forceinline__ void encode_body(VGrid gr, ColPtr vp, const double* __restrict__ vscale,
+                                            double* __restrict__ tau, const int* __restrict__ ctl, int n,
+                                            double sqrt_n, int noscale, HT* __restrict__ H, const EncW& ew) {
   if (ctl && !ctl[1]) return;
   __shared__ __align__(16) uint32_t stile[TILE * HTraits<HT>::SROW];
   double* v = static_cast<double*>(colptr(vp));
-  const int r0 = blockIdx.x * TILE;
+  const int r0 = gr.bid * TILE;
   const int rows = min(TILE, n - r0);
   const int t = threadIdx.x;
   // the block's scalars once (a float64 division is slow on GB300): u = f * v, and the
@@ -109,10 +109,10 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
     s_inv = vscale ? 1.0 / *vscale : 1.0;  // v_j = w / h whether or not s is applied
     if (noscale) {
       s_f = 1.0;
-      if (blockIdx.x == 0) *tau = sqrt_n;
+      if (gr.bid == 0) *tau = sqrt_n;
     } else if (vscale) {
       s_f = sqrt_n;
-      if (blockIdx.x == 0) *tau = 1.0;
+      if (gr.bid == 0) *tau = 1.0;
     } else {
       const double tv = *tau;
       s_f = tv > 0.0 ? sqrt_n / tv : 0.0;
@@ -143,6 +143,13 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
   tile_copy<HT, true>(stile, H, r0, rows);
 }
 
+template <class HT>
+__global__ void __launch_bounds__(TILE)
+k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau, const int* __restrict__ ctl,
+         int n, double sqrt_n, int noscale, HT* __restrict__ H, const __grid_constant__ EncW ew) {
+  encode_body<HT>(hw_grid(), vp, vscale, tau, ctl, n, sqrt_n, noscale, H, ew);
+}
+
 // The encoder inside FGMRES from step 1 on (vn: the pending step j = st->jv): the last
 // block finishes step j (vnext_finish: Givens update, continue decision) while the others
 // form v_{j+1} = (w1 - V_j h2) / h_{j+1,j} for their rows in float64, store it as
@@ -150,10 +157,9 @@ k_encode(ColPtr vp, const double* __restrict__ vscale, double* __restrict__ tau,
 // noscale: u = v, tau = sqrt(n)).  The rows are formed even if the finish ends the cycle;
 // every later kernel of the step then sees active = 0 and returns.
 template <class HT>
-__global__ void __launch_bounds__(TILE)
-k_encode_vn(const VNext vn, int n, double sqrt_n, int noscale, double* __restrict__ tau, HT* __restrict__ H,
-            const __grid_constant__ EncW ew) {
-  if (blockIdx.x == gridDim.x - 1) {
+__device__ __forceinline__ void encode_vn_body(VGrid gr, const VNext& vn, int n, double sqrt_n, int noscale,
+                                               double* __restrict__ tau, HT* __restrict__ H, const EncW& ew) {
+  if (gr.bid == gr.nblk - 1) {
     vnext_finish(vn);
     return;
   }
@@ -168,12 +174,12 @@ k_encode_vn(const VNext vn, int n, double sqrt_n, int noscale, double* __restric
   vnext_hnorm(vn.h2, j, st->w1sq, &shn);
   if (t == 0) {
     sinv = 1.0 / shn;  // once per block (thread 0 wrote shn): float64 division is slow
-    if (blockIdx.x == 0) *tau = noscale ? sqrt_n : 1.0;
+    if (gr.bid == 0) *tau = noscale ? sqrt_n : 1.0;
   }
   __syncthreads();
   const double inv = sinv;
   const double f = noscale ? 1.0 : sqrt_n;
-  const int r0 = blockIdx.x * TILE;
+  const int r0 = gr.bid * TILE;
   const int rows = min(TILE, n - r0);
   if (t < rows) {
     const size_t ld = (size_t)n;
@@ -197,6 +203,13 @@ k_encode_vn(const VNext vn, int n, double sqrt_n, int noscale, double* __restric
   }
   __syncthreads();
   tile_copy<HT, true>(stile, H, r0, rows);
+}
+
+template <class HT>
+__global__ void __launch_bounds__(TILE)
+k_encode_vn(const VNext vn, int n, double sqrt_n, int noscale, double* __restrict__ tau, HT* __restrict__ H,
+            const __grid_constant__ EncW ew) {
+  encode_vn_body<HT>(hw_grid(), vn, n, sqrt_n, noscale, tau, H, ew);
 }
 
 // The encoder of the overlapped-CGS2 step s + 1 >= 1 (vn.dcgs; s = st->jd, whose first
@@ -665,14 +678,14 @@ __device__ __forceinline__ void row_layer_q(const RowSmem<LPR>& sm, int er, int 
 template <int LPR> struct RowBounds { static constexpr int MIN_BLOCKS = 1; };
 
 template <class HT, int FORM, int LPR, int DB, int K = 1>
-__global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
-k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
-            const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
-            const __grid_constant__ LayerWT lw) {
+__device__ __forceinline__ void gconv_row_body(VGrid gb, const int* __restrict__ rp, const int* __restrict__ col,
+                                               const float* __restrict__ valhat, const HT* __restrict__ Hin,
+                                               HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
+                                               const LayerWT& lw) {
   constexpr int RB = TILE / LPR;
   __shared__ RowSmem<LPR> sm;
   const int t = threadIdx.x;
-  const int r0 = blockIdx.x * RB;
+  const int r0 = gb.bid * RB;
   const int gr = t / LPR, p = t % LPR;
   int rs, deg, c[DB];
   float v[DB];
@@ -690,14 +703,22 @@ k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float
 
 template <class HT, int FORM, int LPR, int DB, int K = 1>
 __global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
-k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
-                const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
-                const int* __restrict__ ctl, const __grid_constant__ LayerWT lw, const __grid_constant__ DecWT dw) {
+k_gconv_row(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
+            const HT* __restrict__ Hin, HT* __restrict__ Hout, int n, const int* __restrict__ ctl,
+            const __grid_constant__ LayerWT lw) {
+  gconv_row_body<HT, FORM, LPR, DB, K>(hw_grid(), rp, col, valhat, Hin, Hout, n, ctl, lw);
+}
+
+template <class HT, int FORM, int LPR, int DB, int K = 1>
+__device__ __forceinline__ void gconv_row_dec_body(VGrid gb, const int* __restrict__ rp, const int* __restrict__ col,
+                                                   const float* __restrict__ valhat, const HT* __restrict__ Hin,
+                                                   ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
+                                                   const int* __restrict__ ctl, const LayerWT& lw, const DecWT& dw) {
   constexpr int RB = TILE / LPR;
   constexpr int PW = 16 / LPR;
   __shared__ RowSmem<LPR> sm;
   const int t = threadIdx.x;
-  const int r0 = blockIdx.x * RB;
+  const int r0 = gb.bid * RB;
   const int gr = t / LPR, p = t % LPR;
   int rs, deg, c[DB];
   float v[DB];
@@ -744,6 +765,14 @@ k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const f
   }
 }
 
+template <class HT, int FORM, int LPR, int DB, int K = 1>
+__global__ void __launch_bounds__(TILE, RowBounds<LPR>::MIN_BLOCKS)
+k_gconv_row_dec(const int* __restrict__ rp, const int* __restrict__ col, const float* __restrict__ valhat,
+                const HT* __restrict__ Hin, ColPtr zp, const double* __restrict__ tau, double sqrt_n, int n,
+                const int* __restrict__ ctl, const __grid_constant__ LayerWT lw, const __grid_constant__ DecWT dw) {
+  gconv_row_dec_body<HT, FORM, LPR, DB, K>(hw_grid(), rp, col, valhat, Hin, zp, tau, sqrt_n, n, ctl, lw, dw);
+}
+
 template <class HT>
 __global__ void k_hidden_to_f32(const HT* __restrict__ H, float* __restrict__ out, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
@@ -751,6 +780,98 @@ __global__ void k_hidden_to_f32(const HT* __restrict__ H, float* __restrict__ ou
     if constexpr (sizeof(HT) == 4) out[i] = H[i];
     else out[i] = __uint_as_float(((uint32_t)H[i]) << 16);
   }
+}
+
+// ---------------------------------------------------------------- grouped GNP (serving)
+//
+// The encoder, layer and decoder-fused layer bodies for up to GW requests in one launch
+// (work table: each request's stand-alone grid).  Each request's weights travel in the
+// kernel parameters; a switch on the entry index hands the body that request's copy at a
+// constant offset, so the epilogues read constant-bank operands as the stand-alone
+// kernels do (six inlined copies of each body).
+static_assert(GW == 6, "GNP_GW_SWITCH has six cases");
+#define GNP_GW_SWITCH(i, CALL) \
+  switch (i) {                 \
+    case 0: CALL(0); break;    \
+    case 1: CALL(1); break;    \
+    case 2: CALL(2); break;    \
+    case 3: CALL(3); break;    \
+    case 4: CALL(4); break;    \
+    default: CALL(5); break;   \
+  }
+
+struct GEncP {
+  GTable t;
+  const GSlot* sl;
+  EncW w[GW];
+};
+struct GLayerP {
+  GTable t;
+  const GSlot* sl;
+  int l;
+  LayerWT w[GW];
+};
+struct GDecP {
+  GTable t;
+  const GSlot* sl;
+  LayerWT lw[GW];
+  DecWT dw[GW];
+};
+
+// A request's grid here is its stand-alone encoder grid plus one block (k_encode_vn's).  At a
+// cycle's first step (st->fresh: k_residual just restarted it) the request runs k_encode's
+// body, v_0 = r / beta, on the first nt blocks and the extra block returns; later steps
+// run k_encode_vn's body (v_j formed from step j-1's passes, whose Givens update the extra
+// block does; after step m-1 that update ends the cycle).
+template <class HT>
+__global__ void __launch_bounds__(TILE) kg_encode(const __grid_constant__ GEncP P) {
+  VGrid g;
+  const int i = gt_entry(P.t, g);
+  const GSlot& d = P.sl[P.t.slot[i]];
+  HT* H0 = static_cast<HT*>(d.Hh[0]);
+  const int* ctl = reinterpret_cast<const int*>(d.st);
+  if (d.st->fresh) {
+    if (g.bid == g.nblk - 1) return;
+    const VGrid ge{g.bid, g.nblk - 1};
+    const ColPtr v{d.V, sizeof(double) * (size_t)d.n, ctl, 0};
+#define GNP_ENC0(k) encode_body<HT>(ge, v, &d.st->vscale, d.tau, ctl, d.n, d.sqrt_n, d.noscale, H0, P.w[k])
+    GNP_GW_SWITCH(i, GNP_ENC0)
+#undef GNP_ENC0
+  } else {
+    const VNext vn{d.V, d.w, d.h1, d.h2, d.st, d.Hb, d.R, d.cs, d.sn, d.g, d.hist, d.thist, d.hf, 0};
+#define GNP_ENC1(k) encode_vn_body<HT>(g, vn, d.n, d.sqrt_n, d.noscale, d.tau, H0, P.w[k])
+    GNP_GW_SWITCH(i, GNP_ENC1)
+#undef GNP_ENC1
+  }
+}
+
+// Layer P.l (< L - 1) of each request: Hh[l % 2] -> Hh[(l + 1) % 2].
+template <class HT, int FORM>
+__global__ void __launch_bounds__(TILE, RowBounds<4>::MIN_BLOCKS) kg_gconv_row(const __grid_constant__ GLayerP P) {
+  VGrid g;
+  const int i = gt_entry(P.t, g);
+  const GSlot& d = P.sl[P.t.slot[i]];
+  const HT* Hin = static_cast<const HT*>(d.Hh[P.l & 1]);
+  HT* Hout = static_cast<HT*>(d.Hh[(P.l + 1) & 1]);
+  const int* ctl = reinterpret_cast<const int*>(d.st);
+#define GNP_LAY(k) gconv_row_body<HT, FORM, 4, 5>(g, d.rp, d.col, d.valhat, Hin, Hout, d.n, ctl, P.w[k])
+  GNP_GW_SWITCH(i, GNP_LAY)
+#undef GNP_LAY
+}
+
+// The decoder-fused last layer of each request: Hh[(L - 1) % 2] -> z_j.
+template <class HT, int FORM>
+__global__ void __launch_bounds__(TILE, RowBounds<4>::MIN_BLOCKS) kg_gconv_row_dec(const __grid_constant__ GDecP P) {
+  VGrid g;
+  const int i = gt_entry(P.t, g);
+  const GSlot& d = P.sl[P.t.slot[i]];
+  const HT* Hin = static_cast<const HT*>(d.Hh[(d.L - 1) & 1]);
+  const int* ctl = reinterpret_cast<const int*>(d.st);
+  const ColPtr z{d.Z, sizeof(float) * (size_t)d.n, ctl, 0};
+#define GNP_DEC(k) \
+  gconv_row_dec_body<HT, FORM, 4, 5>(g, d.rp, d.col, d.valhat, Hin, z, d.tau, d.sqrt_n, d.n, ctl, P.lw[k], P.dw[k])
+  GNP_GW_SWITCH(i, GNP_DEC)
+#undef GNP_DEC
 }
 
 // ---------------------------------------------------------------- host side
@@ -1019,6 +1140,94 @@ static int multi_row_layers_k(gnp_model* M, float* H0, float* H1, ColPtr zp, con
 }
 
 bool multi_row_ok(const gnp_model* M) { return M->cfg.L >= 1 && row_kernel_mode(M->A) != 0; }
+
+// ---------------------------------------------------------------- grouped GNP launches
+
+bool grouped_ok(const gnp_model* M) { return M && M->cfg.L >= 1 && row_kernel_mode(M->A) / 10 == 4; }
+
+std::vector<GTable> gt_build(const std::vector<std::pair<int, int>>& entries, int cap) {
+  std::vector<GTable> out;
+  for (size_t e0 = 0; e0 < entries.size(); e0 += (size_t)cap) {
+    GTable t{};
+    t.count = (int)std::min(entries.size() - e0, (size_t)cap);
+    int b = 0;
+    for (int k = 0; k < t.count; ++k) {
+      t.slot[k] = entries[e0 + k].first;
+      t.start[k] = b;
+      b += entries[e0 + k].second;
+    }
+    t.start[t.count] = b;
+    out.push_back(t);
+  }
+  return out;
+}
+
+template <class HT, int FORM>
+static int grouped_apply_t(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st) {
+  constexpr int RB = TILE / 4;
+  const int R = (int)reqs.size();
+  int Lmax = 0;
+  for (const GHost& q : reqs) Lmax = std::max(Lmax, q.M->cfg.L);
+  for (int c0 = 0; c0 < R; c0 += GW) {  // encoder
+    const int c1 = std::min(R, c0 + GW);
+    std::vector<std::pair<int, int>> e;
+    for (int k = c0; k < c1; ++k) e.push_back({reqs[k].slot, (reqs[k].n + TILE - 1) / TILE + 1});
+    GEncP P{};
+    P.t = gt_build(e, GW)[0];
+    P.sl = d_slots;
+    for (int k = c0; k < c1; ++k) {
+      DecW dw;
+      fill_enc_dec(reqs[k].M->w_host, reqs[k].M->cfg.L, P.w[k - c0], dw);
+    }
+    kg_encode<HT><<<P.t.start[P.t.count], TILE, 0, st>>>(P);
+  }
+  for (int l = 0; l + 1 < Lmax; ++l) {  // layers before the last
+    std::vector<const GHost*> sub;
+    for (const GHost& q : reqs)
+      if (l + 1 < q.M->cfg.L) sub.push_back(&q);
+    for (size_t c0 = 0; c0 < sub.size(); c0 += GW) {
+      const size_t c1 = std::min(sub.size(), c0 + GW);
+      std::vector<std::pair<int, int>> e;
+      for (size_t k = c0; k < c1; ++k) e.push_back({sub[k]->slot, (sub[k]->n + RB - 1) / RB});
+      GLayerP P{};
+      P.t = gt_build(e, GW)[0];
+      P.sl = d_slots;
+      P.l = l;
+      for (size_t k = c0; k < c1; ++k) fill_layer_wt(sub[k]->M->w_host, l, P.w[k - c0]);
+      kg_gconv_row<HT, FORM><<<P.t.start[P.t.count], TILE, 0, st>>>(P);
+    }
+  }
+  for (int c0 = 0; c0 < R; c0 += GW) {  // decoder-fused last layer
+    const int c1 = std::min(R, c0 + GW);
+    std::vector<std::pair<int, int>> e;
+    for (int k = c0; k < c1; ++k) e.push_back({reqs[k].slot, (reqs[k].n + RB - 1) / RB});
+    GDecP P{};
+    P.t = gt_build(e, GW)[0];
+    P.sl = d_slots;
+    for (int k = c0; k < c1; ++k) {
+      const gnp_model* M = reqs[k].M;
+      fill_layer_wt(M->w_host, M->cfg.L - 1, P.lw[k - c0]);
+      fill_dec_wt(M->w_host, M->cfg.L, P.dw[k - c0]);
+    }
+    kg_gconv_row_dec<HT, FORM><<<P.t.start[P.t.count], TILE, 0, st>>>(P);
+  }
+  return check_launch("grouped GNP apply");
+}
+
+int grouped_apply_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st) {
+  if (reqs.empty()) return GNP_OK;
+  const gnp_model* M = reqs[0].M;
+  for (const GHost& q : reqs)
+    GNP_REQUIRE(grouped_ok(q.M) && q.M->hprec == M->hprec && q.M->cfg.form == M->cfg.form,
+                "grouped_apply_launch: requests of one launch need the short-row kernels and one hidden "
+                "precision and layer form");
+  const bool paper = M->cfg.form == GNP_LAYER_PAPER;
+  if (M->hprec == GNP_H_BF16)
+    return paper ? grouped_apply_t<uint16_t, GNP_LAYER_PAPER>(reqs, d_slots, st)
+                 : grouped_apply_t<uint16_t, GNP_LAYER_RESID>(reqs, d_slots, st);
+  return paper ? grouped_apply_t<float, GNP_LAYER_PAPER>(reqs, d_slots, st)
+               : grouped_apply_t<float, GNP_LAYER_RESID>(reqs, d_slots, st);
+}
 
 int multi_row_layers(gnp_model* M, int K, float* H0, float* H1, ColPtr zp, const double* tau_one, const int* ctl,
                      cudaStream_t st) {

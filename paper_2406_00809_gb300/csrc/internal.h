@@ -142,6 +142,69 @@ int tma_layer_launch(const gnp_mat* A, int form, bool dec, const float* valhat, 
                      const double* tau, double sqrt_n, const int* ctl, const LayerW& lw, const DecW& dw,
                      cudaStream_t st);
 
+// ---------------------------------------------------------------- grouped steps (serving)
+//
+// One request of the grouped solve server, as its kernels see it (a device array indexed by
+// slot): its matrix, its GNP scratch and its FGMRES workspace.  A grouped launch runs the
+// same kernel body for several requests at once: its blocks are the requests' own grids
+// laid end to end (GTable), each block working on its request's data with the block index
+// and count that request's stand-alone launch would have, so every request computes
+// exactly what a lone solve computes.
+struct GSlot {
+  const int* rp;
+  const int* col;
+  const double* val;
+  const float* valhat;  // A_hat = A / gamma (float32)
+  int n, L, noscale;
+  double sqrt_n;
+  void* Hh[2];  // hidden ping-pong blocks
+  double* tau;
+  double* V;
+  float* Z;
+  double* w;
+  DevState* st;
+  double* Hb;  // H_bar
+  double* R;
+  double* cs;
+  double* sn;
+  double* g;
+  double* h1;
+  double* h2;
+  double* hf;
+  double* hist;
+  unsigned long long* thist;
+  double* partials;
+  unsigned* counter;
+  const double* b;
+  double* x;
+};
+
+// Requests per grouped GNP launch: each request's weights ride in the launch's kernel
+// parameters (the decoder-fused layer carries a layer's and the decoder's, 4.4 KB), so that
+// the epilogues read them as constant-bank operands as the stand-alone kernels do.
+constexpr int GW = 6;
+
+// Host view of one grouped request: its slot in the device array, size and model.
+struct GHost {
+  int slot;
+  int n;
+  const gnp_model* M;
+};
+
+// Whether a request with preconditioner M can run in grouped steps (the short-row layer
+// kernels with four lanes per row, L >= 1).
+bool grouped_ok(const gnp_model* M);
+// z = M(v) of the current FGMRES step for every request of `reqs` (one hidden precision
+// and layer form): the encoder (forming v_j and finishing step j-1, or v_0 = r / beta at a
+// cycle's first step), the L-1 Res-GCONV layers and the decoder-fused last layer.
+int grouped_apply_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st);
+// The rest of the step for every request: w = A z with CGS2 pass 1, then pass 2.
+int grouped_krylov_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st);
+// Cycle end for the requests of `reqs`: x += Z y, r = b - A x, beta and the restart.
+int grouped_cycle_end_launch(const std::vector<GHost>& reqs, int m, const GSlot* d_slots, cudaStream_t st);
+// Work tables: entries (slot, blocks) in order, at most `cap` per table.
+std::vector<GTable> gt_build(const std::vector<std::pair<int, int>>& entries, int cap);
+
 // Make the host copy of the weights current (after training).
 int model_sync_host(gnp_model* M);
 // Everything apply_launch needs that is not a stream operation (host weights, kernel

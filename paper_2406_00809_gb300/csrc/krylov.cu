@@ -254,11 +254,11 @@ constexpr int SPMV_ROW_DMAX = 32;
 // w_i = sum_j a_ij x_j for the rows i = blockIdx.x * blockDim.x + threadIdx.x + c * gridDim.x
 // * blockDim.x, one thread per row, in column order with eight nonzeros' loads in flight.
 template <class XT>
-__device__ __forceinline__ void row_spmv(const int* __restrict__ rp, const int* __restrict__ col,
+__device__ __forceinline__ void row_spmv(VGrid gr, const int* __restrict__ rp, const int* __restrict__ col,
                                          const double* __restrict__ val, const XT* __restrict__ x,
                                          double* __restrict__ w, int n) {
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gstride = gridDim.x * blockDim.x;
+  const int gtid = gr.bid * blockDim.x + threadIdx.x;
+  const int gstride = gr.nblk * blockDim.x;
   for (int i = gtid; i < n; i += gstride) {
     const int rs = __ldg(rp + i), re = __ldg(rp + i + 1);
     double s = 0.0;
@@ -283,25 +283,34 @@ __device__ __forceinline__ void row_spmv(const int* __restrict__ rp, const int* 
 }
 
 template <class XT>
-__global__ void __launch_bounds__(RED_THREADS)
-k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-               ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
-               double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
+__device__ __forceinline__ void spmv_dot_row_body(VGrid gr, const int* __restrict__ rp, const int* __restrict__ col,
+                                                  const double* __restrict__ val, ColPtr xp, double* __restrict__ w,
+                                                  const double* __restrict__ V, int n, DevState* st,
+                                                  double* __restrict__ h1, double* __restrict__ partials,
+                                                  unsigned* counter) {
   if (!st->active) return;
   __shared__ double sred[RED_SH];
   __shared__ double shtot[GNP_MAX_RESTART + 2];
   const int j = st->j;
   const int K = j + 2;  // h1[0..j] and ||w||^2
-  const size_t ld = (size_t)n;
-  row_spmv(rp, col, val, static_cast<const XT*>(colptr_k(xp)), w, n);
-  block_dots(V, w, n, K, j + 1, sred, partials + (size_t)blockIdx.x * K);
-  if (!last_block_arrive(counter)) return;
-  reduce_partials(partials, gridDim.x, K, shtot);
+  row_spmv(gr, rp, col, val, static_cast<const XT*>(colptr_k(xp)), w, n);
+  block_dots(gr, V, w, n, K, j + 1, sred, partials + (size_t)gr.bid * K);
+  if (!last_block_arrive(counter, gr.nblk)) return;
+  reduce_partials(partials, gr.nblk, K, shtot);
   if (threadIdx.x == 0) {
     for (int k = 0; k <= j; ++k) h1[k] = shtot[k];
     st->wnorm0 = sqrt(shtot[j + 1]);
+    st->fresh = 0;
     *counter = 0;
   }
+}
+
+template <class XT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_spmv_dot_row(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+               ColPtr xp, double* __restrict__ w, const double* __restrict__ V, int n, DevState* st,
+               double* __restrict__ h1, double* __restrict__ partials, unsigned* counter) {
+  spmv_dot_row_body<XT>(hw_grid(), rp, col, val, xp, w, V, n, st, h1, partials, counter);
 }
 
 // ---------------------------------------------------------------- overlapped CGS2
@@ -398,7 +407,7 @@ k_spmv_rdot_row(const int* __restrict__ rp, const int* __restrict__ col, const d
   const int s = a.st->j;
   const int K = s + 2;
   double* w = const_cast<double*>(a.w);
-  row_spmv(rp, col, val, static_cast<const XT*>(colptr_k(xp)), w, n);
+  row_spmv(hw_grid(), rp, col, val, static_cast<const XT*>(colptr_k(xp)), w, n);
   block_dots(a.V, w, n, K, s + 1, sred, partials + (size_t)blockIdx.x * K);
   if (!last_block_arrive(counter)) return;
   rdot_tail(a, partials, gridDim.x, s, counter);
@@ -508,15 +517,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_dfinish(const VNext a) {
 }
 
 // r = b - A x -> V[:, 0], beta = ||r||; the last block restarts the cycle state.
-__global__ void __launch_bounds__(TILE)
-k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
-           const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ V0, int n,
-           DevState* st, double* __restrict__ g, double* __restrict__ hist,
-           unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
+__device__ __forceinline__ void residual_body(VGrid gr, const int* __restrict__ rp, const int* __restrict__ col,
+                                              const double* __restrict__ val, const double* __restrict__ x,
+                                              const double* __restrict__ b, double* __restrict__ V0, int n,
+                                              DevState* st, double* __restrict__ g, double* __restrict__ hist,
+                                              unsigned long long* __restrict__ thist, double* __restrict__ partials,
+                                              unsigned* counter) {
   using TR = TrSpmv<double>;
   __shared__ TileSmem<TR> sm;
   __shared__ double sh[32];
-  const int r0 = blockIdx.x * TILE;
+  const int r0 = gr.bid * TILE;
   const int rows = min(TILE, n - r0);
   tile_load_rp<TR>(sm, rp, r0, rows);
   __syncthreads();
@@ -531,10 +541,10 @@ k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double
     acc = r * r;
   }
   double t = block_sum(acc, sh);
-  if (threadIdx.x == 0) partials[blockIdx.x] = t;
-  if (last_block_arrive(counter)) {
+  if (threadIdx.x == 0) partials[gr.bid] = t;
+  if (last_block_arrive(counter, gr.nblk)) {
     __shared__ double tot[1];
-    reduce_partials(partials, gridDim.x, 1, tot);
+    reduce_partials(partials, gr.nblk, 1, tot);
     if (threadIdx.x == 0) {
       const double beta = sqrt(tot[0]);
       st->beta = beta;
@@ -548,11 +558,20 @@ k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double
       st->jj = 0;
       st->flags = 0;
       st->vscale = beta;
+      st->fresh = 1;
       g[0] = beta;
       st->active = (isfinite(beta) && beta > st->tol && st->iters < st->maxiters) ? 1 : 0;
       *counter = 0;
     }
   }
+}
+
+__global__ void __launch_bounds__(TILE)
+k_residual(const int* __restrict__ rp, const int* __restrict__ col, const double* __restrict__ val,
+           const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ V0, int n,
+           DevState* st, double* __restrict__ g, double* __restrict__ hist,
+           unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
+  residual_body(hw_grid(), rp, col, val, x, b, V0, n, st, g, hist, thist, partials, counter);
 }
 
 // ||b|| and tol = rtol ||b||.
@@ -591,11 +610,12 @@ k_vscale(double* __restrict__ V, int n, const DevState* st) {
 // ---------------------------------------------------------------- CGS2 passes
 
 template <int PASS>
-__global__ void __launch_bounds__(RED_THREADS)
-k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, double* __restrict__ h1,
-      double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
-      double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
-      unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
+__device__ __forceinline__ void cgs_body(VGrid gr, double* __restrict__ V, int n, double* __restrict__ w,
+                                         DevState* st, double* __restrict__ h1, double* __restrict__ h2,
+                                         double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
+                                         double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
+                                         unsigned long long* __restrict__ thist, double* __restrict__ partials,
+                                         unsigned* counter) {
   if (!st->active) return;
   constexpr bool NORM = PASS == 1 || PASS == 4;  // the dots also give ||w||^2 (entry j+1)
   __shared__ double shh[GNP_MAX_RESTART + 2];
@@ -605,8 +625,8 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   __shared__ double sx[PASS == 4 ? 2 * (GNP_MAX_RESTART + 4) : 1];
   const int j = st->j;
   const size_t ld = (size_t)n;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gstride = gridDim.x * blockDim.x;
+  const int gtid = gr.bid * blockDim.x + threadIdx.x;
+  const int gstride = gr.nblk * blockDim.x;
   if (PASS >= 2) {
     const double* hp = (PASS == 3) ? h2 : h1;
     for (int k = threadIdx.x; k <= j; k += blockDim.x) shh[k] = hp[k];
@@ -624,7 +644,7 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
       acc += x * x;
     }
     double t = block_sum(acc, shred[0]);
-    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+    if (threadIdx.x == 0) partials[gr.bid] = t;
   } else {
     if (PASS == 2 || PASS == 4) {
       for (int i = gtid; i < n; i += gstride) {
@@ -635,11 +655,11 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
       }
     }
     const int K = NORM ? j + 2 : j + 1;  // passes 1 and 4 also ||w||^2 as entry j+1
-    block_dots(V, w, n, K, NORM ? j + 1 : -1, sred, partials + (size_t)blockIdx.x * K);
+    block_dots(gr, V, w, n, K, NORM ? j + 1 : -1, sred, partials + (size_t)gr.bid * K);
   }
-  if (!last_block_arrive(counter)) return;
+  if (!last_block_arrive(counter, gr.nblk)) return;
   const int K = NORM ? j + 2 : (PASS == 2 ? j + 1 : 1);
-  reduce_partials(partials, gridDim.x, K, shtot);
+  reduce_partials(partials, gr.nblk, K, shtot);
   if (PASS == 4) {
     // h2 and ||w1||^2 go out; k_vnext finishes the step (Givens update in its block 0)
     for (int i = threadIdx.x; i <= j; i += blockDim.x) h2[i] = shtot[i];
@@ -676,6 +696,15 @@ k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, doubl
   // PASS 3: column j of H_bar and the Givens update of the least-squares problem
   const double hn = sqrt(shtot[0]);
   arnoldi_step_finish(st, j, shtot + 1, hn, shh, &shred[0][0], H, R, cs, sn, g, hist, thist);
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(RED_THREADS)
+k_cgs(double* __restrict__ V, int n, double* __restrict__ w, DevState* st, double* __restrict__ h1,
+      double* __restrict__ h2, double* __restrict__ H, double* __restrict__ R, double* __restrict__ cs,
+      double* __restrict__ sn, double* __restrict__ g, double* __restrict__ hist,
+      unsigned long long* __restrict__ thist, double* __restrict__ partials, unsigned* counter) {
+  cgs_body<PASS>(hw_grid(), V, n, w, st, h1, h2, H, R, cs, sn, g, hist, thist, partials, counter);
 }
 
 // After k_cgs<4>, for step j = st->jv.  Block 0 finishes the step while the others form
@@ -719,14 +748,14 @@ k_vnext(const VNext a, int n) {
 // multiply and one fused multiply-add (the reciprocals of the diagonal are formed in
 // parallel first) instead of a five-level shuffle tree and a division: float64 operations
 // that depend on one another cost tens of cycles each on GB300.
+// sR: jj x jj doubles of dynamic shared memory (the upper triangle of R, column-major).
 template <class ZT>
-__global__ void __launch_bounds__(RED_THREADS)
-k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevState* st,
-          const double* __restrict__ R, const double* __restrict__ g) {
+__device__ __forceinline__ void xupdate_body(VGrid gr, const ZT* __restrict__ Z, double* __restrict__ x, int n,
+                                             const DevState* st, const double* __restrict__ R,
+                                             const double* __restrict__ g, double* sR) {
   __shared__ double y[GNP_MAX_RESTART];
   __shared__ double sg[GNP_MAX_RESTART];
   __shared__ double rinv[GNP_MAX_RESTART];
-  extern __shared__ double sR[];  // jj x jj upper triangle of R, column-major, ld = jj
   const int jj = st->jj;
   if (jj == 0) return;
   const int ldh = st->m + 1;
@@ -751,11 +780,52 @@ k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevStat
   }
   __syncthreads();
   const size_t ld = (size_t)n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int i = gr.bid * blockDim.x + threadIdx.x; i < n; i += gr.nblk * blockDim.x) {
     double acc = x[i];
     for (int k = 0; k < jj; ++k) acc += (double)Z[k * ld + i] * y[k];
     x[i] = acc;
   }
+}
+
+template <class ZT>
+__global__ void __launch_bounds__(RED_THREADS)
+k_xupdate(const ZT* __restrict__ Z, double* __restrict__ x, int n, const DevState* st,
+          const double* __restrict__ R, const double* __restrict__ g) {
+  extern __shared__ double sR[];
+  xupdate_body<ZT>(hw_grid(), Z, x, n, st, R, g, sR);
+}
+
+// ---------------------------------------------------------------- grouped steps (serving)
+//
+// The same bodies for several requests per launch (GTable: each request's stand-alone
+// grid; GSlot: its data).  The GNP-preconditioned step of the two-pass CGS2 schedule:
+// w = A z with pass 1, pass 2 (the Givens update of the step follows in the next step's
+// encoder); the cycle end x += Z y and the restart r = b - A x.
+__global__ void __launch_bounds__(RED_THREADS) kg_spmv_dot_row(const __grid_constant__ GTable t, const GSlot* sl) {
+  VGrid g;
+  const GSlot& d = sl[t.slot[gt_entry(t, g)]];
+  const ColPtr z{d.Z, sizeof(float) * (size_t)d.n, reinterpret_cast<const int*>(d.st), 0};
+  spmv_dot_row_body<float>(g, d.rp, d.col, d.val, z, d.w, d.V, d.n, d.st, d.h1, d.partials, d.counter);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) kg_cgs2(const __grid_constant__ GTable t, const GSlot* sl) {
+  VGrid g;
+  const GSlot& d = sl[t.slot[gt_entry(t, g)]];
+  cgs_body<4>(g, d.V, d.n, d.w, d.st, d.h1, d.h2, d.Hb, d.R, d.cs, d.sn, d.g, d.hist, d.thist, d.partials,
+              d.counter);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) kg_xupdate(const __grid_constant__ GTable t, const GSlot* sl) {
+  extern __shared__ double sR[];
+  VGrid g;
+  const GSlot& d = sl[t.slot[gt_entry(t, g)]];
+  xupdate_body<float>(g, d.Z, d.x, d.n, d.st, d.R, d.g, sR);
+}
+
+__global__ void __launch_bounds__(TILE) kg_residual(const __grid_constant__ GTable t, const GSlot* sl) {
+  VGrid g;
+  const GSlot& d = sl[t.slot[gt_entry(t, g)]];
+  residual_body(g, d.rp, d.col, d.val, d.x, d.b, d.V, d.n, d.st, d.g, d.hist, d.thist, d.partials, d.counter);
 }
 
 // ---------------------------------------------------------------- host side
@@ -779,6 +849,27 @@ int solver_ensure_zd(Solver* S, int m) {
   GNP_TRY(dev_alloc(&S->Zd, (size_t)S->n * m));
   S->zd_m = m;
   return GNP_OK;
+}
+
+int grouped_krylov_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st) {
+  std::vector<std::pair<int, int>> e;
+  for (const GHost& q : reqs) e.push_back({q.slot, dot_blocks(q.n)});
+  const std::vector<GTable> tabs = gt_build(e, GT_MAX);
+  for (const GTable& t : tabs) kg_spmv_dot_row<<<t.start[t.count], RED_THREADS, 0, st>>>(t, d_slots);
+  for (const GTable& t : tabs) kg_cgs2<<<t.start[t.count], RED_THREADS, 0, st>>>(t, d_slots);
+  return check_launch("grouped FGMRES step");
+}
+
+int grouped_cycle_end_launch(const std::vector<GHost>& reqs, int m, const GSlot* d_slots, cudaStream_t st) {
+  std::vector<std::pair<int, int>> ex, er;
+  for (const GHost& q : reqs) {
+    ex.push_back({q.slot, red_blocks(q.n)});
+    er.push_back({q.slot, (q.n + TILE - 1) / TILE});
+  }
+  const int xsm = (int)sizeof(double) * m * m;
+  for (const GTable& t : gt_build(ex, GT_MAX)) kg_xupdate<<<t.start[t.count], RED_THREADS, xsm, st>>>(t, d_slots);
+  for (const GTable& t : gt_build(er, GT_MAX)) kg_residual<<<t.start[t.count], TILE, 0, st>>>(t, d_slots);
+  return check_launch("grouped FGMRES cycle end");
 }
 
 // The reorthogonalisation stream (highest priority, so that its short kernels take SM

@@ -10,6 +10,20 @@
 // the queue, so no request waits for another's cycle (the requests' work overlaps on the
 // device).  A request's result does not depend on what else runs: every kernel reads
 // only its own request's data and all reductions have a fixed order.
+//
+// Grouped steps (gnp_server_config::grouped): requests whose GNP runs on the short-row
+// layer kernels share one stream and advance one FGMRES step per round, every kernel of
+// the step launched once for all of them over a work table (each request's own grid,
+// GTable; its data, GSlot).  A round is the encoder, the L Res-GCONV layers and the two
+// CGS2 passes of the step for every grouped request, captured once as a CUDA graph per
+// set of grouped requests, plus the cycle-end kernels (x update, residual) of the requests
+// whose restart cycle ends in that round.  Request r sits at phase p in [0, m] of its cycle:
+// rounds with p < m run step p; at p = m the encoder's extra block finishes step m-1 (which
+// ends the cycle), and the cycle end follows in the same round.  The loop reads each cycle's
+// state asynchronously (pinned copy + event), applies the stopping rules and, when a
+// request ends or a grouped request is admitted, drains the stream, releases and admits,
+// and captures the round again: admission at step granularity.  The grouped step follows
+// the two-pass CGS2 schedule of fgmres_solve (GNP_ORTHO=cgs2), kernel for kernel.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -50,6 +64,36 @@ struct Request {
   int result = GNP_OK;
   int status = -1;
   gnp_solve_info info{};
+  // grouped steps: the request's slot, its phase in the cycle (rounds since the cycle
+  // began, 0..m), a cycle end enqueued whose state the loop has not read, and the
+  // stopping rules' verdict (released at the next rebuild of the round)
+  bool grouped = false;
+  int slot = -1;
+  int phase = 0;
+  bool end_pending = false;
+  bool retire = false;
+  int end_status = GNP_OK;
+};
+
+// The grouped requests: one stream, the device slot array, the captured round.
+struct Group {
+  cudaStream_t stream = nullptr;
+  GSlot* d_slots = nullptr;
+  GSlot h_slots[GT_MAX] = {};
+  Request* req[GT_MAX] = {};
+  cudaGraphExec_t exec = nullptr;
+  struct End {
+    cudaEvent_t ev;
+    std::vector<Request*> reqs;
+  };
+  std::deque<End> ends;            // enqueued cycle ends, oldest first
+  std::deque<cudaEvent_t> rounds;  // one event per enqueued round (bounds the rounds in flight)
+  std::vector<cudaEvent_t> pool;
+  int live() const {
+    int c = 0;
+    for (Request* r : req) c += r != nullptr;
+    return c;
+  }
 };
 
 struct Server {
@@ -66,10 +110,12 @@ struct Server {
   long long next_ticket = 1;
   size_t used_bytes = 0;
   bool stop = false;
-  // statistics (`rounds`: restart cycles launched)
+  // statistics (`rounds`: restart cycles begun)
   long long rounds = 0, completed = 0, admitted = 0, max_active_seen = 0;
   int error = GNP_OK;
   char errmsg[256] = {0};
+  Group grp;  // loop thread only (besides its count, grp_live, published under the lock)
+  int grp_live = 0;
 };
 
 static size_t request_footprint(const gnp_mat* A, int m, int maxiters) {
@@ -100,23 +146,15 @@ static void finish(Server* sv, Request* r, int status) {
   r->info.seconds = std::chrono::duration<double>(Clock::now() - r->t_submit).count();
 }
 
-// Allocate the request's workspace and stream, run its initial residual, capture and
-// instantiate its cycle graph.  Returns true when the request is still running afterwards.
-static bool setup(Server* sv, Request* r) {
-  (void)sv;
-  int s = GNP_OK;
-  if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
-    set_error("server: stream or event creation failed");
-    s = GNP_ERR_CUDA;
-  }
+// Allocate the request's workspace, run its initial residual on `st` and apply the checks
+// that can end a solve before its first cycle.  Returns true when the request still runs.
+static bool prepare(Server* sv, Request* r, int s, cudaStream_t st) {
   if (s == GNP_OK) s = solver_create(r->A->n, r->m, r->maxiters, &r->S);
   if (s == GNP_OK && r->M) s = apply_ws_alloc(r->ws, r->A->n);
   if (s == GNP_OK && cudaMallocHost(reinterpret_cast<void**>(&r->mirror), sizeof(DevState)) != cudaSuccess) {
     set_error("server: cudaMallocHost failed");
     s = GNP_ERR_OOM;
   }
-  cudaStream_t st = r->stream;
   if (s == GNP_OK && r->M) s = apply_prepare(r->M);
   if (s == GNP_OK) s = solve_init_launch(r->A, r->S, r->b, r->x, r->rtol, r->maxiters, r->m, 0.0, st);
   if (s == GNP_OK && cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost, st) !=
@@ -152,6 +190,20 @@ static bool setup(Server* sv, Request* r) {
     finish(sv, r, GNP_ERR_NOT_CONVERGED);
     return false;
   }
+  return true;
+}
+
+// Allocate the request's workspace and stream, run its initial residual, capture and
+// instantiate its cycle graph.  Returns true when the request is still running afterwards.
+static bool setup(Server* sv, Request* r) {
+  int s = GNP_OK;
+  if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) {
+    set_error("server: stream or event creation failed");
+    s = GNP_ERR_CUDA;
+  }
+  cudaStream_t st = r->stream;
+  if (!prepare(sv, r, s, st)) return false;
   // capture the restart cycle once; its device-side step state makes it replayable
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     set_error("server: begin capture failed");
@@ -197,13 +249,275 @@ static void fill_result(Request* r) {
   r->info.rel_res_est = hs.res_est / bn;
 }
 
+// ---------------------------------------------------------------- grouped steps
+
+static cudaEvent_t group_event(Group& G) {
+  cudaEvent_t e = nullptr;
+  if (!G.pool.empty()) {
+    e = G.pool.back();
+    G.pool.pop_back();
+  } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    e = nullptr;
+  }
+  return e;
+}
+
+// Every grouped request ends with `status` (a launch or the device failed).
+static void group_fail_all(Server* sv, int status) {
+  for (Request* r : sv->grp.req)
+    if (r && !r->retire) {
+      r->retire = true;
+      r->end_status = status;
+    }
+}
+
+// The oldest enqueued cycle end, once its state copy has landed: the stopping rules of
+// each of its requests (as fgmres_solve applies them after a cycle).
+static void group_end_read(Server* sv) {
+  Group& G = sv->grp;
+  Group::End e = G.ends.front();
+  G.ends.pop_front();
+  for (Request* r : e.reqs) {
+    r->end_pending = false;
+    ++r->ctl.cycles;
+    int status = GNP_OK;
+    const DevState& hs = *r->mirror;
+    const bool end = cycle_after(hs, r->beta, r->maxiters, r->ctl, &status);
+    r->beta = hs.beta;
+    if (end && !r->retire) {
+      r->retire = true;
+      r->end_status = status;
+    }
+  }
+  G.pool.push_back(e.ev);
+}
+
+// Read the cycle ends that have completed (blocking: all of them).  Returns whether any.
+static bool group_poll(Server* sv, bool block) {
+  Group& G = sv->grp;
+  bool any = false;
+  while (!G.ends.empty()) {
+    const cudaError_t q = block ? cudaEventSynchronize(G.ends.front().ev) : cudaEventQuery(G.ends.front().ev);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) {
+      set_error("server: grouped round failed: %s", cudaGetErrorString(q));
+      for (Request* r : G.ends.front().reqs) r->end_pending = false;
+      G.pool.push_back(G.ends.front().ev);
+      G.ends.pop_front();
+      group_fail_all(sv, GNP_ERR_CUDA);
+      any = true;
+      continue;
+    }
+    group_end_read(sv);
+    any = true;
+  }
+  return any;
+}
+
+// Capture the round for the current grouped requests: per class of hidden precision and
+// layer form the GNP application, then the CGS2 passes of all of them.
+static int group_capture(Server* sv) {
+  Group& G = sv->grp;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+  std::vector<GHost> all;
+  std::vector<std::vector<GHost>> cls(4);
+  for (int k = 0; k < GT_MAX; ++k) {
+    Request* r = G.req[k];
+    if (!r) continue;
+    const GHost h{k, r->A->n, r->M};
+    all.push_back(h);
+    cls[(r->M->hprec == GNP_H_BF16 ? 2 : 0) + (r->M->cfg.form == GNP_LAYER_PAPER ? 0 : 1)].push_back(h);
+  }
+  if (all.empty()) return GNP_OK;
+  GNP_TRY_CUDA(cudaMemcpy(G.d_slots, G.h_slots, sizeof(G.h_slots), cudaMemcpyHostToDevice));
+  GNP_TRY_CUDA(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal));
+  int s = GNP_OK;
+  for (const auto& c : cls)
+    if (s == GNP_OK) s = grouped_apply_launch(c, G.d_slots, G.stream);
+  if (s == GNP_OK) s = grouped_krylov_launch(all, G.d_slots, G.stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(G.stream, &graph);
+  if (s != GNP_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&G.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    set_error("server: capture of the grouped round failed: %s", cudaGetErrorString(ce));
+    G.exec = nullptr;
+    return GNP_ERR_CUDA;
+  }
+  return GNP_OK;
+}
+
+// Release the requests the stopping rules ended and admit `fresh` (grouped requests taken
+// from the queue): drain the stream, read every pending cycle end, free and fill slots,
+// capture the round again.  Requests that end here go to `ended`.
+static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<Request*>& ended) {
+  Group& G = sv->grp;
+  if (!G.stream) {
+    int e = GNP_OK;
+    if (cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking) != cudaSuccess) e = GNP_ERR_CUDA;
+    if (e == GNP_OK) e = dev_alloc(&G.d_slots, (size_t)GT_MAX);
+    if (e != GNP_OK) {
+      set_error("server: grouped stream or slot array");
+      for (Request* r : fresh) {
+        finish(sv, r, GNP_ERR_CUDA);
+        ended.push_back(r);
+      }
+      fresh.clear();
+      return;
+    }
+  }
+  if (cudaStreamSynchronize(G.stream) != cudaSuccess) {
+    set_error("server: grouped round failed: %s", cudaGetErrorString(cudaGetLastError()));
+    group_fail_all(sv, GNP_ERR_CUDA);
+  }
+  group_poll(sv, true);
+  for (cudaEvent_t e : G.rounds) G.pool.push_back(e);
+  G.rounds.clear();
+  for (int k = 0; k < GT_MAX; ++k) {
+    Request* r = G.req[k];
+    if (!r || !r->retire) continue;
+    fill_result(r);
+    finish(sv, r, r->end_status);
+    ended.push_back(r);
+    G.req[k] = nullptr;
+    G.h_slots[k] = GSlot{};
+  }
+  for (Request* r : fresh) {
+    ++sv->admitted;
+    if (!prepare(sv, r, GNP_OK, G.stream)) {
+      fill_result(r);
+      ended.push_back(r);
+      continue;
+    }
+    int k = 0;
+    while (G.req[k]) ++k;  // admission left a free slot for every grouped request
+    Solver* S = r->S;
+    GSlot& d = G.h_slots[k];
+    d = GSlot{};
+    d.rp = r->A->rp;
+    d.col = r->A->col;
+    d.val = r->A->val;
+    d.valhat = r->M->valhat;
+    d.n = r->A->n;
+    d.L = r->M->cfg.L;
+    d.noscale = r->M->cfg.no_scale ? 1 : 0;
+    d.sqrt_n = std::sqrt((double)r->A->n);
+    d.Hh[0] = r->ws.H[0];
+    d.Hh[1] = r->ws.H[1];
+    d.tau = r->ws.tau;
+    d.V = S->V;
+    d.Z = S->Z;
+    d.w = S->w;
+    d.st = S->st;
+    d.Hb = S->H;
+    d.R = S->R;
+    d.cs = S->cs;
+    d.sn = S->sn;
+    d.g = S->g;
+    d.h1 = S->h1;
+    d.h2 = S->h2;
+    d.hf = S->hf;
+    d.hist = S->hist;
+    d.thist = S->thist;
+    d.partials = S->red.partials;
+    d.counter = S->red.counter;
+    d.b = r->b;
+    d.x = r->x;
+    r->slot = k;
+    r->phase = 0;
+    G.req[k] = r;
+    ++sv->rounds;
+  }
+  fresh.clear();
+  if (group_capture(sv) != GNP_OK) {
+    group_fail_all(sv, GNP_ERR_CUDA);
+    group_rebuild(sv, fresh, ended);  // releases them all (nothing left to capture)
+  }
+}
+
+// Enqueue one round: the step of every grouped request, then the cycle end of those at
+// phase m (each after its previous cycle's state has been read), the copies of their
+// state and an event.
+static void group_round(Server* sv) {
+  Group& G = sv->grp;
+  std::vector<GHost> ending;
+  std::vector<Request*> ending_r;
+  for (int k = 0; k < GT_MAX; ++k) {
+    Request* r = G.req[k];
+    if (!r || r->phase != r->m) continue;
+    while (r->end_pending) group_poll(sv, true);
+    if (r->retire) continue;
+    ending.push_back(GHost{k, r->A->n, r->M});
+    ending_r.push_back(r);
+  }
+  int s = GNP_OK;
+  if (cudaGraphLaunch(G.exec, G.stream) != cudaSuccess) {
+    set_error("server: grouped round launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    s = GNP_ERR_CUDA;
+  }
+  if (s == GNP_OK && !ending.empty()) {
+    s = grouped_cycle_end_launch(ending, ending_r[0]->m, G.d_slots, G.stream);
+    for (Request* r : ending_r)
+      if (s == GNP_OK && cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                         G.stream) != cudaSuccess)
+        s = GNP_ERR_CUDA;
+    Group::End e{group_event(G), ending_r};
+    if (s == GNP_OK && (!e.ev || cudaEventRecord(e.ev, G.stream) != cudaSuccess)) s = GNP_ERR_CUDA;
+    if (s == GNP_OK) {
+      for (Request* r : ending_r) r->end_pending = true;
+      G.ends.push_back(e);
+    } else if (e.ev) {
+      G.pool.push_back(e.ev);
+    }
+  }
+  if (s != GNP_OK) {
+    group_fail_all(sv, GNP_ERR_CUDA);
+    return;
+  }
+  for (Request* r : G.req) {
+    if (!r) continue;
+    r->phase = r->phase == r->m ? 0 : r->phase + 1;
+    if (r->phase == 0 && !r->retire) ++sv->rounds;
+  }
+  // at most three rounds in flight: the loop stays close to the device
+  cudaEvent_t ev = group_event(G);
+  if (ev && cudaEventRecord(ev, G.stream) == cudaSuccess) G.rounds.push_back(ev);
+  else if (ev) G.pool.push_back(ev);
+  while (G.rounds.size() > 3) {
+    cudaEventSynchronize(G.rounds.front());
+    G.pool.push_back(G.rounds.front());
+    G.rounds.pop_front();
+  }
+}
+
+static void group_destroy(Group& G) {
+  if (G.stream) cudaStreamSynchronize(G.stream);
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto& e : G.ends) G.pool.push_back(e.ev);
+  for (cudaEvent_t e : G.rounds) G.pool.push_back(e);
+  for (cudaEvent_t e : G.pool) cudaEventDestroy(e);
+  G.pool.clear();
+  G.ends.clear();
+  G.rounds.clear();
+  if (G.stream) cudaStreamDestroy(G.stream);
+  dev_free(G.d_slots);
+  G.exec = nullptr;
+  G.stream = nullptr;
+}
+
 static void server_loop(Server* sv) {
   cudaSetDevice(sv->device);
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     // admission (under the lock): FIFO, by slot count and device-memory footprint
-    std::vector<Request*> fresh, ended;
-    while (!sv->queue.empty() && (int)(sv->running.size() + fresh.size()) < sv->cfg.max_active) {
+    std::vector<Request*> fresh, gfresh, ended;
+    while (!sv->queue.empty() &&
+           (int)(sv->running.size() + sv->grp_live + fresh.size() + gfresh.size()) < sv->cfg.max_active) {
       Request* r = sv->queue.front();
       if (r->footprint > sv->cfg.max_bytes) {
         sv->queue.pop_front();
@@ -214,17 +528,29 @@ static void server_loop(Server* sv) {
         continue;
       }
       if (sv->used_bytes + r->footprint > sv->cfg.max_bytes) break;
+      // a request that can run in grouped steps always does (its result must not depend on
+      // the load), so it waits for a grouped slot
+      const bool grp = sv->cfg.grouped && grouped_ok(r->M);
+      if (grp && sv->grp_live + (int)gfresh.size() >= GT_MAX) break;
       sv->queue.pop_front();
       sv->used_bytes += r->footprint;
-      fresh.push_back(r);
+      r->grouped = grp;
+      (grp ? gfresh : fresh).push_back(r);
     }
-    if (sv->stop && sv->queue.empty() && sv->running.empty() && fresh.empty()) break;
-    if (sv->running.empty() && fresh.empty()) {
+    if (sv->stop && sv->queue.empty() && sv->running.empty() && sv->grp_live == 0 && fresh.empty() &&
+        gfresh.empty())
+      break;
+    if (sv->running.empty() && sv->grp_live == 0 && fresh.empty() && gfresh.empty()) {
       sv->cv.wait_for(lk, std::chrono::milliseconds(50));
       continue;
     }
     lk.unlock();
-    bool progressed = !fresh.empty();
+    bool progressed = !fresh.empty() || !gfresh.empty();
+    // grouped requests: read finished cycle ends; release and admit (rebuilding the round)
+    progressed |= group_poll(sv, false);
+    bool rebuild = !gfresh.empty();
+    for (Request* r : sv->grp.req) rebuild |= r && r->retire;
+    if (rebuild) group_rebuild(sv, gfresh, ended);
     for (Request* r : fresh) {
       ++sv->admitted;
       if (setup(sv, r) && launch_next(sv, r) == GNP_OK) {
@@ -235,7 +561,8 @@ static void server_loop(Server* sv) {
         ended.push_back(r);
       }
     }
-    sv->max_active_seen = std::max<long long>(sv->max_active_seen, (long long)sv->running.size());
+    const int glive = sv->grp.live();
+    sv->max_active_seen = std::max<long long>(sv->max_active_seen, (long long)(sv->running.size() + glive));
     // every request whose cycle has ended: stopping rules, then its next cycle or retirement
     std::vector<Request*> still;
     for (Request* r : sv->running) {
@@ -270,6 +597,10 @@ static void server_loop(Server* sv) {
       }
     }
     sv->running.swap(still);
+    if (glive > 0) {
+      group_round(sv);
+      progressed = true;
+    }
     for (Request* r : ended) release(r);
     lk.lock();
     for (Request* r : ended) {
@@ -277,7 +608,8 @@ static void server_loop(Server* sv) {
       r->status = r->result;
       ++sv->completed;
     }
-    sv->n_active = (int)sv->running.size();
+    sv->grp_live = glive;
+    sv->n_active = (int)sv->running.size() + glive;
     if (!ended.empty()) sv->done_cv.notify_all();
     if (!progressed) {
       // no cycle ended and nothing was admitted: wait a little (new requests wake the loop)
@@ -412,6 +744,7 @@ void gnp_server_destroy(gnp_server* h) {
   }
   sv->cv.notify_all();
   if (sv->loop.joinable()) sv->loop.join();
+  group_destroy(sv->grp);
   for (auto& kv : sv->all) {
     release(kv.second);
     delete kv.second;

@@ -42,6 +42,8 @@ struct DevState {
   double rho_est;  // rho_s = ||w_s - V_s h_s|| by the first pass (Pythagorean)
   double rho_inv;  // 1 / rho (0 after a breakdown)
   double nu_inv;   // 1 / nu_s, nu_s = ||v'_s - V_{s-1} a_s|| (the second pass of step s)
+  int fresh;       // 1 from a cycle's restart (k_residual) until the first pass of its first
+                   // step (k_spmv_dot_row): tells the grouped encoder which body to run
 };
 
 // Device clock in nanoseconds (the PTX %globaltimer register, common to all SMs).
@@ -142,11 +144,11 @@ __device__ __forceinline__ void block_reduce_kc(const double (&a)[KC], double* s
 // pass for up to 32 columns, so that the basis loads of a row are in flight together and
 // the block reduces once.
 template <int KW>
-__device__ __forceinline__ void block_dots_w(const double* __restrict__ V, const double* __restrict__ w, int n,
-                                             int K, int normk, double* sh, double* part) {
+__device__ __forceinline__ void block_dots_w(VGrid gr, const double* __restrict__ V, const double* __restrict__ w,
+                                             int n, int K, int normk, double* sh, double* part) {
   const size_t ld = (size_t)n;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gstride = gridDim.x * blockDim.x;
+  const int gtid = gr.bid * blockDim.x + threadIdx.x;
+  const int gstride = gr.nblk * blockDim.x;
   for (int k0 = 0; k0 < K; k0 += KW) {
     double acc[KW];
 #pragma unroll
@@ -166,11 +168,15 @@ __device__ __forceinline__ void block_dots_w(const double* __restrict__ V, const
   }
 }
 
+__device__ __forceinline__ void block_dots(VGrid gr, const double* __restrict__ V, const double* __restrict__ w,
+                                           int n, int K, int normk, double* sh, double* part) {
+  if (K <= 8) block_dots_w<8>(gr, V, w, n, K, normk, sh, part);
+  else if (K <= 16) block_dots_w<16>(gr, V, w, n, K, normk, sh, part);
+  else block_dots_w<32>(gr, V, w, n, K, normk, sh, part);
+}
 __device__ __forceinline__ void block_dots(const double* __restrict__ V, const double* __restrict__ w, int n,
                                            int K, int normk, double* sh, double* part) {
-  if (K <= 8) block_dots_w<8>(V, w, n, K, normk, sh, part);
-  else if (K <= 16) block_dots_w<16>(V, w, n, K, normk, sh, part);
-  else block_dots_w<32>(V, w, n, K, normk, sh, part);
+  block_dots(hw_grid(), V, w, n, K, normk, sh, part);
 }
 
 

@@ -48,7 +48,7 @@ class _SolveInfo(C.Structure):
 
 
 class _ServerConfig(C.Structure):
-    _fields_ = [("max_bytes", C.c_size_t), ("max_active", C.c_int), ("restart", C.c_int)]
+    _fields_ = [("max_bytes", C.c_size_t), ("max_active", C.c_int), ("restart", C.c_int), ("grouped", C.c_int)]
 
 
 class _ServerStats(C.Structure):
@@ -578,8 +578,8 @@ class Server:
     """Continuous-batching solve server (gnp_server_*).  Keeps the buffers of every
     submitted request alive until it is collected."""
 
-    def __init__(self, max_bytes: int, max_active: int = 64, restart: int = 30):
-        cfg = _ServerConfig(max_bytes, max_active, restart)
+    def __init__(self, max_bytes: int, max_active: int = 64, restart: int = 30, grouped: bool = False):
+        cfg = _ServerConfig(max_bytes, max_active, restart, 1 if grouped else 0)
         out = C.c_void_p()
         _check(lib().gnp_server_create(C.byref(cfg), C.byref(out)))
         self.h = out
