@@ -605,7 +605,8 @@ def run_serve(args):
     t0 = time.perf_counter()
     pool = SB.build_pool(g, sa, rng)
     setup_s = time.perf_counter() - t0
-    srv = g.Server(max_bytes=int(sa.max_gb * (1 << 30)), max_active=sa.max_active, restart=30)
+    srv = g.Server(max_bytes=int(sa.max_gb * (1 << 30)), max_active=sa.max_active, restart=30,
+                   grouped=bool(args.serve_grouped))
     solo = SB.solo_latencies(g, srv, pool, sa)
     capacity = 1.0 / float(np.mean([s_["seconds"] for s_ in solo]))
     clk, clkf = clocks_start(args.clocks_log) if rank == 0 else (None, None)
@@ -627,6 +628,7 @@ def run_serve(args):
                        "powerlaw_shift_fraction": sa.powerlaw_shift, "n_range": [sa.nmin, sa.nmax],
                        "requests_per_rate": sa.requests, "loads": args.serve_loads,
                        "train_steps_per_problem": sa.train_steps, "maxiters": sa.maxiters,
+                       "server_mode": "grouped steps" if args.serve_grouped else "per-request streams",
                        "parallelism": f"replicas{ws}"},
             "pool": [{k: p[k] for k in ("fam", "n", "nnz", "train_s")} for p in pool], "setup_s": setup_s,
             "solo": solo, "sequential_capacity_per_s": capacity, "rates": rates, "clocks": clocks}
@@ -644,6 +646,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-loads", default="1,2,4", help="arrival rates as multiples of the sequential capacity")
     ap.add_argument("--serve-train-steps", type=int, default=500)
+    ap.add_argument("--serve-grouped", type=int, default=0, choices=[0, 1],
+                    help="1: the server's grouped steps for the short-row requests")
     ap.add_argument("--train-steps", type=int, default=None)
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -20,7 +20,9 @@ The arrival rates are multiples (--load) of the sequential capacity: one solve o
 pool problem is first run alone through the server, and 1 / (mean solo latency) is the
 rate at which requests served one at a time would just keep up.  Load 1 and above
 therefore measure how much concurrent requests gain over serial service.  One JSON line
-per rate (plus one with the solo latencies).
+per rate (plus one with the solo latencies).  --grouped 1 runs the server in grouped mode
+(the Poisson and convection-diffusion requests advance in grouped steps, the power-law
+ones, whose long rows need the tile kernels, per request).
 """
 from __future__ import annotations
 
@@ -164,6 +166,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--max-gb", type=float, default=120.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--grouped", type=int, default=0, choices=[0, 1],
+                    help="1: grouped steps for the requests whose GNP runs on the short-row kernels")
     a = ap.parse_args()
     import torch
     from paper_2406_00809_gb300 import build
@@ -175,13 +179,14 @@ def main():
     setup_s = time.perf_counter() - t0
     print(json.dumps({"pool": [{k: p[k] for k in ("fam", "n", "nnz", "train_s")} for p in pool],
                       "setup_s": setup_s}), flush=True)
-    srv = g.Server(max_bytes=int(a.max_gb * (1 << 30)), max_active=a.max_active, restart=30)
+    srv = g.Server(max_bytes=int(a.max_gb * (1 << 30)), max_active=a.max_active, restart=30,
+                   grouped=bool(a.grouped))
     solo = solo_latencies(g, srv, pool, a)
     capacity = 1.0 / float(np.mean([s_["seconds"] for s_ in solo]))
     print(json.dumps({"solo": solo, "sequential_capacity_per_s": capacity}), flush=True)
     for i, load in enumerate(float(r) for r in a.load.split(",")):
         out = run_rate(g, srv, pool, a, load * capacity, a.seed + 1 + i)
-        out.update({"metric": "serve latency", "load": load, "hprec": a.hprec, "pool": a.pool,
+        out.update({"metric": "serve latency", "load": load, "hprec": a.hprec, "pool": a.pool, "grouped": a.grouped,
                     "n_range": [a.nmin, a.nmax], "train_steps": a.train_steps})
         print(json.dumps(out), flush=True)
     srv.close()
