@@ -352,12 +352,14 @@ double gnp_time_auc(const double* res_history, const double* time_history, int l
  * Grouped mode (grouped = 1): requests whose GNP runs on the short-row layer kernels (every
  * row of A at most 16 nonzeros, L >= 1), at most 16 at once, advance together one FGMRES
  * step per round on one stream: each kernel of the step (encoder, Res-GCONV layers, SpMV
- * with CGS2 pass 1, pass 2) is launched once for all of them over a work table of the
- * requests' own grids, the round captured as one CUDA graph per set of running requests;
- * the requests whose restart cycle ends in a round get their cycle end in the same round.
- * Requests are admitted and retired between rounds.  Each grouped request computes
- * exactly what a lone fgmres_solve computes with the two-pass CGS2 schedule
- * (GNP_ORTHO=cgs2 in the environment); the other requests run as in per-request mode. */
+ * with CGS2 pass 1, pass 2, and the cycle end: x update and residual for the requests
+ * whose restart cycle ends in that round) is launched once for all of them over a work
+ * table of the requests' own grids.  The stopping rules run on the device at each cycle
+ * end, so eight rounds are captured as one CUDA graph per set of running requests and
+ * requests are admitted and released between launches of it (every eight steps).  Each
+ * grouped request computes exactly what a lone fgmres_solve computes with the two-pass
+ * CGS2 schedule (GNP_ORTHO=cgs2 in the environment); the other requests run as in
+ * per-request mode. */
 typedef struct gnp_server_config {
   size_t max_bytes; /* device-memory budget for the running requests' workspaces */
   int max_active;   /* requests running at once (slots) */
@@ -368,7 +370,7 @@ typedef struct gnp_server_config {
 typedef struct gnp_server_stats_t {
   int queued, active;
   size_t used_bytes;
-  long long rounds; /* restart cycles begun */
+  long long rounds; /* restart cycles run (a grouped request's counted when it ends) */
   long long completed, max_active_seen;
 } gnp_server_stats_t;
 

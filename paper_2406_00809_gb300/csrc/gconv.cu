@@ -818,7 +818,9 @@ struct GDecP {
   DecWT dw[GW];
 };
 
-// A request's grid here is its stand-alone encoder grid plus one block (k_encode_vn's).  At a
+// A request's grid here is its stand-alone encoder grid plus one block (k_encode_vn's); its
+// block 0 also advances the request's phase (GCtl), which no other kernel of the round
+// writes and which the cycle-end kernels read later in the round.  At a
 // cycle's first step (st->fresh: k_residual just restarted it) the request runs k_encode's
 // body, v_0 = r / beta, on the first nt blocks and the extra block returns; later steps
 // run k_encode_vn's body (v_j formed from step j-1's passes, whose Givens update the extra
@@ -830,6 +832,7 @@ __global__ void __launch_bounds__(TILE) kg_encode(const __grid_constant__ GEncP 
   const GSlot& d = P.sl[P.t.slot[i]];
   HT* H0 = static_cast<HT*>(d.Hh[0]);
   const int* ctl = reinterpret_cast<const int*>(d.st);
+  if (g.bid == 0 && threadIdx.x == 0) d.gc->phase = d.gc->phase >= d.m ? 0 : d.gc->phase + 1;  // the round
   if (d.st->fresh) {
     if (g.bid == g.nblk - 1) return;
     const VGrid ge{g.bid, g.nblk - 1};

@@ -150,7 +150,17 @@ int tma_layer_launch(const gnp_mat* A, int form, bool dec, const float* valhat, 
 // laid end to end (GTable), each block working on its request's data with the block index
 // and count that request's stand-alone launch would have, so every request computes
 // exactly what a lone solve computes.
+// A grouped request's place in its cycle and its stopping rules, kept on the device (not in
+// DevState, which the step kernels load and store whole): phase = the round's index in
+// the cycle (0..m, set by the round's encoder; -1 before the first round), the counters of
+// cycle_after, and done / status once the rules end the solve.
+struct GCtl {
+  int phase, done, status, stagn, mism, restarts, cycles, pad;
+};
+
 struct GSlot {
+  GCtl* gc;
+  int m;
   const int* rp;
   const int* col;
   const double* val;
@@ -200,7 +210,8 @@ bool grouped_ok(const gnp_model* M);
 int grouped_apply_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st);
 // The rest of the step for every request: w = A z with CGS2 pass 1, then pass 2.
 int grouped_krylov_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st);
-// Cycle end for the requests of `reqs`: x += Z y, r = b - A x, beta and the restart.
+// Cycle end for the requests of `reqs` that reach it this round (phase m): x += Z y,
+// r = b - A x, beta, the stopping rules, and the restart or the end of the solve.
 int grouped_cycle_end_launch(const std::vector<GHost>& reqs, int m, const GSlot* d_slots, cudaStream_t st);
 // Work tables: entries (slot, blocks) in order, at most `cap` per table.
 std::vector<GTable> gt_build(const std::vector<std::pair<int, int>>& entries, int cap);

@@ -522,7 +522,7 @@ __device__ __forceinline__ void residual_body(VGrid gr, const int* __restrict__ 
                                               const double* __restrict__ b, double* __restrict__ V0, int n,
                                               DevState* st, double* __restrict__ g, double* __restrict__ hist,
                                               unsigned long long* __restrict__ thist, double* __restrict__ partials,
-                                              unsigned* counter) {
+                                              unsigned* counter, GCtl* gc = nullptr) {
   using TR = TrSpmv<double>;
   __shared__ TileSmem<TR> sm;
   __shared__ double sh[32];
@@ -547,6 +547,7 @@ __device__ __forceinline__ void residual_body(VGrid gr, const int* __restrict__ 
     reduce_partials(partials, gr.nblk, 1, tot);
     if (threadIdx.x == 0) {
       const double beta = sqrt(tot[0]);
+      const double beta_prev = st->beta;  // the residual this cycle began from
       st->beta = beta;
       if (st->iters == 0) {
         hist[0] = beta / st->bnorm;
@@ -561,6 +562,22 @@ __device__ __forceinline__ void residual_body(VGrid gr, const int* __restrict__ 
       st->fresh = 1;
       g[0] = beta;
       st->active = (isfinite(beta) && beta > st->tol && st->iters < st->maxiters) ? 1 : 0;
+      if (gc) {  // grouped steps: the stopping rules here, so the next cycle needs no host
+        CycleCtl c;
+        c.stagn = gc->stagn;
+        c.mism = gc->mism;
+        c.restarts = gc->restarts;
+        c.cycles = ++gc->cycles;
+        int status = GNP_OK;
+        if (cycle_after(*st, beta_prev, st->maxiters, c, &status)) {
+          gc->done = 1;
+          gc->status = status;
+          st->active = 0;
+        }
+        gc->stagn = c.stagn;
+        gc->mism = c.mism;
+        gc->restarts = c.restarts;
+      }
       *counter = 0;
     }
   }
@@ -815,17 +832,25 @@ __global__ void __launch_bounds__(RED_THREADS) kg_cgs2(const __grid_constant__ G
               d.counter);
 }
 
+// Every round launches the cycle end for every request; only those at phase m (their
+// encoder finished step m-1 this round) and not done run it.  The residual's last block
+// applies the stopping rules (cycle_after) and either restarts the cycle or marks the
+// request done (active = 0: its later rounds do nothing, x stays as the deciding cycle
+// left it).
 __global__ void __launch_bounds__(RED_THREADS) kg_xupdate(const __grid_constant__ GTable t, const GSlot* sl) {
   extern __shared__ double sR[];
   VGrid g;
   const GSlot& d = sl[t.slot[gt_entry(t, g)]];
+  if (d.gc->phase != d.m || d.gc->done) return;
   xupdate_body<float>(g, d.Z, d.x, d.n, d.st, d.R, d.g, sR);
 }
 
 __global__ void __launch_bounds__(TILE) kg_residual(const __grid_constant__ GTable t, const GSlot* sl) {
   VGrid g;
   const GSlot& d = sl[t.slot[gt_entry(t, g)]];
-  residual_body(g, d.rp, d.col, d.val, d.x, d.b, d.V, d.n, d.st, d.g, d.hist, d.thist, d.partials, d.counter);
+  if (d.gc->phase != d.m || d.gc->done) return;
+  residual_body(g, d.rp, d.col, d.val, d.x, d.b, d.V, d.n, d.st, d.g, d.hist, d.thist, d.partials, d.counter,
+                d.gc);
 }
 
 // ---------------------------------------------------------------- host side
@@ -861,6 +886,7 @@ int grouped_krylov_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, 
 }
 
 int grouped_cycle_end_launch(const std::vector<GHost>& reqs, int m, const GSlot* d_slots, cudaStream_t st) {
+  // (every request of the round: the kernels pick the ones at the end of their cycle)
   std::vector<std::pair<int, int>> ex, er;
   for (const GHost& q : reqs) {
     ex.push_back({q.slot, red_blocks(q.n)});
@@ -1173,37 +1199,6 @@ int solve_init_launch(const gnp_mat* A, Solver* S, const double* b, double* x, d
   k_residual<<<nt, TILE, 0, st>>>(A->rp, A->col, A->val, x, b, S->V, n, S->st, S->g, S->hist,
                                   S->thist, S->red.partials, S->red.counter);
   return check_launch("solve init");
-}
-
-bool cycle_after(const DevState& hs, double beta_prev, int maxiters, CycleCtl& c, int* status) {
-  if ((hs.last_flags & FL_NAN) || !std::isfinite(hs.beta)) {
-    *status = GNP_ERR_NAN;
-    return true;
-  }
-  if (hs.beta <= hs.tol) {
-    *status = GNP_OK;
-    return true;
-  }
-  if (hs.last_flags & FL_TIMEOUT) {
-    *status = GNP_ERR_TIMEOUT;
-    return true;
-  }
-  c.mism = (hs.last_flags & FL_EST_CONV) ? c.mism + 1 : 0;
-  c.stagn = (hs.beta >= beta_prev) ? c.stagn + 1 : 0;
-  if (c.mism >= 3) {
-    *status = GNP_ERR_RESIDUAL_MISMATCH;
-    return true;
-  }
-  if (c.stagn >= 2) {
-    *status = GNP_ERR_STAGNATION;
-    return true;
-  }
-  ++c.restarts;
-  if (hs.iters >= maxiters) {
-    *status = GNP_ERR_NOT_CONVERGED;
-    return true;
-  }
-  return false;
 }
 
 static bool graphs_enabled() {

@@ -14,16 +14,15 @@
 // Grouped steps (gnp_server_config::grouped): requests whose GNP runs on the short-row
 // layer kernels share one stream and advance one FGMRES step per round, every kernel of
 // the step launched once for all of them over a work table (each request's own grid,
-// GTable; its data, GSlot).  A round is the encoder, the L Res-GCONV layers and the two
-// CGS2 passes of the step for every grouped request, captured once as a CUDA graph per
-// set of grouped requests, plus the cycle-end kernels (x update, residual) of the requests
-// whose restart cycle ends in that round.  Request r sits at phase p in [0, m] of its cycle:
-// rounds with p < m run step p; at p = m the encoder's extra block finishes step m-1 (which
-// ends the cycle), and the cycle end follows in the same round.  The loop reads each cycle's
-// state asynchronously (pinned copy + event), applies the stopping rules and, when a
-// request ends or a grouped request is admitted, drains the stream, releases and admits,
-// and captures the round again: admission at step granularity.  The grouped step follows
-// the two-pass CGS2 schedule of fgmres_solve (GNP_ORTHO=cgs2), kernel for kernel.
+// GTable; its data, GSlot).  A round is the encoder, the L Res-GCONV layers, the two CGS2
+// passes and the cycle end (x update, residual) of every grouped request; the cycle-end
+// kernels act only for the requests whose cycle ends in that round, and the residual's
+// last block applies the stopping rules on the device (GCtl), so rounds need no host.
+// GROUP_ROUNDS rounds are captured as one CUDA graph per set of grouped requests; after
+// each launch the loop reads the control blocks (pinned copy + event) and, when a request
+// is done or a grouped request waits, drains the stream, releases and admits, and
+// captures again: admission every GROUP_ROUNDS steps.  The grouped step follows the
+// two-pass CGS2 schedule of fgmres_solve (GNP_ORTHO=cgs2), kernel for kernel.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -64,30 +63,29 @@ struct Request {
   int result = GNP_OK;
   int status = -1;
   gnp_solve_info info{};
-  // grouped steps: the request's slot, its phase in the cycle (rounds since the cycle
-  // began, 0..m), a cycle end enqueued whose state the loop has not read, and the
-  // stopping rules' verdict (released at the next rebuild of the round)
+  // grouped steps: the request's slot, and the stopping rules' verdict (read from its
+  // control block; the request is released at the next rebuild)
   bool grouped = false;
   int slot = -1;
-  int phase = 0;
-  bool end_pending = false;
   bool retire = false;
   int end_status = GNP_OK;
 };
 
-// The grouped requests: one stream, the device slot array, the captured round.
+// Rounds (FGMRES steps of every grouped request) per launch of the captured graph.
+constexpr int GROUP_ROUNDS = 8;
+
+// The grouped requests: one stream, the device slot array and control blocks, the graph of
+// GROUP_ROUNDS rounds, the launches in flight (each followed by a copy of the control
+// blocks to pinned memory and an event).
 struct Group {
   cudaStream_t stream = nullptr;
   GSlot* d_slots = nullptr;
+  GCtl* d_ctl = nullptr;
+  GCtl* h_ctl = nullptr;  // pinned
   GSlot h_slots[GT_MAX] = {};
   Request* req[GT_MAX] = {};
   cudaGraphExec_t exec = nullptr;
-  struct End {
-    cudaEvent_t ev;
-    std::vector<Request*> reqs;
-  };
-  std::deque<End> ends;            // enqueued cycle ends, oldest first
-  std::deque<cudaEvent_t> rounds;  // one event per enqueued round (bounds the rounds in flight)
+  std::deque<cudaEvent_t> launches;
   std::vector<cudaEvent_t> pool;
   int live() const {
     int c = 0;
@@ -110,7 +108,7 @@ struct Server {
   long long next_ticket = 1;
   size_t used_bytes = 0;
   bool stop = false;
-  // statistics (`rounds`: restart cycles begun)
+  // statistics (`rounds`: restart cycles run; a grouped request's are counted when it ends)
   long long rounds = 0, completed = 0, admitted = 0, max_active_seen = 0;
   int error = GNP_OK;
   char errmsg[256] = {0};
@@ -271,71 +269,62 @@ static void group_fail_all(Server* sv, int status) {
     }
 }
 
-// The oldest enqueued cycle end, once its state copy has landed: the stopping rules of
-// each of its requests (as fgmres_solve applies them after a cycle).
-static void group_end_read(Server* sv) {
-  Group& G = sv->grp;
-  Group::End e = G.ends.front();
-  G.ends.pop_front();
-  for (Request* r : e.reqs) {
-    r->end_pending = false;
-    ++r->ctl.cycles;
-    int status = GNP_OK;
-    const DevState& hs = *r->mirror;
-    const bool end = cycle_after(hs, r->beta, r->maxiters, r->ctl, &status);
-    r->beta = hs.beta;
-    if (end && !r->retire) {
-      r->retire = true;
-      r->end_status = status;
-    }
-  }
-  G.pool.push_back(e.ev);
-}
-
-// Read the cycle ends that have completed (blocking: all of them).  Returns whether any.
+// Read the launches that have completed (blocking: all of them): requests whose control
+// block says done are to be released.  Returns whether any launch completed.
 static bool group_poll(Server* sv, bool block) {
   Group& G = sv->grp;
   bool any = false;
-  while (!G.ends.empty()) {
-    const cudaError_t q = block ? cudaEventSynchronize(G.ends.front().ev) : cudaEventQuery(G.ends.front().ev);
+  while (!G.launches.empty()) {
+    const cudaError_t q = block ? cudaEventSynchronize(G.launches.front()) : cudaEventQuery(G.launches.front());
     if (q == cudaErrorNotReady) break;
+    G.pool.push_back(G.launches.front());
+    G.launches.pop_front();
+    any = true;
     if (q != cudaSuccess) {
       set_error("server: grouped round failed: %s", cudaGetErrorString(q));
-      for (Request* r : G.ends.front().reqs) r->end_pending = false;
-      G.pool.push_back(G.ends.front().ev);
-      G.ends.pop_front();
       group_fail_all(sv, GNP_ERR_CUDA);
-      any = true;
       continue;
     }
-    group_end_read(sv);
-    any = true;
+    // h_ctl holds the copy of this launch or a later one: done never reverts
+    for (int k = 0; k < GT_MAX; ++k) {
+      Request* r = G.req[k];
+      if (r && !r->retire && G.h_ctl[k].done) {
+        r->retire = true;
+        r->end_status = G.h_ctl[k].status;
+      }
+    }
   }
   return any;
 }
 
-// Capture the round for the current grouped requests: per class of hidden precision and
-// layer form the GNP application, then the CGS2 passes of all of them.
+// Capture GROUP_ROUNDS rounds for the current grouped requests: per class of hidden
+// precision and layer form the GNP application, then the CGS2 passes and the cycle end
+// of all of them.
 static int group_capture(Server* sv) {
   Group& G = sv->grp;
   if (G.exec) cudaGraphExecDestroy(G.exec);
   G.exec = nullptr;
   std::vector<GHost> all;
   std::vector<std::vector<GHost>> cls(4);
+  int m = 0;
   for (int k = 0; k < GT_MAX; ++k) {
     Request* r = G.req[k];
     if (!r) continue;
     const GHost h{k, r->A->n, r->M};
     all.push_back(h);
     cls[(r->M->hprec == GNP_H_BF16 ? 2 : 0) + (r->M->cfg.form == GNP_LAYER_PAPER ? 0 : 1)].push_back(h);
+    m = r->m;
   }
   if (all.empty()) return GNP_OK;
   GNP_TRY_CUDA(cudaMemcpy(G.d_slots, G.h_slots, sizeof(G.h_slots), cudaMemcpyHostToDevice));
   GNP_TRY_CUDA(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal));
   int s = GNP_OK;
-  for (const auto& c : cls)
-    if (s == GNP_OK) s = grouped_apply_launch(c, G.d_slots, G.stream);
-  if (s == GNP_OK) s = grouped_krylov_launch(all, G.d_slots, G.stream);
+  for (int round = 0; round < GROUP_ROUNDS && s == GNP_OK; ++round) {
+    for (const auto& c : cls)
+      if (s == GNP_OK) s = grouped_apply_launch(c, G.d_slots, G.stream);
+    if (s == GNP_OK) s = grouped_krylov_launch(all, G.d_slots, G.stream);
+    if (s == GNP_OK) s = grouped_cycle_end_launch(all, m, G.d_slots, G.stream);
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(G.stream, &graph);
   if (s != GNP_OK) {
@@ -345,24 +334,27 @@ static int group_capture(Server* sv) {
   if (ce == cudaSuccess) ce = cudaGraphInstantiate(&G.exec, graph, 0);
   if (graph) cudaGraphDestroy(graph);
   if (ce != cudaSuccess) {
-    set_error("server: capture of the grouped round failed: %s", cudaGetErrorString(ce));
+    set_error("server: capture of the grouped rounds failed: %s", cudaGetErrorString(ce));
     G.exec = nullptr;
     return GNP_ERR_CUDA;
   }
   return GNP_OK;
 }
 
-// Release the requests the stopping rules ended and admit `fresh` (grouped requests taken
-// from the queue): drain the stream, read every pending cycle end, free and fill slots,
-// capture the round again.  Requests that end here go to `ended`.
+// Release the requests that are done and admit `fresh` (grouped requests taken from the
+// queue): drain the stream, read the control blocks, free and fill slots, capture the
+// rounds again.  Requests that end here go to `ended`.
 static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<Request*>& ended) {
   Group& G = sv->grp;
   if (!G.stream) {
     int e = GNP_OK;
     if (cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking) != cudaSuccess) e = GNP_ERR_CUDA;
     if (e == GNP_OK) e = dev_alloc(&G.d_slots, (size_t)GT_MAX);
+    if (e == GNP_OK) e = dev_alloc(&G.d_ctl, (size_t)GT_MAX);
+    if (e == GNP_OK && cudaMallocHost(reinterpret_cast<void**>(&G.h_ctl), sizeof(GCtl) * GT_MAX) != cudaSuccess)
+      e = GNP_ERR_OOM;
     if (e != GNP_OK) {
-      set_error("server: grouped stream or slot array");
+      set_error("server: grouped stream, slot array or control blocks");
       for (Request* r : fresh) {
         finish(sv, r, GNP_ERR_CUDA);
         ended.push_back(r);
@@ -376,11 +368,25 @@ static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<
     group_fail_all(sv, GNP_ERR_CUDA);
   }
   group_poll(sv, true);
-  for (cudaEvent_t e : G.rounds) G.pool.push_back(e);
-  G.rounds.clear();
+  if (cudaMemcpy(G.h_ctl, G.d_ctl, sizeof(GCtl) * GT_MAX, cudaMemcpyDeviceToHost) != cudaSuccess)
+    group_fail_all(sv, GNP_ERR_CUDA);
   for (int k = 0; k < GT_MAX; ++k) {
     Request* r = G.req[k];
-    if (!r || !r->retire) continue;
+    if (!r) continue;
+    if (!r->retire && G.h_ctl[k].done) {
+      r->retire = true;
+      r->end_status = G.h_ctl[k].status;
+    }
+    if (!r->retire) continue;
+    const GCtl& c = G.h_ctl[k];
+    r->ctl.stagn = c.stagn;
+    r->ctl.mism = c.mism;
+    r->ctl.restarts = c.restarts;
+    r->ctl.cycles = c.cycles;
+    sv->rounds += c.cycles;
+    if (cudaMemcpy(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess &&
+        r->end_status == GNP_OK)
+      r->end_status = GNP_ERR_CUDA;
     fill_result(r);
     finish(sv, r, r->end_status);
     ended.push_back(r);
@@ -396,9 +402,17 @@ static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<
     }
     int k = 0;
     while (G.req[k]) ++k;  // admission left a free slot for every grouped request
+    const GCtl c0{-1, 0, GNP_OK, 0, 0, 0, 0, 0};
+    if (cudaMemcpy(G.d_ctl + k, &c0, sizeof(GCtl), cudaMemcpyHostToDevice) != cudaSuccess) {
+      finish(sv, r, GNP_ERR_CUDA);
+      ended.push_back(r);
+      continue;
+    }
     Solver* S = r->S;
     GSlot& d = G.h_slots[k];
     d = GSlot{};
+    d.gc = G.d_ctl + k;
+    d.m = r->m;
     d.rp = r->A->rp;
     d.col = r->A->col;
     d.val = r->A->val;
@@ -429,9 +443,7 @@ static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<
     d.b = r->b;
     d.x = r->x;
     r->slot = k;
-    r->phase = 0;
     G.req[k] = r;
-    ++sv->rounds;
   }
   fresh.clear();
   if (group_capture(sv) != GNP_OK) {
@@ -440,72 +452,36 @@ static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<
   }
 }
 
-// Enqueue one round: the step of every grouped request, then the cycle end of those at
-// phase m (each after its previous cycle's state has been read), the copies of their
-// state and an event.
-static void group_round(Server* sv) {
+// Launch the captured rounds again unless two launches are still in flight; then the copy
+// of the control blocks and an event.  Returns whether it launched.
+static bool group_launch(Server* sv) {
   Group& G = sv->grp;
-  std::vector<GHost> ending;
-  std::vector<Request*> ending_r;
-  for (int k = 0; k < GT_MAX; ++k) {
-    Request* r = G.req[k];
-    if (!r || r->phase != r->m) continue;
-    while (r->end_pending) group_poll(sv, true);
-    if (r->retire) continue;
-    ending.push_back(GHost{k, r->A->n, r->M});
-    ending_r.push_back(r);
-  }
-  int s = GNP_OK;
-  if (cudaGraphLaunch(G.exec, G.stream) != cudaSuccess) {
-    set_error("server: grouped round launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-    s = GNP_ERR_CUDA;
-  }
-  if (s == GNP_OK && !ending.empty()) {
-    s = grouped_cycle_end_launch(ending, ending_r[0]->m, G.d_slots, G.stream);
-    for (Request* r : ending_r)
-      if (s == GNP_OK && cudaMemcpyAsync(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost,
-                                         G.stream) != cudaSuccess)
-        s = GNP_ERR_CUDA;
-    Group::End e{group_event(G), ending_r};
-    if (s == GNP_OK && (!e.ev || cudaEventRecord(e.ev, G.stream) != cudaSuccess)) s = GNP_ERR_CUDA;
-    if (s == GNP_OK) {
-      for (Request* r : ending_r) r->end_pending = true;
-      G.ends.push_back(e);
-    } else if (e.ev) {
-      G.pool.push_back(e.ev);
-    }
-  }
-  if (s != GNP_OK) {
-    group_fail_all(sv, GNP_ERR_CUDA);
-    return;
-  }
-  for (Request* r : G.req) {
-    if (!r) continue;
-    r->phase = r->phase == r->m ? 0 : r->phase + 1;
-    if (r->phase == 0 && !r->retire) ++sv->rounds;
-  }
-  // at most three rounds in flight: the loop stays close to the device
+  if (!G.exec || G.launches.size() >= 2) return false;
   cudaEvent_t ev = group_event(G);
-  if (ev && cudaEventRecord(ev, G.stream) == cudaSuccess) G.rounds.push_back(ev);
-  else if (ev) G.pool.push_back(ev);
-  while (G.rounds.size() > 3) {
-    cudaEventSynchronize(G.rounds.front());
-    G.pool.push_back(G.rounds.front());
-    G.rounds.pop_front();
+  if (!ev || cudaGraphLaunch(G.exec, G.stream) != cudaSuccess ||
+      cudaMemcpyAsync(G.h_ctl, G.d_ctl, sizeof(GCtl) * GT_MAX, cudaMemcpyDeviceToHost, G.stream) != cudaSuccess ||
+      cudaEventRecord(ev, G.stream) != cudaSuccess) {
+    set_error("server: grouped round launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    if (ev) G.pool.push_back(ev);
+    group_fail_all(sv, GNP_ERR_CUDA);
+    return false;
   }
+  G.launches.push_back(ev);
+  return true;
 }
 
 static void group_destroy(Group& G) {
   if (G.stream) cudaStreamSynchronize(G.stream);
   if (G.exec) cudaGraphExecDestroy(G.exec);
-  for (auto& e : G.ends) G.pool.push_back(e.ev);
-  for (cudaEvent_t e : G.rounds) G.pool.push_back(e);
+  for (cudaEvent_t e : G.launches) G.pool.push_back(e);
   for (cudaEvent_t e : G.pool) cudaEventDestroy(e);
   G.pool.clear();
-  G.ends.clear();
-  G.rounds.clear();
+  G.launches.clear();
   if (G.stream) cudaStreamDestroy(G.stream);
   dev_free(G.d_slots);
+  dev_free(G.d_ctl);
+  if (G.h_ctl) cudaFreeHost(G.h_ctl);
+  G.h_ctl = nullptr;
   G.exec = nullptr;
   G.stream = nullptr;
 }
@@ -597,10 +573,7 @@ static void server_loop(Server* sv) {
       }
     }
     sv->running.swap(still);
-    if (glive > 0) {
-      group_round(sv);
-      progressed = true;
-    }
+    if (glive > 0) progressed |= group_launch(sv);
     for (Request* r : ended) release(r);
     lk.lock();
     for (Request* r : ended) {

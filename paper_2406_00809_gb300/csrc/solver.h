@@ -440,7 +440,38 @@ struct CycleCtl {
   int stagn = 0, mism = 0, restarts = 0, cycles = 0;
 };
 // After a cycle whose state is hs and whose starting residual was beta_prev: returns true
-// when the solve ends, with *status set.
-bool cycle_after(const DevState& hs, double beta_prev, int maxiters, CycleCtl& c, int* status);
+// when the solve ends, with *status set.  The stopping rules of fgmres_solve (host, after
+// every cycle) and of the solve server's grouped steps (device, at every cycle end).
+__host__ __device__ inline bool cycle_after(const DevState& hs, double beta_prev, int maxiters, CycleCtl& c,
+                                            int* status) {
+  if ((hs.last_flags & FL_NAN) || !isfinite(hs.beta)) {
+    *status = GNP_ERR_NAN;
+    return true;
+  }
+  if (hs.beta <= hs.tol) {
+    *status = GNP_OK;
+    return true;
+  }
+  if (hs.last_flags & FL_TIMEOUT) {
+    *status = GNP_ERR_TIMEOUT;
+    return true;
+  }
+  c.mism = (hs.last_flags & FL_EST_CONV) ? c.mism + 1 : 0;
+  c.stagn = (hs.beta >= beta_prev) ? c.stagn + 1 : 0;
+  if (c.mism >= 3) {
+    *status = GNP_ERR_RESIDUAL_MISMATCH;
+    return true;
+  }
+  if (c.stagn >= 2) {
+    *status = GNP_ERR_STAGNATION;
+    return true;
+  }
+  ++c.restarts;
+  if (hs.iters >= maxiters) {
+    *status = GNP_ERR_NOT_CONVERGED;
+    return true;
+  }
+  return false;
+}
 
 }  // namespace gnp
