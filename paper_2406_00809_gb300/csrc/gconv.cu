@@ -1197,7 +1197,7 @@ static int grouped_apply_t(const std::vector<GHost>& reqs, const GSlot* d_slots,
       P.sl = d_slots;
       P.l = l;
       for (size_t k = c0; k < c1; ++k) fill_layer_wt(sub[k]->M->w_host, l, P.w[k - c0]);
-      kg_gconv_row<HT, FORM><<<P.t.start[P.t.count], TILE, 0, st>>>(P);
+      GNP_TRY_CUDA(launch_pdl(kg_gconv_row<HT, FORM>, P.t.start[P.t.count], 0, st, P));
     }
   }
   for (int c0 = 0; c0 < R; c0 += GW) {  // decoder-fused last layer
@@ -1212,7 +1212,7 @@ static int grouped_apply_t(const std::vector<GHost>& reqs, const GSlot* d_slots,
       fill_layer_wt(M->w_host, M->cfg.L - 1, P.lw[k - c0]);
       fill_dec_wt(M->w_host, M->cfg.L, P.dw[k - c0]);
     }
-    kg_gconv_row_dec<HT, FORM><<<P.t.start[P.t.count], TILE, 0, st>>>(P);
+    GNP_TRY_CUDA(launch_pdl(kg_gconv_row_dec<HT, FORM>, P.t.start[P.t.count], 0, st, P));
   }
   return check_launch("grouped GNP apply");
 }

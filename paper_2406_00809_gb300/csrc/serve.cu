@@ -18,11 +18,15 @@
 // passes and the cycle end (x update, residual) of every grouped request; the cycle-end
 // kernels act only for the requests whose cycle ends in that round, and the residual's
 // last block applies the stopping rules on the device (GCtl), so rounds need no host.
-// GROUP_ROUNDS rounds are captured as one CUDA graph per set of grouped requests; after
-// each launch the loop reads the control blocks (pinned copy + event) and, when a request
-// is done or a grouped request waits, drains the stream, releases and admits, and
-// captures again: admission every GROUP_ROUNDS steps.  The grouped step follows the
-// two-pass CGS2 schedule of fgmres_solve (GNP_ORTHO=cgs2), kernel for kernel.
+// GROUP_ROUNDS rounds are captured as one CUDA graph per set of grouped requests, and at
+// most two launches of it are in flight.  After each launch the loop reads the control
+// blocks (pinned copy + event).  A request that is done has its final x and state (its
+// kernels do nothing from then on): its result is read at once, and its memory is freed
+// once every launch that still names it has completed.  A waiting request is set up on a
+// second stream and its slot filled, the rounds captured again on that stream while the
+// launches in flight run: admission every GROUP_ROUNDS steps, without draining the GPU.
+// The grouped step follows the two-pass CGS2 schedule of fgmres_solve (GNP_ORTHO=cgs2),
+// kernel for kernel.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -74,22 +78,39 @@ struct Request {
 // Rounds (FGMRES steps of every grouped request) per launch of the captured graph.
 constexpr int GROUP_ROUNDS = 8;
 
-// The grouped requests: one stream, the device slot array and control blocks, the graph of
-// GROUP_ROUNDS rounds, the launches in flight (each followed by a copy of the control
-// blocks to pinned memory and an event).
+// The grouped requests: the rounds' stream and a second one (set-up and capture), the
+// device slot array and control blocks, the graph of GROUP_ROUNDS rounds, the launches in
+// flight (each followed by a copy of the control blocks to pinned memory and an event),
+// and the released requests and graphs that launches in flight may still name.
 struct Group {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr, aux = nullptr;
   GSlot* d_slots = nullptr;
   GCtl* d_ctl = nullptr;
   GCtl* h_ctl = nullptr;  // pinned
   GSlot h_slots[GT_MAX] = {};
   Request* req[GT_MAX] = {};
+  bool busy[GT_MAX] = {};  // released, but a launch in flight may still name the slot
   cudaGraphExec_t exec = nullptr;
   std::deque<cudaEvent_t> launches;
+  std::deque<unsigned long long> launch_seq;  // the launches' numbers (1, 2, ...)
+  unsigned long long seq = 0;                 // launches issued
+  unsigned long long since[GT_MAX] = {};      // the first launch after slot k was filled
+  struct Grave {
+    cudaEvent_t ev;  // recorded after the last launch that may name these
+    std::vector<Request*> reqs;
+    std::vector<int> slots;
+    cudaGraphExec_t exec;
+  };
+  std::deque<Grave> graves;
   std::vector<cudaEvent_t> pool;
   int live() const {
     int c = 0;
     for (Request* r : req) c += r != nullptr;
+    return c;
+  }
+  int used() const {
+    int c = 0;
+    for (int k = 0; k < GT_MAX; ++k) c += req[k] != nullptr || busy[k];
     return c;
   }
 };
@@ -112,8 +133,8 @@ struct Server {
   long long rounds = 0, completed = 0, admitted = 0, max_active_seen = 0;
   int error = GNP_OK;
   char errmsg[256] = {0};
-  Group grp;  // loop thread only (besides its count, grp_live, published under the lock)
-  int grp_live = 0;
+  Group grp;  // loop thread only (besides its slot count, grp_used, published under the lock)
+  int grp_used = 0;
 };
 
 static size_t request_footprint(const gnp_mat* A, int m, int maxiters) {
@@ -277,18 +298,21 @@ static bool group_poll(Server* sv, bool block) {
   while (!G.launches.empty()) {
     const cudaError_t q = block ? cudaEventSynchronize(G.launches.front()) : cudaEventQuery(G.launches.front());
     if (q == cudaErrorNotReady) break;
+    const unsigned long long s = G.launch_seq.front();
     G.pool.push_back(G.launches.front());
     G.launches.pop_front();
+    G.launch_seq.pop_front();
     any = true;
     if (q != cudaSuccess) {
       set_error("server: grouped round failed: %s", cudaGetErrorString(q));
       group_fail_all(sv, GNP_ERR_CUDA);
       continue;
     }
-    // h_ctl holds the copy of this launch or a later one: done never reverts
+    // h_ctl holds the copy of launch s or a later one (done never reverts); a slot filled
+    // after launch s was issued may still hold its previous request's block there
     for (int k = 0; k < GT_MAX; ++k) {
       Request* r = G.req[k];
-      if (r && !r->retire && G.h_ctl[k].done) {
+      if (r && !r->retire && s >= G.since[k] && G.h_ctl[k].done) {
         r->retire = true;
         r->end_status = G.h_ctl[k].status;
       }
@@ -297,12 +321,31 @@ static bool group_poll(Server* sv, bool block) {
   return any;
 }
 
-// Capture GROUP_ROUNDS rounds for the current grouped requests: per class of hidden
-// precision and layer form the GNP application, then the CGS2 passes and the cycle end
-// of all of them.
-static int group_capture(Server* sv) {
+// Free what no launch in flight names any more (blocking: everything); the released
+// requests' results are then published (`ended`).
+static void group_bury(Server* sv, std::vector<Request*>& ended, bool block) {
   Group& G = sv->grp;
-  if (G.exec) cudaGraphExecDestroy(G.exec);
+  while (!G.graves.empty()) {
+    Group::Grave& g = G.graves.front();
+    const cudaError_t q = block ? cudaEventSynchronize(g.ev) : cudaEventQuery(g.ev);
+    if (q == cudaErrorNotReady) break;
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (int k : g.slots) G.busy[k] = false;
+    for (Request* r : g.reqs) {
+      finish(sv, r, r->end_status);
+      ended.push_back(r);
+    }
+    G.pool.push_back(g.ev);
+    G.graves.pop_front();
+  }
+}
+
+// Capture GROUP_ROUNDS rounds for the current grouped requests on the second stream: per
+// class of hidden precision and layer form the GNP application, then the CGS2 passes and
+// the cycle end of all of them.  The previous graph goes to the graveyard with `grave`.
+static int group_capture(Server* sv, Group::Grave& grave) {
+  Group& G = sv->grp;
+  grave.exec = G.exec;
   G.exec = nullptr;
   std::vector<GHost> all;
   std::vector<std::vector<GHost>> cls(4);
@@ -316,17 +359,16 @@ static int group_capture(Server* sv) {
     m = r->m;
   }
   if (all.empty()) return GNP_OK;
-  GNP_TRY_CUDA(cudaMemcpy(G.d_slots, G.h_slots, sizeof(G.h_slots), cudaMemcpyHostToDevice));
-  GNP_TRY_CUDA(cudaStreamBeginCapture(G.stream, cudaStreamCaptureModeThreadLocal));
+  GNP_TRY_CUDA(cudaStreamBeginCapture(G.aux, cudaStreamCaptureModeThreadLocal));
   int s = GNP_OK;
   for (int round = 0; round < GROUP_ROUNDS && s == GNP_OK; ++round) {
     for (const auto& c : cls)
-      if (s == GNP_OK) s = grouped_apply_launch(c, G.d_slots, G.stream);
-    if (s == GNP_OK) s = grouped_krylov_launch(all, G.d_slots, G.stream);
-    if (s == GNP_OK) s = grouped_cycle_end_launch(all, m, G.d_slots, G.stream);
+      if (s == GNP_OK) s = grouped_apply_launch(c, G.d_slots, G.aux);
+    if (s == GNP_OK) s = grouped_krylov_launch(all, G.d_slots, G.aux);
+    if (s == GNP_OK) s = grouped_cycle_end_launch(all, m, G.d_slots, G.aux);
   }
   cudaGraph_t graph = nullptr;
-  cudaError_t ce = cudaStreamEndCapture(G.stream, &graph);
+  cudaError_t ce = cudaStreamEndCapture(G.aux, &graph);
   if (s != GNP_OK) {
     if (graph) cudaGraphDestroy(graph);
     return s;
@@ -341,20 +383,69 @@ static int group_capture(Server* sv) {
   return GNP_OK;
 }
 
-// Release the requests that are done and admit `fresh` (grouped requests taken from the
-// queue): drain the stream, read the control blocks, free and fill slots, capture the
-// rounds again.  Requests that end here go to `ended`.
+// Fill slot k for request r (set up already): its GSlot and a fresh control block.
+static int group_fill(Group& G, int k, Request* r) {
+  const GCtl c0{-1, 0, GNP_OK, 0, 0, 0, 0, 0};
+  Solver* S = r->S;
+  GSlot d{};
+  d.gc = G.d_ctl + k;
+  d.m = r->m;
+  d.rp = r->A->rp;
+  d.col = r->A->col;
+  d.val = r->A->val;
+  d.valhat = r->M->valhat;
+  d.n = r->A->n;
+  d.L = r->M->cfg.L;
+  d.noscale = r->M->cfg.no_scale ? 1 : 0;
+  d.sqrt_n = std::sqrt((double)r->A->n);
+  d.Hh[0] = r->ws.H[0];
+  d.Hh[1] = r->ws.H[1];
+  d.tau = r->ws.tau;
+  d.V = S->V;
+  d.Z = S->Z;
+  d.w = S->w;
+  d.st = S->st;
+  d.Hb = S->H;
+  d.R = S->R;
+  d.cs = S->cs;
+  d.sn = S->sn;
+  d.g = S->g;
+  d.h1 = S->h1;
+  d.h2 = S->h2;
+  d.hf = S->hf;
+  d.hist = S->hist;
+  d.thist = S->thist;
+  d.partials = S->red.partials;
+  d.counter = S->red.counter;
+  d.b = r->b;
+  d.x = r->x;
+  G.h_slots[k] = d;
+  // the launches in flight do not name slot k (it is neither live nor busy): write its entries
+  GNP_TRY_CUDA(cudaMemcpyAsync(G.d_slots + k, &G.h_slots[k], sizeof(GSlot), cudaMemcpyHostToDevice, G.aux));
+  GNP_TRY_CUDA(cudaMemcpyAsync(G.d_ctl + k, &c0, sizeof(GCtl), cudaMemcpyHostToDevice, G.aux));
+  GNP_TRY_CUDA(cudaStreamSynchronize(G.aux));
+  r->slot = k;
+  G.req[k] = r;
+  G.since[k] = G.seq + 1;
+  return GNP_OK;
+}
+
+// Release the requests that are done (their results read now, their memory freed once no
+// launch in flight names them) and admit `fresh` (grouped requests from the queue), then
+// capture the rounds again.  Requests that end at set-up go to `ended`.
 static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<Request*>& ended) {
   Group& G = sv->grp;
   if (!G.stream) {
     int e = GNP_OK;
-    if (cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking) != cudaSuccess) e = GNP_ERR_CUDA;
+    if (cudaStreamCreateWithFlags(&G.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&G.aux, cudaStreamNonBlocking) != cudaSuccess)
+      e = GNP_ERR_CUDA;
     if (e == GNP_OK) e = dev_alloc(&G.d_slots, (size_t)GT_MAX);
     if (e == GNP_OK) e = dev_alloc(&G.d_ctl, (size_t)GT_MAX);
     if (e == GNP_OK && cudaMallocHost(reinterpret_cast<void**>(&G.h_ctl), sizeof(GCtl) * GT_MAX) != cudaSuccess)
       e = GNP_ERR_OOM;
     if (e != GNP_OK) {
-      set_error("server: grouped stream, slot array or control blocks");
+      set_error("server: grouped streams, slot array or control blocks");
       for (Request* r : fresh) {
         finish(sv, r, GNP_ERR_CUDA);
         ended.push_back(r);
@@ -363,93 +454,55 @@ static void group_rebuild(Server* sv, std::vector<Request*>& fresh, std::vector<
       return;
     }
   }
-  if (cudaStreamSynchronize(G.stream) != cudaSuccess) {
-    set_error("server: grouped round failed: %s", cudaGetErrorString(cudaGetLastError()));
-    group_fail_all(sv, GNP_ERR_CUDA);
-  }
-  group_poll(sv, true);
-  if (cudaMemcpy(G.h_ctl, G.d_ctl, sizeof(GCtl) * GT_MAX, cudaMemcpyDeviceToHost) != cudaSuccess)
-    group_fail_all(sv, GNP_ERR_CUDA);
+  Group::Grave grave{nullptr, {}, {}, nullptr};
   for (int k = 0; k < GT_MAX; ++k) {
     Request* r = G.req[k];
-    if (!r) continue;
-    if (!r->retire && G.h_ctl[k].done) {
-      r->retire = true;
-      r->end_status = G.h_ctl[k].status;
+    if (!r || !r->retire) continue;
+    // a done request's kernels no longer write its state or x: read its result now
+    GCtl c{};
+    if (cudaMemcpy(&c, G.d_ctl + k, sizeof(GCtl), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      if (r->end_status == GNP_OK) r->end_status = GNP_ERR_CUDA;
+    } else if (c.done && r->end_status != GNP_ERR_CUDA) {
+      r->end_status = c.status;  // the pinned copy read by the loop may have been in flight
     }
-    if (!r->retire) continue;
-    const GCtl& c = G.h_ctl[k];
     r->ctl.stagn = c.stagn;
     r->ctl.mism = c.mism;
     r->ctl.restarts = c.restarts;
     r->ctl.cycles = c.cycles;
     sv->rounds += c.cycles;
-    if (cudaMemcpy(r->mirror, r->S->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess &&
-        r->end_status == GNP_OK)
-      r->end_status = GNP_ERR_CUDA;
     fill_result(r);
-    finish(sv, r, r->end_status);
-    ended.push_back(r);
+    grave.reqs.push_back(r);
+    grave.slots.push_back(k);
+    G.busy[k] = true;
     G.req[k] = nullptr;
-    G.h_slots[k] = GSlot{};
   }
   for (Request* r : fresh) {
     ++sv->admitted;
-    if (!prepare(sv, r, GNP_OK, G.stream)) {
+    if (!prepare(sv, r, GNP_OK, G.aux)) {
       fill_result(r);
       ended.push_back(r);
       continue;
     }
     int k = 0;
-    while (G.req[k]) ++k;  // admission left a free slot for every grouped request
-    const GCtl c0{-1, 0, GNP_OK, 0, 0, 0, 0, 0};
-    if (cudaMemcpy(G.d_ctl + k, &c0, sizeof(GCtl), cudaMemcpyHostToDevice) != cudaSuccess) {
+    while (G.req[k] || G.busy[k]) ++k;  // admission left a free slot for every grouped request
+    if (group_fill(G, k, r) != GNP_OK) {
       finish(sv, r, GNP_ERR_CUDA);
       ended.push_back(r);
-      continue;
     }
-    Solver* S = r->S;
-    GSlot& d = G.h_slots[k];
-    d = GSlot{};
-    d.gc = G.d_ctl + k;
-    d.m = r->m;
-    d.rp = r->A->rp;
-    d.col = r->A->col;
-    d.val = r->A->val;
-    d.valhat = r->M->valhat;
-    d.n = r->A->n;
-    d.L = r->M->cfg.L;
-    d.noscale = r->M->cfg.no_scale ? 1 : 0;
-    d.sqrt_n = std::sqrt((double)r->A->n);
-    d.Hh[0] = r->ws.H[0];
-    d.Hh[1] = r->ws.H[1];
-    d.tau = r->ws.tau;
-    d.V = S->V;
-    d.Z = S->Z;
-    d.w = S->w;
-    d.st = S->st;
-    d.Hb = S->H;
-    d.R = S->R;
-    d.cs = S->cs;
-    d.sn = S->sn;
-    d.g = S->g;
-    d.h1 = S->h1;
-    d.h2 = S->h2;
-    d.hf = S->hf;
-    d.hist = S->hist;
-    d.thist = S->thist;
-    d.partials = S->red.partials;
-    d.counter = S->red.counter;
-    d.b = r->b;
-    d.x = r->x;
-    r->slot = k;
-    G.req[k] = r;
   }
   fresh.clear();
-  if (group_capture(sv) != GNP_OK) {
-    group_fail_all(sv, GNP_ERR_CUDA);
-    group_rebuild(sv, fresh, ended);  // releases them all (nothing left to capture)
+  const int cs = group_capture(sv, grave);
+  grave.ev = group_event(G);
+  if (!grave.ev || cudaEventRecord(grave.ev, G.stream) != cudaSuccess) {
+    // no event: wait for the launches in flight here instead
+    cudaStreamSynchronize(G.stream);
+    if (grave.ev) G.pool.push_back(grave.ev);
+    grave.ev = group_event(G);
+    if (grave.ev) cudaEventRecord(grave.ev, G.stream);
   }
+  if (grave.ev) G.graves.push_back(grave);
+  if (cs != GNP_OK) group_fail_all(sv, GNP_ERR_CUDA);
 }
 
 // Launch the captured rounds again unless two launches are still in flight; then the copy
@@ -467,23 +520,32 @@ static bool group_launch(Server* sv) {
     return false;
   }
   G.launches.push_back(ev);
+  G.launch_seq.push_back(++G.seq);
   return true;
 }
 
 static void group_destroy(Group& G) {
   if (G.stream) cudaStreamSynchronize(G.stream);
+  if (G.aux) cudaStreamSynchronize(G.aux);
   if (G.exec) cudaGraphExecDestroy(G.exec);
+  for (auto& g : G.graves) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    G.pool.push_back(g.ev);
+  }
+  G.graves.clear();
   for (cudaEvent_t e : G.launches) G.pool.push_back(e);
   for (cudaEvent_t e : G.pool) cudaEventDestroy(e);
   G.pool.clear();
   G.launches.clear();
+  G.launch_seq.clear();
   if (G.stream) cudaStreamDestroy(G.stream);
+  if (G.aux) cudaStreamDestroy(G.aux);
   dev_free(G.d_slots);
   dev_free(G.d_ctl);
   if (G.h_ctl) cudaFreeHost(G.h_ctl);
   G.h_ctl = nullptr;
   G.exec = nullptr;
-  G.stream = nullptr;
+  G.stream = G.aux = nullptr;
 }
 
 static void server_loop(Server* sv) {
@@ -493,7 +555,7 @@ static void server_loop(Server* sv) {
     // admission (under the lock): FIFO, by slot count and device-memory footprint
     std::vector<Request*> fresh, gfresh, ended;
     while (!sv->queue.empty() &&
-           (int)(sv->running.size() + sv->grp_live + fresh.size() + gfresh.size()) < sv->cfg.max_active) {
+           (int)(sv->running.size() + sv->grp_used + fresh.size() + gfresh.size()) < sv->cfg.max_active) {
       Request* r = sv->queue.front();
       if (r->footprint > sv->cfg.max_bytes) {
         sv->queue.pop_front();
@@ -507,16 +569,16 @@ static void server_loop(Server* sv) {
       // a request that can run in grouped steps always does (its result must not depend on
       // the load), so it waits for a grouped slot
       const bool grp = sv->cfg.grouped && grouped_ok(r->M);
-      if (grp && sv->grp_live + (int)gfresh.size() >= GT_MAX) break;
+      if (grp && sv->grp_used + (int)gfresh.size() >= GT_MAX) break;
       sv->queue.pop_front();
       sv->used_bytes += r->footprint;
       r->grouped = grp;
       (grp ? gfresh : fresh).push_back(r);
     }
-    if (sv->stop && sv->queue.empty() && sv->running.empty() && sv->grp_live == 0 && fresh.empty() &&
+    if (sv->stop && sv->queue.empty() && sv->running.empty() && sv->grp_used == 0 && fresh.empty() &&
         gfresh.empty())
       break;
-    if (sv->running.empty() && sv->grp_live == 0 && fresh.empty() && gfresh.empty()) {
+    if (sv->running.empty() && sv->grp_used == 0 && fresh.empty() && gfresh.empty()) {
       sv->cv.wait_for(lk, std::chrono::milliseconds(50));
       continue;
     }
@@ -524,6 +586,9 @@ static void server_loop(Server* sv) {
     bool progressed = !fresh.empty() || !gfresh.empty();
     // grouped requests: read finished cycle ends; release and admit (rebuilding the round)
     progressed |= group_poll(sv, false);
+    const size_t buried = ended.size();
+    group_bury(sv, ended, false);
+    progressed |= ended.size() > buried;
     bool rebuild = !gfresh.empty();
     for (Request* r : sv->grp.req) rebuild |= r && r->retire;
     if (rebuild) group_rebuild(sv, gfresh, ended);
@@ -581,7 +646,7 @@ static void server_loop(Server* sv) {
       r->status = r->result;
       ++sv->completed;
     }
-    sv->grp_live = glive;
+    sv->grp_used = sv->grp.used();
     sv->n_active = (int)sv->running.size() + glive;
     if (!ended.empty()) sv->done_cv.notify_all();
     if (!progressed) {
