@@ -166,6 +166,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=64)
     ap.add_argument("--max-gb", type=float, default=120.0)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--rates", default=None,
+                    help="absolute arrival rates (solves/s), in place of --load (to compare server modes)")
     ap.add_argument("--grouped", type=int, default=0, choices=[0, 1],
                     help="1: grouped steps for the requests whose GNP runs on the short-row kernels")
     a = ap.parse_args()
@@ -184,8 +186,11 @@ def main():
     solo = solo_latencies(g, srv, pool, a)
     capacity = 1.0 / float(np.mean([s_["seconds"] for s_ in solo]))
     print(json.dumps({"solo": solo, "sequential_capacity_per_s": capacity}), flush=True)
-    for i, load in enumerate(float(r) for r in a.load.split(",")):
-        out = run_rate(g, srv, pool, a, load * capacity, a.seed + 1 + i)
+    rates = ([float(r) for r in a.rates.split(",")] if a.rates
+             else [float(r) * capacity for r in a.load.split(",")])
+    for i, rate in enumerate(rates):
+        load = rate / capacity
+        out = run_rate(g, srv, pool, a, rate, a.seed + 1 + i)
         out.update({"metric": "serve latency", "load": load, "hprec": a.hprec, "pool": a.pool, "grouped": a.grouped,
                     "n_range": [a.nmin, a.nmax], "train_steps": a.train_steps})
         print(json.dumps(out), flush=True)
