@@ -832,9 +832,9 @@ __global__ void __launch_bounds__(RED_THREADS) kg_cgs2(const __grid_constant__ G
               d.counter);
 }
 
-// Every round launches the cycle end for every request; only those at phase m (their
-// encoder finished step m-1 this round) and not done run it.  The residual's last block
-// applies the stopping rules (cycle_after) and either restarts the cycle or marks the
+// Every grouped step launches the cycle end for every request; only those at phase m (whose
+// encoder finished step m-1 earlier in the same grouped step) and not done run it.  The
+// residual's last block applies the stopping rules (cycle_after) and either restarts the cycle or marks the
 // request done (active = 0: its later rounds do nothing, x stays as the deciding cycle
 // left it).
 __global__ void __launch_bounds__(RED_THREADS) kg_xupdate(const __grid_constant__ GTable t, const GSlot* sl) {

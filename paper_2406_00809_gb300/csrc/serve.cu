@@ -67,7 +67,7 @@ struct Request {
   int result = GNP_OK;
   int status = -1;
   gnp_solve_info info{};
-  // grouped steps: the request's slot, and the stopping rules' verdict (read from its
+  // grouped steps: the request's slot, and the stopping rules' outcome (read from its
   // control block; the request is released at the next rebuild)
   bool grouped = false;
   int slot = -1;

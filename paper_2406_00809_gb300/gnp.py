@@ -576,7 +576,9 @@ def gnp_function(M: Model):
 
 class Server:
     """Continuous-batching solve server (gnp_server_*).  Keeps the buffers of every
-    submitted request alive until it is collected."""
+    submitted request alive until it is collected.  grouped=True: the requests whose GNP
+    runs on the short-row layer kernels advance in grouped steps (one launch per kernel
+    for all of them); results equal lone fgmres_solve calls with GNP_ORTHO=cgs2."""
 
     def __init__(self, max_bytes: int, max_active: int = 64, restart: int = 30, grouped: bool = False):
         cfg = _ServerConfig(max_bytes, max_active, restart, 1 if grouped else 0)
