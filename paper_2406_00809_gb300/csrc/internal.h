@@ -210,7 +210,7 @@ bool grouped_ok(const gnp_model* M);
 int grouped_apply_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st);
 // The rest of the step for every request: w = A z with CGS2 pass 1, then pass 2.
 int grouped_krylov_launch(const std::vector<GHost>& reqs, const GSlot* d_slots, cudaStream_t st);
-// Cycle end for the requests of `reqs` whose cycle ends in the current step (phase m): x += Z y,
+// Cycle end for the requests of `reqs` that reach it this round (phase m): x += Z y,
 // r = b - A x, beta, the stopping rules, and the restart or the end of the solve.
 int grouped_cycle_end_launch(const std::vector<GHost>& reqs, int m, const GSlot* d_slots, cudaStream_t st);
 // Work tables: entries (slot, blocks) in order, at most `cap` per table.
