@@ -85,7 +85,7 @@ def test_grouped_alone_equals_mix_equals_direct(gnp, monkeypatch):
     mix = [(xs[k], srv.wait(t)) for k, t in enumerate(tickets)]
     st = srv.stats()
     srv.close()
-    assert st["max_active_seen"] >= n_grouped
+    assert st["max_active_seen"] > 6  # the mix ran more requests at once than one grouped launch takes
     for (name, *_), (xd, idr), (xa, ia), (xm, im) in zip(probs, direct, alone, mix):
         assert idr.status == ia.status == im.status, name
         assert idr.iters == ia.iters == im.iters, name
